@@ -1,0 +1,172 @@
+/*
+ * sbm.h -- C ABI of the GB300 matrix-free shifted boundary method (SBM) operator.
+ *
+ * The library evaluates y = A x for the SBM discretisation of the Poisson
+ * problem -Lap u = f in Omega, u = g on Gamma (paper, Section 2) on a
+ * Cartesian background mesh of [-1,1]^d, with tensor-product Q_p elements,
+ * in a continuous Galerkin (CG) or symmetric interior penalty discontinuous
+ * Galerkin (DG) form, matrix-free (Section 3, Algorithms 1-3).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns an int status (SBM_OK = 0 or an SBM_ERR_* code);
+ *    no C++ exception crosses this boundary.  sbm_error_string() names a code;
+ *    sbm_last_error_detail() gives a message for the calling thread's last error.
+ *  - The library owns all set-up data (host and device) of an sbm_problem and
+ *    frees it in sbm_destroy().  The caller owns every vector argument (x, y,
+ *    b, diag, ...) and the CUDA stream.  "device" pointers are CUDA device
+ *    (or managed) memory on the current device; "host" pointers are ordinary
+ *    CPU memory (pinned memory gives faster copies but is not required).
+ *  - Device work is enqueued on the given stream (a cudaStream_t passed as
+ *    void*; NULL = the legacy default stream) and is asynchronous unless the
+ *    entry point says otherwise.
+ *  - Vectors are in the problem's global DoF order:
+ *      CG: nodes of the global Gauss-Lobatto lattice ((pN+1)^d nodes, axis 0
+ *          fastest) that belong to an active cell, in increasing lattice order;
+ *      DG: active cells in lexicographic order (axis 0 fastest), (p+1)^d
+ *          values each, local lexicographic order inside a cell.
+ *  - Thread safety: distinct problems may be used from different threads;
+ *    one problem must not be used by two threads at once.
+ */
+#ifndef SBM_H
+#define SBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+  SBM_OK = 0,
+  SBM_ERR_ARG = 1,            /* invalid argument (null pointer, size, degree, ...) */
+  SBM_ERR_OOM = 2,            /* host or device allocation failed */
+  SBM_ERR_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+  SBM_ERR_EMPTY_DOMAIN = 4,   /* no active cell: the true domain misses every cell centre */
+  SBM_ERR_NOT_CONVERGED = 5,  /* iterative solver hit maxit (last iterate is still written) */
+  SBM_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+  SBM_ERR_STATE = 7,          /* call not valid in the problem's current state */
+  SBM_ERR_UNSUPPORTED = 8,    /* combination not built (e.g. degree > 6) */
+  SBM_ERR_GEOMETRY = 9        /* closest-point projection failed for a surrogate point */
+};
+
+/* ---- problem description ------------------------------------------------ */
+enum { SBM_GEOM_BALL = 0, SBM_GEOM_ELLIPSOID = 1, SBM_GEOM_TORUS = 2, SBM_GEOM_BOX = 3 };
+
+/*
+ * Geometry parameters (geom[]), d = dim:
+ *   BALL      : centre c[d], radius r                 phi = |x - c| - r
+ *   ELLIPSOID : semi-axes a[d], rotation R[d*d] (row-major, x = c + R y with
+ *               y in the ellipsoid's frame), centre c[d]
+ *                                                     phi = sum (y_i/a_i)^2 - 1
+ *   TORUS     : major radius R, minor radius r (d = 3, axis z, centred at 0)
+ *                                                     phi = (sqrt(x^2+y^2)-R)^2 + z^2 - r^2
+ *   BOX       : centre c[d], half-widths b[d]        phi = max_i |x_i - c_i| - b_i
+ * A background cell is active iff phi(cell centre) < 0 (strictly).
+ * Penalties: CG sigma = pen_shift * p^2 / h; DG surrogate faces
+ * sigma = pen_shift * (p+1)^2 / h and interior faces
+ * sigma_F = pen_interior * (p+1)^2 / h; h = 2 / cells_per_side.
+ */
+typedef struct {
+  int dim;              /* 2 or 3 */
+  int degree;           /* p, 1..6 */
+  int cells_per_side;   /* N >= 1; the mesh is N^d cells of [-1,1]^d */
+  int dg;               /* 0 = continuous Galerkin, 1 = SIPG discontinuous Galerkin */
+  int geom_kind;        /* SBM_GEOM_* */
+  double geom[16];      /* geometry parameters, see above */
+  double pen_shift;     /* C in sigma = C p^2/h (CG) or C (p+1)^2/h (DG); paper leaves it open */
+  double pen_interior;  /* C_F in sigma_F = C_F (p+1)^2/h (DG interior faces) */
+} sbm_desc;
+
+typedef struct sbm_problem sbm_problem;
+
+/*
+ * Build a problem on the host, in FP64: active cells and surrogate faces
+ * (Section 2), the closest points on Gamma of the surrogate-face Gauss points
+ * and their reference coordinates in the owning cell's frame (Sections 2.1
+ * and 3.4), and the global DoF numbering.  No CUDA call is made (this works
+ * without a GPU).  *out receives the handle (NULL on error).
+ * Errors: SBM_ERR_ARG (bad desc), SBM_ERR_UNSUPPORTED (degree/dim),
+ * SBM_ERR_EMPTY_DOMAIN, SBM_ERR_GEOMETRY, SBM_ERR_OOM.
+ */
+int sbm_create(const sbm_desc* desc, sbm_problem** out);
+
+/*
+ * Build the precomputed operator data (Section 3.4: per surrogate-face
+ * quadrature point, the 1D basis values at the shifted point's reference
+ * coordinates; the cell order and DoF line table the kernels use) and upload
+ * it to the current CUDA device, synchronously.  Must be called once before
+ * any apply/diagonal/solve call; the problem is then bound to that device.
+ * Errors: SBM_ERR_STATE (called twice), SBM_ERR_OOM, SBM_ERR_CUDA.
+ */
+int sbm_setup_face_data(sbm_problem* prob);
+
+/* Free every host and device resource of the problem (NULL is ignored).
+ * The caller must make sure no work that uses the problem is still running. */
+void sbm_destroy(sbm_problem* prob);
+
+/* Sizes: global DoFs, active cells, surrogate faces, DG interior faces
+ * (0 for CG).  Any output pointer may be NULL. */
+int sbm_sizes(const sbm_problem* prob, int64_t* n_dofs, int64_t* n_cells,
+              int64_t* n_sfaces, int64_t* n_ifaces);
+
+/*
+ * Copy the geometry to host buffers (for tests and diagnostics; any may be
+ * NULL):
+ *   cells  [n_cells * dim]         int32 cell multi-indices, lexicographic order
+ *   sfaces [n_sfaces * 3]          int32 (active-cell rank, normal axis k, side s)
+ *                                  per surrogate face; outward normal (2s-1) e_k;
+ *                                  order: by cell, then k, then s
+ *   face_x [n_sfaces * Q * dim]    double closest points x_q on Gamma of the
+ *                                  face Gauss points, Q = (p+1)^(d-1), first
+ *                                  tangential index fastest
+ */
+int sbm_export_geometry(const sbm_problem* prob, int32_t* cells, int32_t* sfaces,
+                        double* face_x);
+
+/*
+ * Matrix-free apply in FP64: y = A x (Section 3.5 workflow; cell term by sum
+ * factorisation, Algorithm 1; surrogate faces, Algorithm 3; DG interior
+ * faces, Algorithm 2).  x and y are device arrays of n_dofs doubles; they
+ * must not overlap.  Atomic-free: repeated calls give bitwise-equal y.
+ * Asynchronous on stream.  Errors: SBM_ERR_ARG, SBM_ERR_STATE (no device data),
+ * SBM_ERR_CUDA.
+ */
+int sbm_apply_f64(sbm_problem* prob, const double* x, double* y, void* stream);
+
+/*
+ * Same as sbm_apply_f64 with host arrays: copies x to the device, applies,
+ * copies y back and synchronises the stream before returning (the path a
+ * caller without device buffers takes; the staging buffers are allocated
+ * once per problem on first use).
+ */
+int sbm_apply_f64_host(sbm_problem* prob, const double* x_host, double* y_host, void* stream);
+
+/*
+ * The diagonal of A (FP64, device array of n_dofs), for Jacobi scaling.
+ * Asynchronous on stream.
+ */
+int sbm_diagonal(sbm_problem* prob, double* diag, void* stream);
+
+/*
+ * Kernel timing (diagnostics).  While enabled, every apply records a CUDA
+ * event before and after its operator kernels (on the apply's stream, after
+ * the y = 0 fill).  sbm_profile_read waits for the recorded events, returns
+ * the summed kernel time in milliseconds and the number of operator kernel
+ * launches since the previous read, and resets both.  Either output may be
+ * NULL.  Enabling adds two event records per apply and nothing else.
+ */
+int sbm_profile_enable(sbm_problem* prob, int on);
+int sbm_profile_read(sbm_problem* prob, double* kernel_ms, int64_t* launches);
+
+/* Human-readable name of a status code (static string). */
+const char* sbm_error_string(int status);
+
+/* Detail message of the calling thread's most recent failed call ("" if none). */
+const char* sbm_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBM_H */

@@ -1,0 +1,241 @@
+"""GB300 matrix-free shifted boundary method (SBM) operator.
+
+Thin Python binding of the C ABI in ``include/sbm.h`` (``libsbm.so``, built
+in-tree by ``paper_2507_17053_gb300._build.build()``).  The functions here
+only marshal arguments: every step of the operator runs in the library's CUDA
+kernels.  PyTorch tensors are accepted for device and host buffers; streams
+are ``torch.cuda.Stream`` objects (default: the current stream).
+
+There is no CPU fallback: if the library cannot be loaded, every entry point
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsbm.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "sbm.h")
+
+SBM_OK = 0
+STATUS = {
+    0: "SBM_OK", 1: "SBM_ERR_ARG", 2: "SBM_ERR_OOM", 3: "SBM_ERR_CUDA",
+    4: "SBM_ERR_EMPTY_DOMAIN", 5: "SBM_ERR_NOT_CONVERGED", 6: "SBM_ERR_TIMEOUT",
+    7: "SBM_ERR_STATE", 8: "SBM_ERR_UNSUPPORTED", 9: "SBM_ERR_GEOMETRY",
+}
+GEOM_KIND = {"ball": 0, "ellipsoid": 1, "torus": 2, "box": 3}
+
+
+class SbmError(RuntimeError):
+    def __init__(self, status: int, func: str, detail: str):
+        super().__init__(f"{func}: {STATUS.get(status, status)} ({detail})")
+        self.status = status
+
+
+class sbm_desc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("degree", ctypes.c_int),
+        ("cells_per_side", ctypes.c_int),
+        ("dg", ctypes.c_int),
+        ("geom_kind", ctypes.c_int),
+        ("geom", ctypes.c_double * 16),
+        ("pen_shift", ctypes.c_double),
+        ("pen_interior", ctypes.c_double),
+    ]
+
+
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_SIGS = {
+    "sbm_create": (ctypes.c_int, [ctypes.POINTER(sbm_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "sbm_setup_face_data": (ctypes.c_int, [ctypes.c_void_p]),
+    "sbm_destroy": (None, [ctypes.c_void_p]),
+    "sbm_sizes": (ctypes.c_int, [ctypes.c_void_p, _c_i64p, _c_i64p, _c_i64p, _c_i64p]),
+    "sbm_export_geometry": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "sbm_apply_f64": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "sbm_apply_f64_host": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "sbm_diagonal": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "sbm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), _c_i64p]),
+    "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sbm_last_error_detail": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/sbm.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sbm_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsbm.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} not built; run paper_2507_17053_gb300._build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, func: str):
+    if status != SBM_OK:
+        detail = lib().sbm_last_error_detail().decode()
+        raise SbmError(status, func, detail)
+
+
+def _ptr(t) -> int:
+    """Raw data pointer of a tensor/ndarray (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data            # numpy
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_desc(dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
+              pen_interior=1.0) -> sbm_desc:
+    d = sbm_desc()
+    d.dim, d.degree, d.cells_per_side, d.dg = dim, degree, cells, int(bool(dg))
+    d.geom_kind = GEOM_KIND[kind] if isinstance(kind, str) else int(kind)
+    g = list(geom)
+    if len(g) > 16:
+        raise ValueError("at most 16 geometry parameters")
+    for i, v in enumerate(g):
+        d.geom[i] = float(v)
+    d.pen_shift, d.pen_interior = float(pen_shift), float(pen_interior)
+    return d
+
+
+# ---- entry points with the C names ------------------------------------------
+
+def sbm_create(desc: sbm_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sbm_create(ctypes.byref(desc), ctypes.byref(h)), "sbm_create")
+    return h.value
+
+
+def sbm_setup_face_data(handle: int) -> None:
+    _check(lib().sbm_setup_face_data(handle), "sbm_setup_face_data")
+
+
+def sbm_destroy(handle: int) -> None:
+    lib().sbm_destroy(handle)
+
+
+def sbm_sizes(handle: int) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().sbm_sizes(handle, *[ctypes.byref(x) for x in v]), "sbm_sizes")
+    return dict(n_dofs=v[0].value, n_cells=v[1].value, n_sfaces=v[2].value, n_ifaces=v[3].value)
+
+
+def sbm_export_geometry(handle: int, cells=None, sfaces=None, face_x=None) -> None:
+    _check(lib().sbm_export_geometry(handle, _ptr(cells), _ptr(sfaces), _ptr(face_x)),
+           "sbm_export_geometry")
+
+
+def sbm_apply_f64(handle: int, x, y, stream=None) -> None:
+    _check(lib().sbm_apply_f64(handle, _ptr(x), _ptr(y), _stream(stream)), "sbm_apply_f64")
+
+
+def sbm_apply_f64_host(handle: int, x_host, y_host, stream=None) -> None:
+    _check(lib().sbm_apply_f64_host(handle, _ptr(x_host), _ptr(y_host), _stream(stream)),
+           "sbm_apply_f64_host")
+
+
+def sbm_diagonal(handle: int, diag, stream=None) -> None:
+    _check(lib().sbm_diagonal(handle, _ptr(diag), _stream(stream)), "sbm_diagonal")
+
+
+def sbm_profile_enable(handle: int, on: bool) -> None:
+    _check(lib().sbm_profile_enable(handle, int(bool(on))), "sbm_profile_enable")
+
+
+def sbm_profile_read(handle: int) -> tuple[float, int]:
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().sbm_profile_read(handle, ctypes.byref(ms), ctypes.byref(n)), "sbm_profile_read")
+    return ms.value, n.value
+
+
+class Problem:
+    """Owning wrapper around an sbm_problem handle."""
+
+    def __init__(self, dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
+                 pen_interior=1.0, device=True):
+        self.desc = make_desc(dim, degree, cells, kind, geom, dg, pen_shift, pen_interior)
+        self.dim, self.degree, self.dg = dim, degree, bool(dg)
+        self.handle = sbm_create(self.desc)
+        if device:
+            sbm_setup_face_data(self.handle)
+        s = sbm_sizes(self.handle)
+        self.n_dofs, self.n_cells = s["n_dofs"], s["n_cells"]
+        self.n_sfaces, self.n_ifaces = s["n_sfaces"], s["n_ifaces"]
+
+    @classmethod
+    def from_workload(cls, w, device=True):
+        return cls(w.dim, w.degree, w.cells, w.kind, w.geom, dg=w.dg, pen_shift=w.pen_shift,
+                   pen_interior=w.pen_interior, device=device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def geometry(self):
+        import numpy as np
+        n = self.degree + 1
+        Q = n ** (self.dim - 1)
+        cells = np.zeros((self.n_cells, self.dim), dtype=np.int32)
+        sfaces = np.zeros((self.n_sfaces, 3), dtype=np.int32)
+        fx = np.zeros((self.n_sfaces, Q, self.dim), dtype=np.float64)
+        sbm_export_geometry(self.handle, cells, sfaces, fx)
+        return cells, sfaces, fx
+
+    def apply_f64(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _expect(x, torch.float64, self.n_dofs)
+        _expect(y, torch.float64, self.n_dofs)
+        sbm_apply_f64(self.handle, x, y, stream)
+        return y
+
+    def apply_f64_host(self, x_host, y_host=None, stream=None):
+        import numpy as np
+        if y_host is None:
+            y_host = np.empty(self.n_dofs, dtype=np.float64)
+        sbm_apply_f64_host(self.handle, x_host, y_host, stream)
+        return y_host
+
+
+def _expect(t, dtype, n):
+    if t.dtype != dtype or t.numel() != n or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {n} elements")

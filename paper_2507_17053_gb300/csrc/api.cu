@@ -1,0 +1,321 @@
+// C ABI of the SBM operator library (declarations and contracts in include/sbm.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.hpp"
+
+namespace sbm {
+
+static thread_local std::string g_detail;
+
+static int fail(int code, const std::string& msg) {
+  g_detail = msg;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* where) {
+  g_detail = std::string(where) + ": " + cudaGetErrorString(e);
+  return SBM_ERR_CUDA;
+}
+
+template <typename T>
+KTab<T> make_ktab(const HostProblem& hp) {
+  KTab<T> t;
+  std::memset(&t, 0, sizeof(t));
+  const Tables1D& tb = hp.tab;
+  const int n = hp.n;
+  const double hd2 = std::pow(hp.h, hp.d - 2);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      t.M[i][j] = (T)tb.M[i][j];
+      t.K[i][j] = (T)tb.K[i][j];
+      t.Mh[i][j] = (T)(hd2 * tb.M[i][j]);
+      t.Kh[i][j] = (T)(hd2 * tb.K[i][j]);
+      t.S[i][j] = (T)tb.S[i][j];
+    }
+  for (int j = 0; j < n; ++j) {
+    t.D0[j] = (T)tb.D0[j];
+    t.D1[j] = (T)tb.D1[j];
+  }
+  const double hd1 = std::pow(hp.h, hp.d - 1);
+  for (int q = 0; q < hp.L; ++q) {
+    const int qa = q % n, qb = q / n;
+    const double w = (hp.d == 3) ? tb.gwts[qa] * tb.gwts[qb] : tb.gwts[qa];
+    t.W[q] = (T)(hd1 * w);
+  }
+  t.h_inv = (T)(1.0 / hp.h);
+  t.sigma = (T)hp.sigma;
+  return t;
+}
+template KTab<double> make_ktab<double>(const HostProblem&);
+template KTab<float> make_ktab<float>(const HostProblem&);
+
+cudaError_t Profiler::begin(cudaStream_t st) {
+  if (used + 2 > ev.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      ev.push_back(e);
+    }
+  }
+  return cudaEventRecord(ev[used], st);
+}
+
+cudaError_t Profiler::end(cudaStream_t st, int nlaunch) {
+  cudaError_t err = cudaEventRecord(ev[used + 1], st);
+  used += 2;
+  launches += nlaunch;
+  return err;
+}
+
+void Profiler::release() {
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  ev.clear();
+  used = 0;
+  launches = 0;
+}
+
+template <typename T>
+static cudaError_t upload(T** dst, const T* src, size_t count) {
+  *dst = nullptr;
+  if (count == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)dst, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+static void free_device(DeviceData* dd) {
+  cudaFree(dd->lines);
+  cudaFree(dd->cell_rank);
+  cudaFree(dd->face_start);
+  cudaFree(dd->face_kind);
+  cudaFree(dd->face_phi);
+  cudaFree(dd->nbr);
+  cudaFree(dd->stage_x);
+  cudaFree(dd->stage_y);
+  *dd = DeviceData();
+}
+
+// Order the cells for the kernels and upload the set-up data.
+static int build_device(const HostProblem& hp, DeviceData* dd) {
+  const int d = hp.d, n = hp.n, L = hp.L;
+  const int64_t Nc = (int64_t)hp.cell_bg.size();
+  const int64_t F = (int64_t)hp.sfaces.size() / 3;
+  // faces per cell (surrogate faces are grouped by cell already)
+  std::vector<int32_t> nf(Nc, 0), first_face(Nc, -1);
+  for (int64_t f = 0; f < F; ++f) {
+    const int c = hp.sfaces[3 * f];
+    if (first_face[c] < 0) first_face[c] = (int32_t)f;
+    nf[c]++;
+  }
+  dd->ncolours = hp.desc.dg ? 1 : (1 << d);
+  dd->col_start.assign(dd->ncolours + 1, 0);
+  dd->col_nint.assign(dd->ncolours, 0);
+  dd->order.clear();
+  dd->order.reserve(Nc);
+  for (int col = 0; col < dd->ncolours; ++col) {
+    dd->col_start[col] = (int)dd->order.size();
+    for (int pass = 0; pass < 2; ++pass)
+      for (int64_t c = 0; c < Nc; ++c) {
+        int cc = 0;
+        if (!hp.desc.dg)
+          for (int l = 0; l < d; ++l) cc |= (hp.cells[c * d + l] & 1) << l;
+        if (cc != col) continue;
+        if ((pass == 0) == (nf[c] == 0)) dd->order.push_back((int32_t)c);
+      }
+    int nint = 0;
+    for (int i = dd->col_start[col]; i < (int)dd->order.size(); ++i)
+      if (nf[dd->order[i]] == 0) nint++;
+    dd->col_nint[col] = nint;
+  }
+  dd->col_start[dd->ncolours] = (int)dd->order.size();
+
+  std::vector<int32_t> lines_o, fstart(Nc + 1, 0), fkind;
+  std::vector<double> fphi;
+  if (!hp.desc.dg) lines_o.resize(Nc * L);
+  fkind.reserve(F);
+  fphi.reserve(F * L * d * n);
+  for (int64_t i = 0; i < Nc; ++i) {
+    const int c = dd->order[i];
+    if (!hp.desc.dg)
+      std::memcpy(&lines_o[i * L], &hp.lines[(int64_t)c * L], L * sizeof(int32_t));
+    fstart[i] = (int32_t)fkind.size();
+    for (int j = 0; j < nf[c]; ++j) {
+      const int64_t f = first_face[c] + j;
+      fkind.push_back(hp.sfaces[3 * f + 1] | (hp.sfaces[3 * f + 2] << 2));
+      for (int q = 0; q < L; ++q)
+        for (int l = 0; l < d; ++l) {
+          double phi[kMaxN];
+          lagrange_values(hp.tab, hp.face_xi[(f * L + q) * d + l], phi);
+          for (int jj = 0; jj < n; ++jj) fphi.push_back(phi[jj]);
+        }
+    }
+  }
+  fstart[Nc] = (int32_t)fkind.size();
+
+  cudaError_t e;
+  if ((e = upload(&dd->lines, lines_o.data(), lines_o.size())) != cudaSuccess) goto err;
+  if ((e = upload(&dd->cell_rank, dd->order.data(), dd->order.size())) != cudaSuccess) goto err;
+  if ((e = upload(&dd->face_start, fstart.data(), fstart.size())) != cudaSuccess) goto err;
+  if ((e = upload(&dd->face_kind, fkind.data(), fkind.size())) != cudaSuccess) goto err;
+  if ((e = upload(&dd->face_phi, fphi.data(), fphi.size())) != cudaSuccess) goto err;
+  return SBM_OK;
+err:
+  free_device(dd);
+  return e == cudaErrorMemoryAllocation ? fail(SBM_ERR_OOM, "device allocation failed")
+                                        : cuda_fail(e, "upload");
+}
+
+}  // namespace sbm
+
+using namespace sbm;
+
+extern "C" {
+
+const char* sbm_error_string(int status) {
+  switch (status) {
+    case SBM_OK: return "ok";
+    case SBM_ERR_ARG: return "invalid argument";
+    case SBM_ERR_OOM: return "out of memory";
+    case SBM_ERR_CUDA: return "CUDA error";
+    case SBM_ERR_EMPTY_DOMAIN: return "empty domain (no active cell)";
+    case SBM_ERR_NOT_CONVERGED: return "not converged";
+    case SBM_ERR_TIMEOUT: return "device wait timed out";
+    case SBM_ERR_STATE: return "invalid state";
+    case SBM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SBM_ERR_GEOMETRY: return "closest-point projection failed";
+  }
+  return "unknown status";
+}
+
+const char* sbm_last_error_detail(void) { return g_detail.c_str(); }
+
+int sbm_create(const sbm_desc* desc, sbm_problem** out) {
+  if (!out) return fail(SBM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(SBM_ERR_ARG, "desc is NULL");
+  sbm_problem* P = new (std::nothrow) sbm_problem();
+  if (!P) return fail(SBM_ERR_OOM, "host allocation failed");
+  std::string err;
+  int st;
+  try {
+    st = build_host_problem(*desc, &P->hp, &err);
+  } catch (const std::bad_alloc&) {
+    st = SBM_ERR_OOM;
+    err = "host allocation failed";
+  }
+  if (st != SBM_OK) {
+    delete P;
+    return fail(st, err);
+  }
+  *out = P;
+  return SBM_OK;
+}
+
+int sbm_setup_face_data(sbm_problem* prob) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  if (prob->on_device) return fail(SBM_ERR_STATE, "device data already set up");
+  cudaError_t e = cudaGetDevice(&prob->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  int st;
+  try {
+    st = build_device(prob->hp, &prob->dd);
+  } catch (const std::bad_alloc&) {
+    st = fail(SBM_ERR_OOM, "host allocation failed");
+  }
+  if (st == SBM_OK) prob->on_device = true;
+  return st;
+}
+
+void sbm_destroy(sbm_problem* prob) {
+  if (!prob) return;
+  prob->prof.release();
+  if (prob->on_device) free_device(&prob->dd);
+  delete prob;
+}
+
+int sbm_sizes(const sbm_problem* prob, int64_t* n_dofs, int64_t* n_cells, int64_t* n_sfaces,
+              int64_t* n_ifaces) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  if (n_dofs) *n_dofs = prob->hp.n_dofs;
+  if (n_cells) *n_cells = (int64_t)prob->hp.cell_bg.size();
+  if (n_sfaces) *n_sfaces = (int64_t)prob->hp.sfaces.size() / 3;
+  if (n_ifaces) *n_ifaces = prob->hp.desc.dg ? (int64_t)prob->hp.ifaces.size() / 3 : 0;
+  return SBM_OK;
+}
+
+int sbm_export_geometry(const sbm_problem* prob, int32_t* cells, int32_t* sfaces, double* face_x) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  const HostProblem& hp = prob->hp;
+  if (cells) std::memcpy(cells, hp.cells.data(), hp.cells.size() * sizeof(int32_t));
+  if (sfaces) std::memcpy(sfaces, hp.sfaces.data(), hp.sfaces.size() * sizeof(int32_t));
+  if (face_x) std::memcpy(face_x, hp.face_x.data(), hp.face_x.size() * sizeof(double));
+  return SBM_OK;
+}
+
+int sbm_apply_f64(sbm_problem* prob, const double* x, double* y, void* stream) {
+  if (!prob || !x || !y) return fail(SBM_ERR_ARG, "NULL argument");
+  if (x == y) return fail(SBM_ERR_ARG, "x and y must not overlap");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (prob->hp.desc.dg) return fail(SBM_ERR_UNSUPPORTED, "DG apply not built");
+  cudaError_t e = launch_cg_apply_f64(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof);
+  if (e != cudaSuccess) return cuda_fail(e, "sbm_apply_f64");
+  return SBM_OK;
+}
+
+int sbm_apply_f64_host(sbm_problem* prob, const double* x_host, double* y_host, void* stream) {
+  if (!prob || !x_host || !y_host) return fail(SBM_ERR_ARG, "NULL argument");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  DeviceData& dd = prob->dd;
+  const size_t bytes = (size_t)prob->hp.n_dofs * sizeof(double);
+  cudaError_t e;
+  if (!dd.stage_x) {
+    if ((e = cudaMalloc((void**)&dd.stage_x, bytes)) != cudaSuccess) return cuda_fail(e, "stage");
+    if ((e = cudaMalloc((void**)&dd.stage_y, bytes)) != cudaSuccess) return cuda_fail(e, "stage");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((e = cudaMemcpyAsync(dd.stage_x, x_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "H2D");
+  int s = sbm_apply_f64(prob, dd.stage_x, dd.stage_y, stream);
+  if (s != SBM_OK) return s;
+  if ((e = cudaMemcpyAsync(y_host, dd.stage_y, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "D2H");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
+  return SBM_OK;
+}
+
+int sbm_diagonal(sbm_problem* prob, double* diag, void* stream) {
+  (void)stream;
+  if (!prob || !diag) return fail(SBM_ERR_ARG, "NULL argument");
+  return fail(SBM_ERR_UNSUPPORTED, "diagonal not built yet");
+}
+
+int sbm_profile_enable(sbm_problem* prob, int on) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  prob->prof.on = (on != 0);
+  return SBM_OK;
+}
+
+int sbm_profile_read(sbm_problem* prob, double* kernel_ms, int64_t* launches) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  Profiler& pf = prob->prof;
+  double total = 0.0;
+  for (size_t i = 0; i + 1 < pf.used; i += 2) {
+    cudaError_t e = cudaEventSynchronize(pf.ev[i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, pf.ev[i], pf.ev[i + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+    total += ms;
+  }
+  if (kernel_ms) *kernel_ms = total;
+  if (launches) *launches = pf.launches;
+  pf.used = 0;
+  pf.launches = 0;
+  return SBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal definitions shared by the C ABI and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "setup.hpp"
+
+namespace sbm {
+
+// 1D operator tables handed to kernels by value (kernel parameter space is a
+// constant bank: every FMA with a table operand reads it for free).
+template <typename T>
+struct KTab {
+  T M[kMaxN][kMaxN];     // 1D mass on [0,1]
+  T K[kMaxN][kMaxN];     // 1D stiffness on [0,1]
+  T Mh[kMaxN][kMaxN];    // h^(d-2) * M   (last sweep of the cell operator)
+  T Kh[kMaxN][kMaxN];    // h^(d-2) * K
+  T S[kMaxN][kMaxN];     // S[q][j] = phi_j(g_q)
+  T D0[kMaxN];           // phi_j'(0)
+  T D1[kMaxN];           // phi_j'(1)
+  T W[kMaxN * kMaxN];    // face weights h^(d-1) w_qa w_qb (tangential Gauss index q)
+  T h_inv;
+  T sigma;
+};
+
+template <typename T>
+KTab<T> make_ktab(const HostProblem& hp);
+
+// Device-resident set-up data of one problem.
+struct DeviceData {
+  // cells in kernel order: for each colour (CG) -- interior cells, then cells
+  // that own surrogate faces; DG uses one "colour" with the same split.
+  int ncolours = 0;
+  std::vector<int> col_start;    // [ncolours + 1] offsets into the ordered cell list
+  std::vector<int> col_nint;     // [ncolours] interior cells in each colour
+  std::vector<int32_t> order;    // ordered position -> active-cell rank
+  int32_t* lines = nullptr;      // CG [Nc * L]: global index of node (0, line) per x-line
+  int32_t* cell_rank = nullptr;  // [Nc] ordered position -> active-cell rank (DG base)
+  int32_t* face_start = nullptr; // [Nc + 1] per ordered cell, range into the ordered face list
+  int32_t* face_kind = nullptr;  // [F] k | (s << 2)
+  double* face_phi = nullptr;    // [F * Q * d * n] phi_j(xi_{q,l}) at the shifted points
+  int32_t* nbr = nullptr;        // DG [Nc * 2d] neighbour rank per (k, s), -1 = surrogate
+  double* stage_x = nullptr;     // host-apply staging buffers (allocated on first use)
+  double* stage_y = nullptr;
+};
+
+// Optional kernel timing: a pair of CUDA events around the operator kernels
+// of every apply (after the y = 0 memset), read back by sbm_profile_read.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // start/stop pairs
+  size_t used = 0;               // events recorded since the last read
+  int64_t launches = 0;          // operator kernel launches since the last read
+  cudaError_t begin(cudaStream_t st);
+  cudaError_t end(cudaStream_t st, int nlaunch);
+  void release();
+};
+
+struct CellLaunch {
+  int d, n;
+  int cpb;          // cells per block on interior tiles
+  int threads;      // block size
+};
+CellLaunch cell_launch_shape(int d, int n);
+
+// FP64 apply, CG: y = A x (memset + one launch per colour).
+cudaError_t launch_cg_apply_f64(const HostProblem& hp, const DeviceData& dd, const double* x,
+                                double* y, cudaStream_t st, Profiler* prof);
+
+}  // namespace sbm
+
+struct sbm_problem {
+  sbm::HostProblem hp;
+  sbm::DeviceData dd;
+  int device = 0;
+  bool on_device = false;   // sbm_setup_face_data done
+  sbm::Profiler prof;
+};

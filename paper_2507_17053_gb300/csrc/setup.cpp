@@ -1,0 +1,479 @@
+// Host-side FP64 set-up of an SBM problem (see setup.hpp).
+//
+// Compiled with -ffp-contract=off so that the level-set tests that decide
+// which cells are active are evaluated exactly as written (no fused
+// multiply-add reassociation), on x86 and Arm alike.
+#include "setup.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace sbm {
+
+// ---------------------------------------------------------------------------
+// 1D tables
+// ---------------------------------------------------------------------------
+
+// Legendre P_m(t) and P_m'(t) by the three-term recurrence.
+static void legendre(int m, double t, double* P, double* dP) {
+  double p0 = 1.0, p1 = t;
+  if (m == 0) { *P = 1.0; *dP = 0.0; return; }
+  for (int k = 1; k < m; ++k) {
+    double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  *P = p1;
+  // (1 - t^2) P_m' = m (P_{m-1} - t P_m); only used away from t = +-1
+  *dP = m * (p0 - t * p1) / (1.0 - t * t);
+}
+
+void build_tables(int p, Tables1D* t) {
+  const int n = p + 1;
+  *t = Tables1D();
+  t->n = n;
+  const double pi = 3.14159265358979323846;
+  // GLL nodes: +-1 and the roots of P_p'; Newton on P_p' with
+  // P_p'' = (2 t P_p' - p(p+1) P_p) / (1 - t^2) (Legendre's equation).
+  double tn[kMaxN];
+  tn[0] = -1.0;
+  tn[p] = 1.0;
+  for (int i = 1; i < p; ++i) {
+    double x = -std::cos(pi * i / p);
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(p, x, &P, &dP);
+      double d2P = (2.0 * x * dP - p * (p + 1.0) * P) / (1.0 - x * x);
+      double dx = dP / d2P;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    tn[i] = x;
+  }
+  for (int i = 0; i < n; ++i) {          // exact symmetry about 0
+    double s = 0.5 * (tn[i] - tn[p - i]);
+    t->nodes[i] = 0.5 * (s + 1.0);
+  }
+  t->nodes[0] = 0.0;
+  t->nodes[p] = 1.0;
+  // Gauss points: roots of P_n, weights 2 / ((1 - t^2) P_n'(t)^2)
+  double tg[kMaxN], wg[kMaxN];
+  for (int i = 0; i < n; ++i) {
+    double x = -std::cos(pi * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(n, x, &P, &dP);
+      double dx = P / dP;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    double P, dP;
+    legendre(n, x, &P, &dP);
+    tg[i] = x;
+    wg[i] = 2.0 / ((1.0 - x * x) * dP * dP);
+  }
+  for (int i = 0; i < n; ++i) {          // exact symmetry about 0
+    double s = 0.5 * (tg[i] - tg[n - 1 - i]);
+    double w = 0.5 * (wg[i] + wg[n - 1 - i]);
+    t->gpts[i] = 0.5 * (s + 1.0);
+    t->gwts[i] = 0.5 * w;
+  }
+  for (int q = 0; q < n; ++q) {
+    lagrange_values(*t, t->gpts[q], t->S[q]);
+    lagrange_derivs(*t, t->gpts[q], t->Dg[q]);
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double m = 0.0, k = 0.0;
+      for (int q = 0; q < n; ++q) {
+        m += t->gwts[q] * t->S[q][i] * t->S[q][j];
+        k += t->gwts[q] * t->Dg[q][i] * t->Dg[q][j];
+      }
+      t->M[i][j] = m;
+      t->K[i][j] = k;
+    }
+  lagrange_derivs(*t, 0.0, t->D0);
+  lagrange_derivs(*t, 1.0, t->D1);
+}
+
+// Barycentric weights lambda_j = 1 / prod_{m != j} (x_j - x_m).
+static void bary_weights(const Tables1D& t, double* lam) {
+  for (int j = 0; j < t.n; ++j) {
+    double prod = 1.0;
+    for (int m = 0; m < t.n; ++m)
+      if (m != j) prod *= (t.nodes[j] - t.nodes[m]);
+    lam[j] = 1.0 / prod;
+  }
+}
+
+// First (modified Lagrange) barycentric form: phi_j(x) = l(x) lambda_j / (x - x_j),
+// l(x) = prod_m (x - x_m); exact Kronecker delta at the nodes.  Stable for
+// extrapolation outside [0,1].
+void lagrange_values(const Tables1D& t, double x, double* phi) {
+  double lam[kMaxN];
+  bary_weights(t, lam);
+  for (int j = 0; j < t.n; ++j)
+    if (x == t.nodes[j]) {
+      for (int m = 0; m < t.n; ++m) phi[m] = (m == j) ? 1.0 : 0.0;
+      return;
+    }
+  double l = 1.0;
+  for (int m = 0; m < t.n; ++m) l *= (x - t.nodes[m]);
+  for (int j = 0; j < t.n; ++j) phi[j] = l * lam[j] / (x - t.nodes[j]);
+}
+
+// Derivatives: at a node x_i the differentiation-matrix entries
+// (lambda_j/lambda_i)/(x_i - x_j) and minus their row sum on the diagonal;
+// elsewhere phi_j'(x) = sum_{k != j} lambda_j prod_{m != j,k} (x - x_m).
+void lagrange_derivs(const Tables1D& t, double x, double* dphi) {
+  double lam[kMaxN];
+  bary_weights(t, lam);
+  for (int i = 0; i < t.n; ++i)
+    if (x == t.nodes[i]) {
+      double diag = 0.0;
+      for (int j = 0; j < t.n; ++j) {
+        if (j == i) continue;
+        dphi[j] = (lam[j] / lam[i]) / (t.nodes[i] - t.nodes[j]);
+        diag -= dphi[j];
+      }
+      dphi[i] = diag;
+      return;
+    }
+  for (int j = 0; j < t.n; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < t.n; ++k) {
+      if (k == j) continue;
+      double prod = lam[j];
+      for (int m = 0; m < t.n; ++m)
+        if (m != j && m != k) prod *= (x - t.nodes[m]);
+      s += prod;
+    }
+    dphi[j] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Level sets and closest points (Section 2.1: closest-point projection onto
+// Gamma, d = x - x~).  Fixed summation orders (axis 0 first).
+// ---------------------------------------------------------------------------
+
+int LevelSet::init(int k, int d, const double* g, std::string* err) {
+  kind = k;
+  dim = d;
+  switch (k) {
+    case SBM_GEOM_BALL:
+      for (int i = 0; i < d; ++i) c[i] = g[i];
+      r = g[d];
+      if (!(r > 0)) { *err = "ball radius must be > 0"; return SBM_ERR_ARG; }
+      return SBM_OK;
+    case SBM_GEOM_ELLIPSOID:
+      for (int i = 0; i < d; ++i) {
+        a[i] = g[i];
+        if (!(a[i] > 0)) { *err = "ellipsoid semi-axes must be > 0"; return SBM_ERR_ARG; }
+      }
+      for (int i = 0; i < d * d; ++i) R[i] = g[d + i];
+      for (int i = 0; i < d; ++i) c[i] = g[d + d * d + i];
+      return SBM_OK;
+    case SBM_GEOM_TORUS:
+      if (d != 3) { *err = "torus needs dim = 3"; return SBM_ERR_ARG; }
+      Rmaj = g[0];
+      rmin = g[1];
+      if (!(rmin > 0 && Rmaj > rmin)) { *err = "torus needs R > r > 0"; return SBM_ERR_ARG; }
+      return SBM_OK;
+    case SBM_GEOM_BOX:
+      for (int i = 0; i < d; ++i) {
+        c[i] = g[i];
+        half[i] = g[d + i];
+        if (!(half[i] > 0)) { *err = "box half-widths must be > 0"; return SBM_ERR_ARG; }
+      }
+      return SBM_OK;
+  }
+  *err = "unknown geometry kind";
+  return SBM_ERR_ARG;
+}
+
+double LevelSet::phi(const double* x) const {
+  switch (kind) {
+    case SBM_GEOM_BALL: {
+      double s = 0.0;
+      for (int i = 0; i < dim; ++i) s = s + (x[i] - c[i]) * (x[i] - c[i]);
+      return std::sqrt(s) - r;
+    }
+    case SBM_GEOM_ELLIPSOID: {
+      double s = 0.0;
+      for (int i = 0; i < dim; ++i) {
+        double y = 0.0;
+        for (int j = 0; j < dim; ++j) y = y + R[j * dim + i] * (x[j] - c[j]);
+        s = s + (y / a[i]) * (y / a[i]);
+      }
+      return s - 1.0;
+    }
+    case SBM_GEOM_TORUS: {
+      double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]);
+      return (rho - Rmaj) * (rho - Rmaj) + x[2] * x[2] - rmin * rmin;
+    }
+    case SBM_GEOM_BOX: {
+      double m = std::fabs(x[0] - c[0]) - half[0];
+      for (int i = 1; i < dim; ++i) m = std::max(m, std::fabs(x[i] - c[i]) - half[i]);
+      return m;
+    }
+  }
+  return 1.0;
+}
+
+// Ellipsoid: in the frame y = R^T (x - c) the closest point is
+// z_i = a_i^2 y_i / (a_i^2 + t) with t the root on (-a_min^2, inf) of
+// F(t) = sum_i (a_i y_i / (a_i^2 + t))^2 - 1 (D. Eberly, "Distance from a
+// point to an ellipse, an ellipsoid, or a hyperellipsoid").  F is convex and
+// decreasing there: safeguarded Newton (bisection whenever a Newton step
+// leaves the bracket).
+static bool ellipsoid_root(int d, const double* a, const double* y, double* tout) {
+  double a2[3], amin2 = 1e300, amax = 0, yn = 0, f0 = -1.0;
+  for (int i = 0; i < d; ++i) {
+    a2[i] = a[i] * a[i];
+    amin2 = std::min(amin2, a2[i]);
+    amax = std::max(amax, a[i]);
+    yn += y[i] * y[i];
+    f0 += (y[i] / a[i]) * (y[i] / a[i]);
+  }
+  yn = std::sqrt(yn);
+  if (f0 == 0.0) { *tout = 0.0; return true; }
+  double lo, hi;
+  if (f0 > 0) { lo = 0.0; hi = amax * yn; }
+  else {
+    lo = -amin2; hi = 0.0;
+    // the root exists in (-a_min^2, 0) only if some y_i on a shortest axis is non-zero
+    bool ok = false;
+    for (int i = 0; i < d; ++i) if (a2[i] == amin2 && y[i] != 0.0) ok = true;
+    if (!ok) return false;
+  }
+  double t = (f0 > 0) ? 0.0 : 0.5 * (lo + hi);
+  for (int it = 0; it < 300; ++it) {
+    double F = -1.0, dF = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double q = a[i] * y[i] / (a2[i] + t);
+      F += q * q;
+      dF += -2.0 * q * q / (a2[i] + t);
+    }
+    if (F > 0) lo = t; else hi = t;
+    if (F == 0.0) break;
+    double tn = t - F / dF;
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (std::fabs(tn - t) <= 1e-16 * std::max(1.0, std::fabs(t)) || tn == lo || tn == hi) {
+      t = tn;
+      break;
+    }
+    t = tn;
+  }
+  *tout = t;
+  return true;
+}
+
+bool LevelSet::closest(const double* x, double* out) const {
+  switch (kind) {
+    case SBM_GEOM_BALL: {
+      double v[3], s = 0.0;
+      for (int i = 0; i < dim; ++i) { v[i] = x[i] - c[i]; s += v[i] * v[i]; }
+      s = std::sqrt(s);
+      if (!(s > 0)) return false;
+      for (int i = 0; i < dim; ++i) out[i] = c[i] + r * v[i] / s;
+      return true;
+    }
+    case SBM_GEOM_TORUS: {
+      double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]);
+      if (!(rho > 0)) return false;
+      double q[3] = {Rmaj * x[0] / rho, Rmaj * x[1] / rho, 0.0};
+      double v[3], s = 0.0;
+      for (int i = 0; i < 3; ++i) { v[i] = x[i] - q[i]; s += v[i] * v[i]; }
+      s = std::sqrt(s);
+      if (!(s > 0)) return false;
+      for (int i = 0; i < 3; ++i) out[i] = q[i] + rmin * v[i] / s;
+      return true;
+    }
+    case SBM_GEOM_BOX: {
+      double v[3];
+      bool inside = true;
+      for (int i = 0; i < dim; ++i) {
+        v[i] = x[i] - c[i];
+        if (std::fabs(v[i]) > half[i]) inside = false;
+      }
+      if (!inside) {
+        for (int i = 0; i < dim; ++i) out[i] = c[i] + std::min(std::max(v[i], -half[i]), half[i]);
+        return true;
+      }
+      int kmin = 0;
+      double gmin = half[0] - std::fabs(v[0]);
+      for (int i = 1; i < dim; ++i) {
+        double gap = half[i] - std::fabs(v[i]);
+        if (gap < gmin) { gmin = gap; kmin = i; }
+      }
+      for (int i = 0; i < dim; ++i) out[i] = x[i];
+      out[kmin] = c[kmin] + (v[kmin] >= 0 ? half[kmin] : -half[kmin]);
+      return true;
+    }
+    case SBM_GEOM_ELLIPSOID: {
+      double y[3], z[3], t;
+      for (int i = 0; i < dim; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < dim; ++j) s += R[j * dim + i] * (x[j] - c[j]);
+        y[i] = s;
+      }
+      if (!ellipsoid_root(dim, a, y, &t)) return false;
+      for (int i = 0; i < dim; ++i) z[i] = a[i] * a[i] * y[i] / (a[i] * a[i] + t);
+      for (int i = 0; i < dim; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < dim; ++j) s += R[i * dim + j] * z[j];
+        out[i] = c[i] + s;
+      }
+      return true;
+    }
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Mesh, faces, numbering
+// ---------------------------------------------------------------------------
+
+int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) {
+  HostProblem& P = *hp;
+  P.desc = desc;
+  const int d = desc.dim, p = desc.degree, N = desc.cells_per_side;
+  if (d != 2 && d != 3) { *err = "dim must be 2 or 3"; return SBM_ERR_ARG; }
+  if (p < 1 || p > 6) { *err = "degree must be in 1..6"; return SBM_ERR_UNSUPPORTED; }
+  if (N < 1 || N > 4096) { *err = "cells_per_side must be in 1..4096"; return SBM_ERR_ARG; }
+  if (!(desc.pen_shift > 0)) { *err = "pen_shift must be > 0"; return SBM_ERR_ARG; }
+  if (desc.dg && !(desc.pen_interior > 0)) { *err = "pen_interior must be > 0"; return SBM_ERR_ARG; }
+  int st = P.ls.init(desc.geom_kind, d, desc.geom, err);
+  if (st != SBM_OK) return st;
+  P.d = d; P.p = p; P.n = p + 1; P.N = N;
+  P.nd = 1; P.L = 1;
+  for (int i = 0; i < d; ++i) P.nd *= P.n;
+  P.L = P.nd / P.n;
+  P.h = 2.0 / N;
+  if (desc.dg) {
+    P.sigma = desc.pen_shift * (p + 1.0) * (p + 1.0) / P.h;
+    P.sigma_f = desc.pen_interior * (p + 1.0) * (p + 1.0) / P.h;
+  } else {
+    P.sigma = desc.pen_shift * p * p / P.h;
+    P.sigma_f = 0.0;
+  }
+  build_tables(p, &P.tab);
+  const double h = P.h;
+
+  // active cells: phi(centre) < 0, centre = -1 + h (i + 1/2)
+  int64_t nbg = 1;
+  for (int i = 0; i < d; ++i) nbg *= N;
+  P.bg_to_cell.assign(nbg, -1);
+  P.cells.clear();
+  P.cell_bg.clear();
+  for (int64_t b = 0; b < nbg; ++b) {
+    int idx[3] = {0, 0, 0};
+    int64_t r = b;
+    double xc[3];
+    for (int i = 0; i < d; ++i) {
+      idx[i] = (int)(r % N);
+      r /= N;
+      xc[i] = -1.0 + h * (idx[i] + 0.5);
+    }
+    if (P.ls.phi(xc) < 0.0) {
+      P.bg_to_cell[b] = (int32_t)P.cell_bg.size();
+      P.cell_bg.push_back(b);
+      for (int i = 0; i < d; ++i) P.cells.push_back(idx[i]);
+    }
+  }
+  const int64_t Nc = (int64_t)P.cell_bg.size();
+  if (Nc == 0) { *err = "no active cell"; return SBM_ERR_EMPTY_DOMAIN; }
+
+  // faces
+  int64_t stride[3] = {1, N, (int64_t)N * N};
+  P.sfaces.clear();
+  P.ifaces.clear();
+  for (int64_t c = 0; c < Nc; ++c) {
+    for (int k = 0; k < d; ++k)
+      for (int s = 0; s < 2; ++s) {
+        int j = P.cells[c * d + k] + (s ? 1 : -1);
+        int32_t nb = -1;
+        if (j >= 0 && j < N) nb = P.bg_to_cell[P.cell_bg[c] + (s ? 1 : -1) * stride[k]];
+        if (nb < 0) {
+          P.sfaces.push_back((int32_t)c); P.sfaces.push_back(k); P.sfaces.push_back(s);
+        } else if (s == 1) {
+          P.ifaces.push_back((int32_t)c); P.ifaces.push_back(k); P.ifaces.push_back(nb);
+        }
+      }
+  }
+
+  // surrogate face Gauss points, closest points, reference coordinates
+  const int64_t F = (int64_t)P.sfaces.size() / 3;
+  const int Q = P.L, n = P.n;
+  P.face_x.assign(F * Q * d, 0.0);
+  P.face_xi.assign(F * Q * d, 0.0);
+  for (int64_t f = 0; f < F; ++f) {
+    const int c = P.sfaces[3 * f], k = P.sfaces[3 * f + 1], s = P.sfaces[3 * f + 2];
+    int tang[2], nt = 0;
+    for (int l = 0; l < d; ++l) if (l != k) tang[nt++] = l;
+    double lo[3];
+    for (int l = 0; l < d; ++l) lo[l] = -1.0 + h * (double)P.cells[c * d + l];
+    for (int q = 0; q < Q; ++q) {
+      int qa = q % n, qb = q / n;
+      double xi[3], xt[3], xq[3];
+      xi[k] = (double)s;
+      xi[tang[0]] = P.tab.gpts[qa];
+      if (d == 3) xi[tang[1]] = P.tab.gpts[qb];
+      for (int l = 0; l < d; ++l) xt[l] = lo[l] + h * xi[l];
+      if (!P.ls.closest(xt, xq)) {
+        *err = "closest-point projection undefined for a surrogate quadrature point";
+        return SBM_ERR_GEOMETRY;
+      }
+      for (int l = 0; l < d; ++l) {
+        P.face_x[(f * Q + q) * d + l] = xq[l];
+        P.face_xi[(f * Q + q) * d + l] = (xq[l] - lo[l]) / h;
+      }
+    }
+  }
+
+  // numbering
+  if (desc.dg) {
+    P.n_dofs = Nc * P.nd;
+    if (P.n_dofs >= (int64_t(1) << 31)) { *err = "too many DoFs for int32 indices"; return SBM_ERR_ARG; }
+    P.lines.clear();
+  } else {
+    const int64_t M = (int64_t)p * N + 1;
+    int64_t nlat = 1;
+    for (int i = 0; i < d; ++i) nlat *= M;
+    std::vector<int32_t> idx(nlat, 0);
+    const int64_t ms[3] = {1, M, M * M};
+    for (int64_t c = 0; c < Nc; ++c) {
+      int64_t base = 0;
+      for (int l = 0; l < d; ++l) base += (int64_t)p * P.cells[c * d + l] * ms[l];
+      for (int r = 0; r < P.nd; ++r) {
+        int64_t off = 0, rr = r;
+        for (int l = 0; l < d; ++l) { off += (rr % n) * ms[l]; rr /= n; }
+        idx[base + off] = 1;
+      }
+    }
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < nlat; ++i) {
+      if (idx[i]) {
+        if (cnt >= (int64_t(1) << 31) - 1) { *err = "too many DoFs for int32 indices"; return SBM_ERR_ARG; }
+        idx[i] = (int32_t)cnt++;
+      } else {
+        idx[i] = -1;
+      }
+    }
+    P.n_dofs = cnt;
+    P.lines.assign(Nc * P.L, 0);
+    for (int64_t c = 0; c < Nc; ++c) {
+      int64_t base = 0;
+      for (int l = 0; l < d; ++l) base += (int64_t)p * P.cells[c * d + l] * ms[l];
+      for (int line = 0; line < P.L; ++line) {
+        int64_t off = (d == 2) ? line * ms[1] : (line % n) * ms[1] + (line / n) * ms[2];
+        P.lines[c * P.L + line] = idx[base + off];
+      }
+    }
+  }
+  return SBM_OK;
+}
+
+}  // namespace sbm

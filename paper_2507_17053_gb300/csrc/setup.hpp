@@ -1,0 +1,81 @@
+// Host-side (FP64) set-up of an SBM problem: 1D tables, level sets and closest
+// points, active cells, surrogate faces, DoF numbering and the per-face data
+// the kernels read.  Plain C++; no CUDA in this file's interface.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sbm.h"
+
+namespace sbm {
+
+constexpr int kMaxN = 7;   // n = p + 1 <= 7 (degrees 1..6)
+
+// 1D tables on the reference interval [0,1] for n = p+1 GLL nodes and n Gauss
+// points (Section 3.1: tensor-product basis and Gauss quadrature).
+struct Tables1D {
+  int n = 0;
+  double nodes[kMaxN] = {};        // GLL nodes x_j
+  double gpts[kMaxN] = {};         // Gauss points g_q
+  double gwts[kMaxN] = {};         // Gauss weights w_q
+  double S[kMaxN][kMaxN] = {};     // S[q][j] = phi_j(g_q)       (nodes -> Gauss points)
+  double Dg[kMaxN][kMaxN] = {};    // Dg[q][j] = phi_j'(g_q)
+  double M[kMaxN][kMaxN] = {};     // 1D mass      sum_q w_q phi_i(g_q) phi_j(g_q)
+  double K[kMaxN][kMaxN] = {};     // 1D stiffness sum_q w_q phi_i'(g_q) phi_j'(g_q)
+  double D0[kMaxN] = {};           // phi_j'(0)
+  double D1[kMaxN] = {};           // phi_j'(1)
+};
+
+// GLL nodes by Newton on (1-t^2) P_p'(t) with the Legendre recurrence, Gauss
+// points by Newton on P_n(t); Lagrange values by the barycentric formula.
+void build_tables(int p, Tables1D* t);
+void lagrange_values(const Tables1D& t, double x, double* phi);     // phi[j], any real x
+void lagrange_derivs(const Tables1D& t, double x, double* dphi);
+
+struct LevelSet {
+  int kind = 0, dim = 0;
+  double c[3] = {0, 0, 0};
+  double r = 0;
+  double a[3] = {1, 1, 1};
+  double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  double Rmaj = 0, rmin = 0;
+  double half[3] = {0, 0, 0};
+
+  int init(int kind, int dim, const double* g, std::string* err);
+  double phi(const double* x) const;
+  // closest point on Gamma; returns false if the projection is undefined
+  bool closest(const double* x, double* out) const;
+};
+
+struct HostProblem {
+  sbm_desc desc{};
+  int d = 0, p = 0, n = 0, N = 0;
+  int nd = 0;        // n^d
+  int L = 0;         // n^(d-1) lines per cell / points per face
+  double h = 0, sigma = 0, sigma_f = 0;
+  Tables1D tab;
+  LevelSet ls;
+
+  // active cells, lexicographic (axis 0 fastest)
+  std::vector<int32_t> cells;       // [Nc * d]
+  std::vector<int64_t> cell_bg;     // background linear index
+  std::vector<int32_t> bg_to_cell;  // [N^d] -> rank or -1
+  // surrogate faces (cell rank, k, s), by cell, then k, then s
+  std::vector<int32_t> sfaces;      // [F * 3]
+  std::vector<double> face_x;       // [F * L * d] closest points
+  std::vector<double> face_xi;      // [F * L * d] reference coordinates in the cell's frame
+  // DG interior faces (K1 rank, k, K2 rank), K2 = K1 + e_k
+  std::vector<int32_t> ifaces;
+
+  int64_t n_dofs = 0;
+  // CG: per active cell, the global index of local node (0, j1, j2) for each
+  // of the L x-lines (j1 + n j2); the n nodes of an x-line are consecutive.
+  std::vector<int32_t> lines;       // [Nc * L]
+};
+
+// Build everything on the host.  Returns SBM_OK or an error code with *err set.
+int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err);
+
+}  // namespace sbm

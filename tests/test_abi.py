@@ -1,0 +1,97 @@
+"""The C-ABI library loads, exports every declared symbol, and checks its
+arguments on the host (no GPU needed)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2507_17053_gb300 as G
+import synthetic as S
+from oracle.operator import Problem as OracleProblem
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return G.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = G.header_functions()
+    assert "sbm_apply_f64" in names and "sbm_create" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_error_strings(lib):
+    for code in range(10):
+        assert lib.sbm_error_string(code)
+    assert lib.sbm_error_string(12345) == b"unknown status"
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(dim=4), "SBM_ERR_ARG"),
+    (dict(degree=0), "SBM_ERR_UNSUPPORTED"),
+    (dict(degree=7), "SBM_ERR_UNSUPPORTED"),
+    (dict(cells=0), "SBM_ERR_ARG"),
+    (dict(kind=9), "SBM_ERR_ARG"),
+    (dict(geom=(0.0, 0.0, -1.0)), "SBM_ERR_ARG"),
+    (dict(geom=(5.0, 5.0, 0.1)), "SBM_ERR_EMPTY_DOMAIN"),
+    (dict(pen_shift=0.0), "SBM_ERR_ARG"),
+])
+def test_create_rejects_bad_descriptions(bad, code):
+    args = dict(dim=2, degree=2, cells=8, kind="ball", geom=(0.0, 0.0, 0.7))
+    args.update(bad)
+    with pytest.raises(G.SbmError) as e:
+        G.sbm_create(G.make_desc(**args))
+    assert G.STATUS[e.value.status] == code
+
+
+def test_null_arguments(lib):
+    assert lib.sbm_create(None, None) == 1
+    out = ctypes.c_void_p()
+    assert lib.sbm_create(None, ctypes.byref(out)) == 1 and out.value is None
+    assert lib.sbm_apply_f64(None, None, None, None) == 1
+    assert lib.sbm_sizes(None, None, None, None, None) == 1
+    lib.sbm_destroy(None)   # no-op
+
+
+def test_apply_before_device_setup_is_a_state_error():
+    P = G.Problem(2, 2, 8, "ball", (0.0, 0.0, 0.7), device=False)
+    with pytest.raises(G.SbmError) as e:
+        G.sbm_apply_f64(P.handle, 16, 32, 0)   # fake non-null addresses: never touched
+    assert G.STATUS[e.value.status] == "SBM_ERR_STATE"
+    with pytest.raises(G.SbmError) as e:
+        G.sbm_apply_f64(P.handle, 16, 16, 0)
+    assert G.STATUS[e.value.status] == "SBM_ERR_ARG"
+
+
+def _compare_geometry(w):
+    O = OracleProblem.from_workload(w)
+    P = G.Problem.from_workload(w, device=False)
+    cells, sfaces, fx = P.geometry()
+    assert P.n_cells == len(O.mesh.cells)
+    assert P.n_dofs == O.n_dofs
+    np.testing.assert_array_equal(cells, O.mesh.cells)          # bit-exact
+    np.testing.assert_array_equal(sfaces, O.mesh.sfaces)
+    if O.dg:
+        assert P.n_ifaces == len(O.mesh.ifaces)
+    # closest points: two independent projections (closed forms / bisection vs Newton)
+    np.testing.assert_allclose(fx, O.mesh.face_x, rtol=0, atol=2e-14)
+
+
+SMALL = [
+    S.DISK_2D_Q2,
+    S.SPHERE_3D_Q4.resized(20),
+    S.ELLIPSOID_3D_Q6.resized(14),
+    S.TORUS_3D_DG_Q3.resized(18),
+] + S.batched_ellipsoids(nprob=4, n_range=(8, 14))
+
+
+@pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
+def test_host_geometry_matches_oracle(w):
+    _compare_geometry(w)
+
+
+@pytest.mark.slow
+def test_host_geometry_matches_oracle_full_sphere():
+    _compare_geometry(S.SPHERE_3D_Q4)

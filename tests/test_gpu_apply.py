@@ -1,0 +1,106 @@
+"""Parity of the CUDA FP64 apply (through the C ABI) with the CPU oracle.
+
+Bar: ||y_gpu - y_oracle||_inf <= 1e-12 ||y_oracle||_inf on the same seeded x;
+repeated applies are bitwise equal (atomic-free scatter)."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2507_17053_gb300 as G
+import synthetic as S
+from oracle.operator import Problem as OracleProblem
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    G.lib()
+
+
+def _pair(w):
+    return OracleProblem.from_workload(w), G.Problem.from_workload(w)
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _check_full(w, seed=None, dist=None):
+    O, P = _pair(w)
+    assert P.n_dofs == O.n_dofs
+    x = S.random_vector(w.seed if seed is None else seed, O.n_dofs, dist or w.dist)
+    xd = torch.from_numpy(x).cuda()
+    y = P.apply_f64(xd)
+    y2 = P.apply_f64(xd)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y2), "repeated apply is not bitwise identical"
+    ref = O.apply(x)
+    err = _rel(y.cpu().numpy(), ref)
+    assert err <= TOL, err
+    return P, O, x, y
+
+
+CG_CASES = [
+    S.DISK_2D_Q2,                                   # the 2D workload at full size
+    S.SPHERE_3D_Q4.resized(14),
+    S.SPHERE_3D_Q4.resized(9),
+    S.ELLIPSOID_3D_Q6.resized(10),
+] + [S.DISK_2D_Q2.resized(11, degree=p) for p in range(1, 7)] \
+  + [S.SPHERE_3D_Q4.resized(7, degree=p) for p in range(1, 7)] \
+  + S.batched_ellipsoids(nprob=5, n_range=(6, 12))
+
+
+@pytest.mark.parametrize("w", CG_CASES, ids=lambda w: w.name)
+def test_cg_apply_matches_oracle(w):
+    _check_full(w)
+
+
+def test_single_active_cell():
+    # a tiny ball around one cell centre: one active cell, 2d surrogate faces
+    for d in (2, 3):
+        c = (-1.0 + 0.25 * 3.5,) * d
+        w = S._wl("single", d, 3, 8, S.ball(d, c, 0.05))
+        P, O, _, _ = _check_full(w)
+        assert P.n_cells == 1 and P.n_sfaces == 2 * d
+
+
+def test_whole_box_and_one_cell_mesh():
+    for d in (2, 3):
+        # every cell active; the surrogate boundary is the box boundary, d = 0
+        _check_full(S._wl("box", d, 2, 5, S.box((0.0,) * d, (1.5,) * d)))
+        _check_full(S._wl("one", d, 4, 1, S.ball(d, (0.0,) * d, 0.9)))
+
+
+def test_host_entry_point_equals_device_apply():
+    w = S.SPHERE_3D_Q4.resized(10)
+    P = G.Problem.from_workload(w)
+    x = S.random_vector(3, P.n_dofs, "uniform")
+    yd = P.apply_f64(torch.from_numpy(x).cuda()).cpu().numpy()
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty(P.n_dofs, dtype=torch.float64).pin_memory()
+    P.apply_f64_host(xh, yh)
+    np.testing.assert_array_equal(yh.numpy(), yd)
+
+
+def _sample_rows(O, rng, nrand=10000, nface_cells=200):
+    rows = rng.choice(O.n_dofs, size=min(nrand, O.n_dofs), replace=False)
+    fc = np.unique(O.mesh.sfaces[:, 0])
+    pick = rng.choice(fc, size=min(nface_cells, len(fc)), replace=False)
+    rows = np.unique(np.concatenate([rows, O.dofmap[pick].ravel()]))
+    return rows
+
+
+@pytest.mark.parametrize("w", [S.SPHERE_3D_Q4, S.ELLIPSOID_3D_Q6], ids=lambda w: w.name)
+def test_full_size_sampled_rows(w):
+    """Full-size workload, launched as the benchmark launches it; checked on
+    10^4 random rows plus every row of 200 sampled surrogate-face cells."""
+    O, P = _pair(w)
+    x = S.random_vector(w.seed, O.n_dofs, w.dist)
+    y = P.apply_f64(torch.from_numpy(x).cuda()).cpu().numpy()
+    rows = _sample_rows(O, np.random.default_rng(0))
+    ref = O.apply_rows(x, rows)
+    scale = np.abs(ref).max()
+    assert np.abs(y[rows] - ref).max() <= TOL * scale
