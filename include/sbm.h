@@ -142,11 +142,81 @@ int sbm_apply_f64(sbm_problem* prob, const double* x, double* y, void* stream);
  */
 int sbm_apply_f64_host(sbm_problem* prob, const double* x_host, double* y_host, void* stream);
 
+/* Face arithmetic of the FP32 apply: FP32 CUDA cores, or the shifted point
+ * evaluation on tensor cores in TF32 / BF16 with FP32 accumulation. */
+enum { SBM_FACE_FP32 = 0, SBM_FACE_TF32 = 1, SBM_FACE_BF16 = 2 };
+
+/*
+ * Matrix-free apply in FP32 (same operator and algorithm as sbm_apply_f64;
+ * the 1D tables and the per-face shifted-point tables rounded to FP32):
+ * y = A x with x, y device arrays of n_dofs floats.  face_mode selects the
+ * face arithmetic (SBM_FACE_*).  Asynchronous on stream.
+ * Errors: SBM_ERR_ARG, SBM_ERR_STATE, SBM_ERR_UNSUPPORTED (face mode not
+ * available), SBM_ERR_CUDA.
+ */
+int sbm_apply_f32(sbm_problem* prob, const float* x, float* y, int face_mode, void* stream);
+
 /*
  * The diagonal of A (FP64, device array of n_dofs), for Jacobi scaling.
  * Asynchronous on stream.
  */
 int sbm_diagonal(sbm_problem* prob, double* diag, void* stream);
+
+/* ---- solvers (the paper gives none; these drive the operator) ----------- */
+enum { SBM_PRECOND_NONE = 0, SBM_PRECOND_JACOBI = 1 };
+
+/*
+ * Conjugate gradients on A x = b in FP64 (optionally Jacobi-preconditioned),
+ * all vectors on the device, CUDA-graph-captured iterations, deterministic
+ * reductions.  x (device, n_dofs) holds the initial guess on entry and the
+ * last iterate on exit.  Stops when the true relative residual
+ * |b - A x| / |b| <= rtol (checked after the recursive residual reaches it,
+ * restarting if the two disagree), or after maxit iterations.  CG assumes a
+ * symmetric positive definite A; the SBM operator is not symmetric when the
+ * shift is non-zero, and CG can diverge on it: that ends the solve with
+ * SBM_ERR_NOT_CONVERGED.  *iters and *relres (may be NULL) receive the
+ * iteration count and the final true relative residual in every case.
+ * Synchronous: returns after the solve (work runs on stream).
+ * Errors: SBM_ERR_ARG, SBM_ERR_STATE, SBM_ERR_NOT_CONVERGED, SBM_ERR_CUDA.
+ */
+int sbm_cg(sbm_problem* prob, const double* b, double* x, double rtol, int maxit, int precond,
+           int* iters, double* relres, void* stream);
+
+/*
+ * Restarted GMRES(restart) on A x = b in FP64 (no preconditioner; CGS2
+ * orthogonalisation), the nonsymmetric counterpart of sbm_cg with the same
+ * conventions; maxit counts operator applications inside Arnoldi steps.
+ * Device workspace: (restart + 1) vectors of n_dofs doubles, allocated and
+ * freed by the call.
+ */
+int sbm_gmres(sbm_problem* prob, const double* b, double* x, double rtol, int maxit, int restart,
+              int* iters, double* relres, void* stream);
+
+/*
+ * Mixed precision: FP64 iterative refinement (defect correction).  Each
+ * outer step computes r = b - A x with the FP64 apply, then solves
+ * A c = r/|r| approximately with FP32 GMRES(restart) on the FP32 apply
+ * (relative tolerance inner_rtol, at most inner_maxit iterations), and
+ * updates x += |r| c in FP64.  Stops when |b - A x|/|b| <= rtol (FP64) or
+ * after max_outer steps.  *iters = FP32 inner iterations in total,
+ * *outer = outer steps; same conventions otherwise.
+ */
+int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int max_outer,
+                 int restart, double inner_rtol, int inner_maxit, int face_mode, int* iters,
+                 int* outer, double* relres, void* stream);
+
+/*
+ * Manufactured data (host, FP64; no CUDA call).  manufactured = 0:
+ * u = prod_i sin(pi x_i), f = d pi^2 u; manufactured = 1 (2D only):
+ * u = 2 cos(x_1) sin(x_2), f = 2 u (the paper's Appendix A solution).
+ * sbm_rhs writes the right-hand side of the weak form (Section 2.1)
+ *   b_i = int f v_i - int_F (grad v_i . n~) g(x_q) + int_F sigma g(x_q) v_i
+ * with g = u at the true-boundary points x_q; sbm_interpolate writes the
+ * nodal interpolant of u.  Both fill host arrays of n_dofs doubles.
+ * Errors: SBM_ERR_ARG (NULL, unknown id).
+ */
+int sbm_rhs(const sbm_problem* prob, int manufactured, double* b_host);
+int sbm_interpolate(const sbm_problem* prob, int manufactured, double* u_host);
 
 /*
  * Kernel timing (diagnostics).  While enabled, every apply records a CUDA

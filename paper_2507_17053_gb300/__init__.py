@@ -58,6 +58,25 @@ _SIGS = {
     "sbm_apply_f64": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "sbm_apply_f64_host": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "sbm_diagonal": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "sbm_apply_f32": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]),
+    "sbm_cg": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                        ctypes.POINTER(ctypes.c_int),
+                                                        ctypes.POINTER(ctypes.c_double),
+                                                        ctypes.c_void_p]),
+    "sbm_gmres": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int,
+                                                           ctypes.c_int,
+                                                           ctypes.POINTER(ctypes.c_int),
+                                                           ctypes.POINTER(ctypes.c_double),
+                                                           ctypes.c_void_p]),
+    "sbm_solve_ir": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int,
+                                                              ctypes.c_int, ctypes.c_double,
+                                                              ctypes.c_int, ctypes.c_int,
+                                                              ctypes.POINTER(ctypes.c_int),
+                                                              ctypes.POINTER(ctypes.c_int),
+                                                              ctypes.POINTER(ctypes.c_double),
+                                                              ctypes.c_void_p]),
+    "sbm_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sbm_interpolate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sbm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), _c_i64p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -169,6 +188,56 @@ def sbm_diagonal(handle: int, diag, stream=None) -> None:
     _check(lib().sbm_diagonal(handle, _ptr(diag), _stream(stream)), "sbm_diagonal")
 
 
+FACE_MODE = {"fp32": 0, "tf32": 1, "bf16": 2}
+PRECOND = {"none": 0, "jacobi": 1}
+
+
+def sbm_apply_f32(handle: int, x, y, face_mode=0, stream=None) -> None:
+    _check(lib().sbm_apply_f32(handle, _ptr(x), _ptr(y), int(face_mode), _stream(stream)),
+           "sbm_apply_f32")
+
+
+def _solve_call(name, status, it, rr, raise_not_converged):
+    if status == 5 and not raise_not_converged:
+        return it.value, rr.value, False
+    _check(status, name)
+    return it.value, rr.value, True
+
+
+def sbm_cg(handle: int, b, x, rtol=1e-10, maxit=10000, precond=0, stream=None,
+           raise_not_converged=False):
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    st = lib().sbm_cg(handle, _ptr(b), _ptr(x), rtol, maxit, int(precond), ctypes.byref(it),
+                      ctypes.byref(rr), _stream(stream))
+    return _solve_call("sbm_cg", st, it, rr, raise_not_converged)
+
+
+def sbm_gmres(handle: int, b, x, rtol=1e-10, maxit=10000, restart=100, stream=None,
+              raise_not_converged=False):
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    st = lib().sbm_gmres(handle, _ptr(b), _ptr(x), rtol, maxit, restart, ctypes.byref(it),
+                         ctypes.byref(rr), _stream(stream))
+    return _solve_call("sbm_gmres", st, it, rr, raise_not_converged)
+
+
+def sbm_solve_ir(handle: int, b, x, rtol=1e-10, max_outer=30, restart=100, inner_rtol=1e-4,
+                 inner_maxit=2000, face_mode=0, stream=None, raise_not_converged=False):
+    it, outer, rr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    st = lib().sbm_solve_ir(handle, _ptr(b), _ptr(x), rtol, max_outer, restart, inner_rtol,
+                            inner_maxit, int(face_mode), ctypes.byref(it), ctypes.byref(outer),
+                            ctypes.byref(rr), _stream(stream))
+    res = _solve_call("sbm_solve_ir", st, it, rr, raise_not_converged)
+    return res + (outer.value,)
+
+
+def sbm_rhs(handle: int, manufactured: int, b_host) -> None:
+    _check(lib().sbm_rhs(handle, int(manufactured), _ptr(b_host)), "sbm_rhs")
+
+
+def sbm_interpolate(handle: int, manufactured: int, u_host) -> None:
+    _check(lib().sbm_interpolate(handle, int(manufactured), _ptr(u_host)), "sbm_interpolate")
+
+
 def sbm_profile_enable(handle: int, on: bool) -> None:
     _check(lib().sbm_profile_enable(handle, int(bool(on))), "sbm_profile_enable")
 
@@ -226,6 +295,35 @@ class Problem:
         _expect(x, torch.float64, self.n_dofs)
         _expect(y, torch.float64, self.n_dofs)
         sbm_apply_f64(self.handle, x, y, stream)
+        return y
+
+    def rhs(self, manufactured=0):
+        import numpy as np
+        b = np.zeros(self.n_dofs)
+        sbm_rhs(self.handle, manufactured, b)
+        return b
+
+    def interpolate(self, manufactured=0):
+        import numpy as np
+        u = np.zeros(self.n_dofs)
+        sbm_interpolate(self.handle, manufactured, u)
+        return u
+
+    def diagonal(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n_dofs, dtype=torch.float64, device="cuda")
+        _expect(out, torch.float64, self.n_dofs)
+        sbm_diagonal(self.handle, out, stream)
+        return out
+
+    def apply_f32(self, x, y=None, face_mode=0, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _expect(x, torch.float32, self.n_dofs)
+        _expect(y, torch.float32, self.n_dofs)
+        sbm_apply_f32(self.handle, x, y, FACE_MODE.get(face_mode, face_mode), stream)
         return y
 
     def apply_f64_host(self, x_host, y_host=None, stream=None):

@@ -5,6 +5,7 @@
 #include <string>
 
 #include "internal.hpp"
+#include "krylov.hpp"
 
 namespace sbm {
 
@@ -93,6 +94,7 @@ static void free_device(DeviceData* dd) {
   cudaFree(dd->face_start);
   cudaFree(dd->face_kind);
   cudaFree(dd->face_phi);
+  cudaFree(dd->face_phi32);
   cudaFree(dd->nbr);
   cudaFree(dd->stage_x);
   cudaFree(dd->stage_y);
@@ -156,12 +158,30 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   }
   fstart[Nc] = (int32_t)fkind.size();
 
+  std::vector<int32_t> nbr;
+  if (hp.desc.dg) {
+    nbr.assign(Nc * 2 * d, -1);
+    const int N = hp.N;
+    int64_t stride[3] = {1, N, (int64_t)N * N};
+    for (int64_t c = 0; c < Nc; ++c)
+      for (int k = 0; k < d; ++k)
+        for (int s = 0; s < 2; ++s) {
+          const int j = hp.cells[c * d + k] + (s ? 1 : -1);
+          if (j < 0 || j >= N) continue;
+          nbr[c * 2 * d + 2 * k + s] = hp.bg_to_cell[hp.cell_bg[c] + (s ? 1 : -1) * stride[k]];
+        }
+  }
   cudaError_t e;
+  if ((e = upload(&dd->nbr, nbr.data(), nbr.size())) != cudaSuccess) goto err;
   if ((e = upload(&dd->lines, lines_o.data(), lines_o.size())) != cudaSuccess) goto err;
   if ((e = upload(&dd->cell_rank, dd->order.data(), dd->order.size())) != cudaSuccess) goto err;
   if ((e = upload(&dd->face_start, fstart.data(), fstart.size())) != cudaSuccess) goto err;
   if ((e = upload(&dd->face_kind, fkind.data(), fkind.size())) != cudaSuccess) goto err;
   if ((e = upload(&dd->face_phi, fphi.data(), fphi.size())) != cudaSuccess) goto err;
+  {
+    std::vector<float> f32(fphi.begin(), fphi.end());
+    if ((e = upload(&dd->face_phi32, f32.data(), f32.size())) != cudaSuccess) goto err;
+  }
   return SBM_OK;
 err:
   free_device(dd);
@@ -260,8 +280,9 @@ int sbm_apply_f64(sbm_problem* prob, const double* x, double* y, void* stream) {
   if (!prob || !x || !y) return fail(SBM_ERR_ARG, "NULL argument");
   if (x == y) return fail(SBM_ERR_ARG, "x and y must not overlap");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
-  if (prob->hp.desc.dg) return fail(SBM_ERR_UNSUPPORTED, "DG apply not built");
-  cudaError_t e = launch_cg_apply_f64(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof);
+  cudaError_t e = prob->hp.desc.dg
+      ? launch_dg_apply<double>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof)
+      : launch_cg_apply<double>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof);
   if (e != cudaSuccess) return cuda_fail(e, "sbm_apply_f64");
   return SBM_OK;
 }
@@ -288,9 +309,123 @@ int sbm_apply_f64_host(sbm_problem* prob, const double* x_host, double* y_host, 
 }
 
 int sbm_diagonal(sbm_problem* prob, double* diag, void* stream) {
-  (void)stream;
   if (!prob || !diag) return fail(SBM_ERR_ARG, "NULL argument");
-  return fail(SBM_ERR_UNSUPPORTED, "diagonal not built yet");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  cudaError_t e = launch_diag_f64(prob->hp, prob->dd, diag, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sbm_diagonal");
+  return SBM_OK;
+}
+
+int sbm_apply_f32(sbm_problem* prob, const float* x, float* y, int face_mode, void* stream) {
+  if (!prob || !x || !y) return fail(SBM_ERR_ARG, "NULL argument");
+  if (x == y) return fail(SBM_ERR_ARG, "x and y must not overlap");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (face_mode != SBM_FACE_FP32) return fail(SBM_ERR_UNSUPPORTED, "face mode not built");
+  cudaError_t e = prob->hp.desc.dg
+      ? launch_dg_apply<float>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof)
+      : launch_cg_apply<float>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof);
+  if (e != cudaSuccess) return cuda_fail(e, "sbm_apply_f32");
+  return SBM_OK;
+}
+
+static ApplyFn<double> apply64_fn(sbm_problem* prob) {
+  return [prob](const double* x, double* y, cudaStream_t st) {
+    return prob->hp.desc.dg ? launch_dg_apply<double>(prob->hp, prob->dd, x, y, st, nullptr)
+                            : launch_cg_apply<double>(prob->hp, prob->dd, x, y, st, nullptr);
+  };
+}
+
+static ApplyFn<float> apply32_fn(sbm_problem* prob) {
+  return [prob](const float* x, float* y, cudaStream_t st) {
+    return prob->hp.desc.dg ? launch_dg_apply<float>(prob->hp, prob->dd, x, y, st, nullptr)
+                            : launch_cg_apply<float>(prob->hp, prob->dd, x, y, st, nullptr);
+  };
+}
+
+static int solve_result(SolveStatus s, const SolveInfo& info, int* iters, double* relres,
+                        const char* what) {
+  if (iters) *iters = info.iters;
+  if (relres) *relres = info.relres;
+  if (s.status == SBM_ERR_CUDA) return cuda_fail(s.cuda, what);
+  if (s.status == SBM_ERR_NOT_CONVERGED)
+    return fail(SBM_ERR_NOT_CONVERGED, std::string(what) + ": relative residual " +
+                                           std::to_string(info.relres) + " after " +
+                                           std::to_string(info.iters) + " iterations");
+  return s.status;
+}
+
+int sbm_cg(sbm_problem* prob, const double* b, double* x, double rtol, int maxit, int precond,
+           int* iters, double* relres, void* stream) {
+  if (!prob || !b || !x || b == x) return fail(SBM_ERR_ARG, "bad vector argument");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (!(rtol > 0) || maxit < 1 || (precond != SBM_PRECOND_NONE && precond != SBM_PRECOND_JACOBI))
+    return fail(SBM_ERR_ARG, "bad solver parameter");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace ws;
+  double* diag = nullptr;
+  SolveInfo info;
+  SolveStatus s{SBM_OK, cudaSuccess};
+  if (precond == SBM_PRECOND_JACOBI) {
+    cudaError_t e = ws.alloc((void**)&diag, prob->hp.n_dofs * sizeof(double));
+    if (e == cudaSuccess) e = launch_diag_f64(prob->hp, prob->dd, diag, st);
+    if (e != cudaSuccess) s = {SBM_ERR_CUDA, e};
+  }
+  if (s.status == SBM_OK)
+    s = solve_cg(apply64_fn(prob), prob->hp.n_dofs, b, x, diag, rtol, maxit, st, ws, &info);
+  cudaStreamSynchronize(st);
+  ws.release();
+  return solve_result(s, info, iters, relres, "sbm_cg");
+}
+
+int sbm_gmres(sbm_problem* prob, const double* b, double* x, double rtol, int maxit, int restart,
+              int* iters, double* relres, void* stream) {
+  if (!prob || !b || !x || b == x) return fail(SBM_ERR_ARG, "bad vector argument");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (!(rtol > 0) || maxit < 1 || restart < 1 || restart > 1000)
+    return fail(SBM_ERR_ARG, "bad solver parameter");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace ws;
+  SolveInfo info;
+  ApplyFn<double> ap = apply64_fn(prob);
+  SolveStatus s = solve_gmres<double, double>(ap, prob->hp.n_dofs, b, x, rtol, maxit, restart, st,
+                                              ws, &info, &ap);
+  cudaStreamSynchronize(st);
+  ws.release();
+  return solve_result(s, info, iters, relres, "sbm_gmres");
+}
+
+int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int max_outer,
+                 int restart, double inner_rtol, int inner_maxit, int face_mode, int* iters,
+                 int* outer, double* relres, void* stream) {
+  if (!prob || !b || !x || b == x) return fail(SBM_ERR_ARG, "bad vector argument");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (!(rtol > 0) || max_outer < 0 || restart < 1 || restart > 1000 || !(inner_rtol > 0) ||
+      inner_maxit < 1)
+    return fail(SBM_ERR_ARG, "bad solver parameter");
+  if (face_mode != SBM_FACE_FP32) return fail(SBM_ERR_UNSUPPORTED, "face mode not built");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace ws;
+  SolveInfo info;
+  SolveStatus s = solve_ir(apply64_fn(prob), apply32_fn(prob), prob->hp.n_dofs, b, x, rtol,
+                           max_outer, restart, inner_rtol, inner_maxit, st, ws, &info);
+  cudaStreamSynchronize(st);
+  ws.release();
+  if (outer) *outer = info.restarts;
+  return solve_result(s, info, iters, relres, "sbm_solve_ir");
+}
+
+int sbm_rhs(const sbm_problem* prob, int manufactured, double* b_host) {
+  if (!prob || !b_host) return fail(SBM_ERR_ARG, "NULL argument");
+  if (!manufactured_ok(manufactured, prob->hp.d)) return fail(SBM_ERR_ARG, "unknown solution id");
+  build_rhs(prob->hp, manufactured, b_host);
+  return SBM_OK;
+}
+
+int sbm_interpolate(const sbm_problem* prob, int manufactured, double* u_host) {
+  if (!prob || !u_host) return fail(SBM_ERR_ARG, "NULL argument");
+  if (!manufactured_ok(manufactured, prob->hp.d)) return fail(SBM_ERR_ARG, "unknown solution id");
+  build_interpolant(prob->hp, manufactured, u_host);
+  return SBM_OK;
 }
 
 int sbm_profile_enable(sbm_problem* prob, int on) {

@@ -1,4 +1,4 @@
-// FP64 matrix-free apply of the continuous Galerkin SBM operator on sm_103a.
+// Matrix-free apply (FP64 or FP32) of the continuous Galerkin SBM operator on sm_103a.
 //
 // One launch per cell colour (2^d colours: cells whose indices have the same
 // parity pattern share no DoF), so the scatter y += A_K x_K is a plain
@@ -34,13 +34,14 @@ CellLaunch cell_launch_shape(int d, int n) {
   return CellLaunch{d, n, cpb, cpb * L};
 }
 
+template <typename T>
 struct CgArgs {
-  const double* __restrict__ x;
-  double* __restrict__ y;
+  const T* __restrict__ x;
+  T* __restrict__ y;
   const int32_t* __restrict__ lines;       // ordered cells x L
   const int32_t* __restrict__ face_start;  // ordered cells + 1
   const int32_t* __restrict__ face_kind;
-  const double* __restrict__ face_phi;
+  const T* __restrict__ face_phi;
   int cell0;        // first ordered cell of the colour
   int nint;         // interior cells of the colour (first in the colour's range)
   int nint_tiles;   // ceil(nint / CPB)
@@ -50,19 +51,18 @@ struct CgArgs {
 
 // 3D: three phases over z-, y- and x-lines.  `X` holds ncells tiles; the x-line
 // result of line `tl` of cell `c` is returned in out[].
-template <int N>
-__device__ __forceinline__ void cell_sweeps_3d(const KTab<double>& t, const double* X, double* A,
-                                               double* E, double* B, double* G, int c, int tl,
-                                               bool act, double (&out)[N]) {
+template <typename T, int N>
+__device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, T* A, T* E, T* B,
+                                               T* G, int c, int tl, bool act, T (&out)[N]) {
   constexpr int ND = N * N * N;
   if (act) {
     const int base = c * ND + (tl % N) + N * (tl / N);      // z-line (j0, j1)
-    double v[N];
+    T v[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = X[base + N * N * j];
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      double a = 0.0, e = 0.0;
+      T a = T(0), e = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         a = fma(t.M[m][j], v[j], a);
@@ -75,7 +75,7 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<double>& t, const doub
   __syncthreads();
   if (act) {
     const int base = c * ND + (tl % N) + N * N * (tl / N);  // y-line (j0, j2)
-    double va[N], ve[N];
+    T va[N], ve[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       va[j] = A[base + N * j];
@@ -83,7 +83,7 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<double>& t, const doub
     }
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      double b = 0.0, g = 0.0;
+      T b = T(0), g = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         b = fma(t.M[m][j], va[j], b);
@@ -97,7 +97,7 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<double>& t, const doub
   __syncthreads();
   if (act) {
     const int base = c * ND + N * tl;                       // x-line (j1, j2) = line tl
-    double vb[N], vg[N];
+    T vb[N], vg[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       vb[j] = B[base + j];
@@ -105,7 +105,7 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<double>& t, const doub
     }
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      double o = 0.0;
+      T o = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         o = fma(t.Kh[m][j], vb[j], o);
@@ -117,19 +117,18 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<double>& t, const doub
 }
 
 // 2D: y-lines then x-lines.
-template <int N>
-__device__ __forceinline__ void cell_sweeps_2d(const KTab<double>& t, const double* X, double* A,
-                                               double* E, int c, int tl, bool act,
-                                               double (&out)[N]) {
+template <typename T, int N>
+__device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X, T* A, T* E, int c,
+                                               int tl, bool act, T (&out)[N]) {
   constexpr int ND = N * N;
   if (act) {
     const int base = c * ND + tl;                           // y-line j0 = tl
-    double v[N];
+    T v[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = X[base + N * j];
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      double a = 0.0, e = 0.0;
+      T a = T(0), e = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         a = fma(t.M[m][j], v[j], a);
@@ -142,7 +141,7 @@ __device__ __forceinline__ void cell_sweeps_2d(const KTab<double>& t, const doub
   __syncthreads();
   if (act) {
     const int base = c * ND + N * tl;                       // x-line j1 = tl
-    double va[N], ve[N];
+    T va[N], ve[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       va[j] = A[base + j];
@@ -150,7 +149,7 @@ __device__ __forceinline__ void cell_sweeps_2d(const KTab<double>& t, const doub
     }
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      double o = 0.0;
+      T o = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         o = fma(t.Kh[m][j], va[j], o);
@@ -170,21 +169,21 @@ __device__ __forceinline__ void cell_sweeps_2d(const KTab<double>& t, const doub
 //   val_q = W_q (sigma E_q - dn u(x~_q)),   grd_q = -W_q E_q,
 // integrated against v and dn v at x~_q by transposed sum factorisation and
 // added to R.  sc must hold 10 L doubles.  All threads of the block call it.
-template <int D, int N>
-__device__ void face_apply(const KTab<double>& t, const double* X, double* R, double* sc,
-                           const double* __restrict__ phi, int k, int s) {
+template <typename T, int D, int N>
+__device__ void face_apply(const KTab<T>& t, const T* X, T* R, T* sc, const T* __restrict__ phi,
+                           int k, int s) {
   constexpr int L = Shape<D, N>::L;
   const int tid = threadIdx.x;
-  double* Tu = sc;
-  double* Td = sc + L;
-  double* Ua = sc + 2 * L;
-  double* Da = sc + 3 * L;
-  double* Ug = sc + 4 * L;
-  double* Dg = sc + 5 * L;
-  double* val = sc + 6 * L;
-  double* grd = sc + 7 * L;
-  double* Va = sc + 8 * L;
-  double* Ga = sc + 9 * L;
+  T* Tu = sc;
+  T* Td = sc + L;
+  T* Ua = sc + 2 * L;
+  T* Da = sc + 3 * L;
+  T* Ug = sc + 4 * L;
+  T* Dg = sc + 5 * L;
+  T* val = sc + 6 * L;
+  T* grd = sc + 7 * L;
+  T* Va = sc + 8 * L;
+  T* Ga = sc + 9 * L;
   // strides of the normal axis and the tangential axes (ascending)
   int sk, sa, sb;
   if (D == 2) {
@@ -197,13 +196,13 @@ __device__ void face_apply(const KTab<double>& t, const double* X, double* R, do
     sb = (k == 2) ? N : N * N;
   }
   const int kend = s ? (N - 1) : 0;
-  const double sg = s ? 1.0 : -1.0;
+  const T sg = s ? T(1) : T(-1);
 
   // 1. traces at the tangential nodes: value and reference normal derivative
   if (tid < L) {
     const int bt = (tid % N) * sa + (D == 3 ? (tid / N) * sb : 0);
     Tu[tid] = X[kend * sk + bt];
-    double dsum = 0.0;
+    T dsum = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) dsum = fma(s ? t.D1[j] : t.D0[j], X[j * sk + bt], dsum);
     Td[tid] = dsum;
@@ -213,7 +212,7 @@ __device__ void face_apply(const KTab<double>& t, const double* X, double* R, do
   if (D == 3) {
     if (tid < L) {
       const int qa = tid % N, jb = tid / N;
-      double u = 0.0, dv = 0.0;
+      T u = T(0), dv = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         u = fma(t.S[qa][j], Tu[j + N * jb], u);
@@ -225,7 +224,7 @@ __device__ void face_apply(const KTab<double>& t, const double* X, double* R, do
     __syncthreads();
     if (tid < L) {
       const int qa = tid % N, qb = tid / N;
-      double u = 0.0, dv = 0.0;
+      T u = T(0), dv = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         u = fma(t.S[qb][j], Ua[qa + N * j], u);
@@ -236,7 +235,7 @@ __device__ void face_apply(const KTab<double>& t, const double* X, double* R, do
     }
   } else {
     if (tid < L) {
-      double u = 0.0, dv = 0.0;
+      T u = T(0), dv = T(0);
 #pragma unroll
       for (int j = 0; j < N; ++j) {
         u = fma(t.S[tid][j], Tu[j], u);
@@ -249,24 +248,24 @@ __device__ void face_apply(const KTab<double>& t, const double* X, double* R, do
   __syncthreads();
   // 3. point evaluation at the shifted points and the pointwise integrands
   if (tid < L) {
-    const double* pq = phi + (size_t)tid * D * N;
-    double p0[N], p1[N];
+    const T* pq = phi + (size_t)tid * D * N;
+    T p0[N], p1[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       p0[j] = __ldg(pq + j);
       p1[j] = __ldg(pq + N + j);
     }
-    double e = 0.0;
+    T e = T(0);
     if (D == 3) {
-      double p2[N];
+      T p2[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) p2[j] = __ldg(pq + 2 * N + j);
 #pragma unroll
       for (int j2 = 0; j2 < N; ++j2) {
-        double s1 = 0.0;
+        T s1 = T(0);
 #pragma unroll
         for (int j1 = 0; j1 < N; ++j1) {
-          double s0 = 0.0;
+          T s0 = T(0);
 #pragma unroll
           for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], X[j0 + N * j1 + N * N * j2], s0);
           s1 = fma(p1[j1], s0, s1);
@@ -276,24 +275,24 @@ __device__ void face_apply(const KTab<double>& t, const double* X, double* R, do
     } else {
 #pragma unroll
       for (int j1 = 0; j1 < N; ++j1) {
-        double s0 = 0.0;
+        T s0 = T(0);
 #pragma unroll
         for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], X[j0 + N * j1], s0);
         e = fma(p1[j1], s0, e);
       }
     }
-    const double W = t.W[tid];
-    const double dn = sg * t.h_inv * Dg[tid];
+    const T W = t.W[tid];
+    const T dn = sg * t.h_inv * Dg[tid];
     val[tid] = W * (t.sigma * e - dn);
     grd[tid] = -W * e * sg * t.h_inv;
   }
   __syncthreads();
   // 4. transposed interpolation back to the tangential nodes, 5. add to R
-  double rv = 0.0, rg = 0.0;
+  T rv = T(0), rg = T(0);
   if (D == 3) {
     if (tid < L) {
       const int ja = tid % N, qb = tid / N;
-      double a = 0.0, g = 0.0;
+      T a = T(0), g = T(0);
 #pragma unroll
       for (int q = 0; q < N; ++q) {
         a = fma(t.S[q][ja], val[q + N * qb], a);
@@ -331,17 +330,17 @@ __device__ void face_apply(const KTab<double>& t, const double* X, double* R, do
 
 // ---- the kernel ----------------------------------------------------------------
 
-template <int D, int N>
+template <typename T, int D, int N>
 __global__ void __launch_bounds__(Shape<D, N>::CPB * Shape<D, N>::L)
-cg_apply_f64_kernel(const CgArgs a, const __grid_constant__ KTab<double> t) {
+cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, CPB = Shape<D, N>::CPB;
-  extern __shared__ double smem[];
-  double* X = smem;
-  double* A = X + CPB * ND;
-  double* E = A + CPB * ND;
-  double* B = E + CPB * ND;
-  double* G = B + CPB * ND;
-  double* sc = G + CPB * ND;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);
+  T* A = X + CPB * ND;
+  T* E = A + CPB * ND;
+  T* B = E + CPB * ND;
+  T* G = B + CPB * ND;
+  T* sc = G + CPB * ND;
   const int tid = threadIdx.x;
 
   if ((int)blockIdx.x < a.nint_tiles) {
@@ -355,9 +354,9 @@ cg_apply_f64_kernel(const CgArgs a, const __grid_constant__ KTab<double> t) {
     __syncthreads();
     const int c = tid / L, tl = tid - c * L;
     const bool act = c < ncells;
-    double out[N];
-    if (D == 3) cell_sweeps_3d<N>(t, X, A, E, B, G, c, tl, act, out);
-    else cell_sweeps_2d<N>(t, X, A, E, c, tl, act, out);
+    T out[N];
+    if (D == 3) cell_sweeps_3d<T, N>(t, X, A, E, B, G, c, tl, act, out);
+    else cell_sweeps_2d<T, N>(t, X, A, E, c, tl, act, out);
     if (act) {
       const int g0 = __ldg(a.lines + (size_t)(first + c) * L + tl);
 #pragma unroll
@@ -374,11 +373,11 @@ cg_apply_f64_kernel(const CgArgs a, const __grid_constant__ KTab<double> t) {
   }
   __syncthreads();
   const bool act = tid < L;
-  double out[N];
-  if (D == 3) cell_sweeps_3d<N>(t, X, A, E, B, G, 0, tid, act, out);
-  else cell_sweeps_2d<N>(t, X, A, E, 0, tid, act, out);
+  T out[N];
+  if (D == 3) cell_sweeps_3d<T, N>(t, X, A, E, B, G, 0, tid, act, out);
+  else cell_sweeps_2d<T, N>(t, X, A, E, 0, tid, act, out);
   __syncthreads();
-  double* R = A;   // A is no longer read: it becomes the cell's result tile
+  T* R = A;   // A is no longer read: it becomes the cell's result tile
   if (act) {
 #pragma unroll
     for (int m = 0; m < N; ++m) R[N * tid + m] = out[m];
@@ -387,7 +386,7 @@ cg_apply_f64_kernel(const CgArgs a, const __grid_constant__ KTab<double> t) {
   const int fs = __ldg(a.face_start + cell), fe = __ldg(a.face_start + cell + 1);
   for (int f = fs; f < fe; ++f) {
     const int kind = __ldg(a.face_kind + f);
-    face_apply<D, N>(t, X, R, sc, a.face_phi + (size_t)f * L * D * N, kind & 3, kind >> 2);
+    face_apply<T, D, N>(t, X, R, sc, a.face_phi + (size_t)f * L * D * N, kind & 3, kind >> 2);
   }
   if (act) {
     const int g0 = __ldg(a.lines + (size_t)cell * L + tid);
@@ -396,31 +395,31 @@ cg_apply_f64_kernel(const CgArgs a, const __grid_constant__ KTab<double> t) {
   }
 }
 
-template <int D, int N>
-static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const double* x,
-                            double* y, cudaStream_t st, Profiler* prof) {
+template <typename T, int D, int N>
+static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                            cudaStream_t st, Profiler* prof) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, CPB = Shape<D, N>::CPB;
-  const KTab<double> t = make_ktab<double>(hp);
-  const size_t smem = (size_t)(5 * CPB * ND + 10 * L) * sizeof(double);
-  cudaError_t err = cudaMemsetAsync(y, 0, (size_t)hp.n_dofs * sizeof(double), st);
+  const KTab<T> t = make_ktab<T>(hp);
+  const size_t smem = (size_t)(5 * CPB * ND + 10 * L) * sizeof(T);
+  cudaError_t err = cudaMemsetAsync(y, 0, (size_t)hp.n_dofs * sizeof(T), st);
   if (err != cudaSuccess) return err;
   if (prof && prof->on && (err = prof->begin(st)) != cudaSuccess) return err;
   int nlaunch = 0;
   for (int c = 0; c < dd.ncolours; ++c) {
     const int n = dd.col_start[c + 1] - dd.col_start[c];
     if (n == 0) continue;
-    CgArgs a;
+    CgArgs<T> a;
     a.x = x;
     a.y = y;
     a.lines = dd.lines;
     a.face_start = dd.face_start;
     a.face_kind = dd.face_kind;
-    a.face_phi = dd.face_phi;
+    a.face_phi = face_phi_of<T>(dd);
     a.cell0 = dd.col_start[c];
     a.nint = dd.col_nint[c];
     a.nint_tiles = (a.nint + CPB - 1) / CPB;
     const int grid = a.nint_tiles + (n - a.nint);
-    cg_apply_f64_kernel<D, N><<<grid, CPB * L, smem, st>>>(a, t);
+    cg_apply_kernel<T, D, N><<<grid, CPB * L, smem, st>>>(a, t);
     nlaunch++;
   }
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -428,14 +427,19 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const d
   return cudaSuccess;
 }
 
-cudaError_t launch_cg_apply_f64(const HostProblem& hp, const DeviceData& dd, const double* x,
-                                double* y, cudaStream_t st, Profiler* prof) {
+template <typename T>
+cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                            cudaStream_t st, Profiler* prof) {
 #define SBM_CASE(DD, NN) \
-  if (hp.d == DD && hp.n == NN) return launch_t<DD, NN>(hp, dd, x, y, st, prof);
+  if (hp.d == DD && hp.n == NN) return launch_t<T, DD, NN>(hp, dd, x, y, st, prof);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE
   return cudaErrorInvalidValue;
 }
+template cudaError_t launch_cg_apply<double>(const HostProblem&, const DeviceData&,
+                                             const double*, double*, cudaStream_t, Profiler*);
+template cudaError_t launch_cg_apply<float>(const HostProblem&, const DeviceData&, const float*,
+                                            float*, cudaStream_t, Profiler*);
 
 }  // namespace sbm

@@ -1,0 +1,387 @@
+// Matrix-free apply (FP64 or FP32) of the SIPG discontinuous Galerkin SBM operator.
+//
+// Cell-centric: every block owns CPB cells and writes their DoFs once (a DG
+// cell's DoFs belong to it alone), so there is a single launch, no colouring
+// and no atomics.  Per cell: the cell term (same sweeps as the CG kernel,
+// Algorithm 1), then its 2d faces in the order (k, s):
+//  * interior face (neighbour active), Algorithm 2 from this cell's side:
+//      [u] = u_K1 - u_K2, {dn u} = (dn u_K1 + dn u_K2)/2 with n = +e_k, K1 the
+//      lower cell; the value test gets +T_v (K1) or -T_v (K2),
+//      T_v = sigma_F [u] - {dn u}, and the normal-derivative test -[u]/2;
+//    the neighbour's trace comes straight from global memory (each face is
+//    evaluated from both sides: twice the face arithmetic, no write conflict);
+//  * surrogate face: Algorithm 3 as in the CG kernel.
+// Face arithmetic is sum-factorised: nodal traces -> tangential Gauss points
+// -> pointwise terms -> transposed interpolation -> added to the cell result.
+#include "internal.hpp"
+
+namespace sbm {
+
+template <int D, int N>
+struct DgShape {
+  static constexpr int L = (D == 3) ? N * N : N;
+  static constexpr int ND = L * N;
+  static constexpr int CPB = (128 / L) > 0 ? (128 / L) : 1;
+};
+
+template <typename T>
+struct DgArgs {
+  const T* __restrict__ x;
+  T* __restrict__ y;
+  const int32_t* __restrict__ cell_rank;   // ordered cell -> active-cell rank
+  const int32_t* __restrict__ nbr;         // [rank][2k+s] neighbour rank or -1
+  const int32_t* __restrict__ face_start;  // ordered cell -> surrogate-face range
+  const T* __restrict__ face_phi;
+  int ncell;
+  T sigma_f;
+};
+
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(DgShape<D, N>::CPB * DgShape<D, N>::L)
+dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
+  constexpr int L = DgShape<D, N>::L, ND = DgShape<D, N>::ND, CPB = DgShape<D, N>::CPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);   // CPB tiles
+  T* A = X + CPB * ND;         // sweep buffers; A becomes the result tile
+  T* E = A + CPB * ND;
+  T* B = E + CPB * ND;
+  T* G = B + CPB * ND;
+  T* T1 = G + CPB * ND;        // face scratch, CPB * L each
+  T* T2 = T1 + CPB * L;
+  T* U1 = T2 + CPB * L;
+  T* U2 = U1 + CPB * L;
+  T* P1 = U2 + CPB * L;
+  T* P2 = P1 + CPB * L;
+  const int tid = threadIdx.x;
+  const int first = blockIdx.x * CPB;
+  const int ncells = min(CPB, a.ncell - first);
+  for (int r = tid; r < ncells * ND; r += blockDim.x) {
+    const int c = r / ND;
+    X[r] = __ldg(a.x + (size_t)__ldg(a.cell_rank + first + c) * ND + (r - c * ND));
+  }
+  __syncthreads();
+  const int c = tid / L, tl = tid - c * L;
+  const bool act = c < ncells;
+  const int pos = first + (act ? c : 0);
+  const int rank = __ldg(a.cell_rank + pos);
+  T* Xc = X + c * ND;
+  T* R = A + c * ND;
+  {
+    // cell term, then park the x-line result in R (A is free after the syncs)
+    constexpr int NN = N;
+    T out[NN];
+    if (act) {
+      if (D == 3) {
+        const int base = c * ND + (tl % N) + N * (tl / N);
+        T v[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = X[base + N * N * j];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          T s0 = T(0), s1 = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            s0 = fma(t.M[m][j], v[j], s0);
+            s1 = fma(t.K[m][j], v[j], s1);
+          }
+          A[base + N * N * m] = s0;
+          E[base + N * N * m] = s1;
+        }
+      } else {
+        const int base = c * ND + tl;
+        T v[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) v[j] = X[base + N * j];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          T s0 = T(0), s1 = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            s0 = fma(t.M[m][j], v[j], s0);
+            s1 = fma(t.K[m][j], v[j], s1);
+          }
+          A[base + N * m] = s0;
+          E[base + N * m] = s1;
+        }
+      }
+    }
+    __syncthreads();
+    if (D == 3) {
+      if (act) {
+        const int base = c * ND + (tl % N) + N * N * (tl / N);
+        T va[N], ve[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          va[j] = A[base + N * j];
+          ve[j] = E[base + N * j];
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          T b = T(0), g = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            b = fma(t.M[m][j], va[j], b);
+            g = fma(t.K[m][j], va[j], g);
+            g = fma(t.M[m][j], ve[j], g);
+          }
+          B[base + N * m] = b;
+          G[base + N * m] = g;
+        }
+      }
+      __syncthreads();
+    }
+    if (act) {
+      const T* P = (D == 3) ? B : A;
+      const T* Q = (D == 3) ? G : E;
+      const int base = c * ND + N * tl;
+      T vb[N], vg[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        vb[j] = P[base + j];
+        vg[j] = Q[base + j];
+      }
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        T o = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          o = fma(t.Kh[m][j], vb[j], o);
+          o = fma(t.Mh[m][j], vg[j], o);
+        }
+        out[m] = o;
+      }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < N; ++m) R[N * tl + m] = out[m];
+    }
+  }
+  __syncthreads();
+
+  int fptr = act ? __ldg(a.face_start + pos) : 0;   // next surrogate face of this cell
+  T* t1 = T1 + c * L;
+  T* t2 = T2 + c * L;
+  T* u1 = U1 + c * L;
+  T* u2 = U2 + c * L;
+  T* p1 = P1 + c * L;
+  T* p2 = P2 + c * L;
+  for (int k = 0; k < D; ++k) {
+    int sk, sa, sb;
+    if (D == 2) {
+      sk = (k == 0) ? 1 : N;
+      sa = (k == 0) ? N : 1;
+      sb = 0;
+    } else {
+      sk = (k == 0) ? 1 : (k == 1 ? N : N * N);
+      sa = (k == 0) ? N : 1;
+      sb = (k == 2) ? N : N * N;
+    }
+    const int bt = (tl % N) * sa + (D == 3 ? (tl / N) * sb : 0);
+    for (int s = 0; s < 2; ++s) {
+      const int nb = act ? __ldg(a.nbr + (size_t)rank * 2 * D + 2 * k + s) : -1;
+      const bool interior = nb >= 0;
+      const int kend = s ? N - 1 : 0;
+      const T sg = s ? T(1) : T(-1);
+      const T* phi = nullptr;
+      if (act && !interior) phi = a.face_phi + (size_t)(fptr++) * L * D * N;
+      // A. nodal traces (own side and, for interior faces, the neighbour's)
+      if (act) {
+        T um = Xc[kend * sk + bt], dm = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) dm = fma(s ? t.D1[j] : t.D0[j], Xc[j * sk + bt], dm);
+        if (interior) {
+          const T* xn = a.x + (size_t)nb * ND;
+          const int nend = s ? 0 : N - 1;
+          T un = __ldg(xn + nend * sk + bt), dnb = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j)
+            dnb = fma(s ? t.D0[j] : t.D1[j], __ldg(xn + j * sk + bt), dnb);
+          t1[tl] = s ? (um - un) : (un - um);        // [u] = u_K1 - u_K2
+          t2[tl] = T(0.5) * (dm + dnb);                 // {d_k u} (reference)
+        } else {
+          t1[tl] = um;
+          t2[tl] = dm;
+        }
+      }
+      __syncthreads();
+      // B. tangential interpolation to the Gauss points
+      if (D == 3) {
+        if (act) {
+          const int qa = tl % N, jb = tl / N;
+          T v1 = T(0), v2 = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            v1 = fma(t.S[qa][j], t1[j + N * jb], v1);
+            v2 = fma(t.S[qa][j], t2[j + N * jb], v2);
+          }
+          u1[tl] = v1;
+          u2[tl] = v2;
+        }
+        __syncthreads();
+        if (act) {
+          const int qa = tl % N, qb = tl / N;
+          T v1 = T(0), v2 = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            v1 = fma(t.S[qb][j], u1[qa + N * j], v1);
+            v2 = fma(t.S[qb][j], u2[qa + N * j], v2);
+          }
+          t1[tl] = v1;   // reuse: values at the Gauss points
+          t2[tl] = v2;
+        }
+      } else {
+        if (act) {
+          T v1 = T(0), v2 = T(0);
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            v1 = fma(t.S[tl][j], t1[j], v1);
+            v2 = fma(t.S[tl][j], t2[j], v2);
+          }
+          u1[tl] = v1;
+          u2[tl] = v2;
+        }
+      }
+      __syncthreads();
+      // C. pointwise integrands
+      if (act) {
+        const T g1 = (D == 3) ? t1[tl] : u1[tl];
+        const T g2 = (D == 3) ? t2[tl] : u2[tl];
+        const T W = t.W[tl];
+        T val, grd;
+        if (interior) {
+          const T Tv = a.sigma_f * g1 - t.h_inv * g2;
+          val = W * sg * Tv;
+          grd = -T(0.5) * W * g1 * t.h_inv;
+        } else {
+          T p0[N], pp1[N];
+          const T* pq = phi + (size_t)tl * D * N;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            p0[j] = __ldg(pq + j);
+            pp1[j] = __ldg(pq + N + j);
+          }
+          T e = T(0);
+          if (D == 3) {
+            T pp2[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) pp2[j] = __ldg(pq + 2 * N + j);
+#pragma unroll
+            for (int j2 = 0; j2 < N; ++j2) {
+              T s1 = T(0);
+#pragma unroll
+              for (int j1 = 0; j1 < N; ++j1) {
+                T s0 = T(0);
+#pragma unroll
+                for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xc[j0 + N * j1 + N * N * j2], s0);
+                s1 = fma(pp1[j1], s0, s1);
+              }
+              e = fma(pp2[j2], s1, e);
+            }
+          } else {
+#pragma unroll
+            for (int j1 = 0; j1 < N; ++j1) {
+              T s0 = T(0);
+#pragma unroll
+              for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xc[j0 + N * j1], s0);
+              e = fma(pp1[j1], s0, e);
+            }
+          }
+          val = W * (t.sigma * e - sg * t.h_inv * g2);
+          grd = -W * e * sg * t.h_inv;
+        }
+        p1[tl] = val;
+        p2[tl] = grd;
+      }
+      __syncthreads();
+      // D. transposed interpolation, E. add to the cell result
+      T rv = T(0), rg = T(0);
+      if (D == 3) {
+        if (act) {
+          const int ja = tl % N, qb = tl / N;
+          T v1 = T(0), v2 = T(0);
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            v1 = fma(t.S[q][ja], p1[q + N * qb], v1);
+            v2 = fma(t.S[q][ja], p2[q + N * qb], v2);
+          }
+          u1[tl] = v1;
+          u2[tl] = v2;
+        }
+        __syncthreads();
+        if (act) {
+          const int ja = tl % N, jb = tl / N;
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            rv = fma(t.S[q][jb], u1[ja + N * q], rv);
+            rg = fma(t.S[q][jb], u2[ja + N * q], rg);
+          }
+        }
+      } else {
+        if (act) {
+#pragma unroll
+          for (int q = 0; q < N; ++q) {
+            rv = fma(t.S[q][tl], p1[q], rv);
+            rg = fma(t.S[q][tl], p2[q], rg);
+          }
+        }
+      }
+      if (act) {
+        R[kend * sk + bt] += rv;
+#pragma unroll
+        for (int j = 0; j < N; ++j) R[j * sk + bt] = fma(s ? t.D1[j] : t.D0[j], rg, R[j * sk + bt]);
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = tid; r < ncells * ND; r += blockDim.x) {
+    const int cc = r / ND;
+    a.y[(size_t)__ldg(a.cell_rank + first + cc) * ND + (r - cc * ND)] = A[r];
+  }
+}
+
+template <typename T, int D, int N>
+static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                        cudaStream_t st, Profiler* prof) {
+  constexpr int L = DgShape<D, N>::L, ND = DgShape<D, N>::ND, CPB = DgShape<D, N>::CPB;
+  const KTab<T> t = make_ktab<T>(hp);
+  const size_t smem = (size_t)(5 * CPB * ND + 6 * CPB * L) * sizeof(T);
+  cudaError_t err;
+  if (smem > 48 * 1024) {
+    err = cudaFuncSetAttribute(dg_apply_kernel<T, D, N>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  DgArgs<T> a;
+  a.x = x;
+  a.y = y;
+  a.cell_rank = dd.cell_rank;
+  a.nbr = dd.nbr;
+  a.face_start = dd.face_start;
+  a.face_phi = face_phi_of<T>(dd);
+  a.ncell = dd.col_start[dd.ncolours];
+  a.sigma_f = (T)hp.sigma_f;
+  if (prof && prof->on && (err = prof->begin(st)) != cudaSuccess) return err;
+  const int grid = (a.ncell + CPB - 1) / CPB;
+  dg_apply_kernel<T, D, N><<<grid, CPB * L, smem, st>>>(a, t);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (prof && prof->on) return prof->end(st, 1);
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_dg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                            cudaStream_t st, Profiler* prof) {
+#define SBM_CASE(DD, NN) \
+  if (hp.d == DD && hp.n == NN) return dg_t<T, DD, NN>(hp, dd, x, y, st, prof);
+  SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
+  SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
+#undef SBM_CASE
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_dg_apply<double>(const HostProblem&, const DeviceData&,
+                                             const double*, double*, cudaStream_t, Profiler*);
+template cudaError_t launch_dg_apply<float>(const HostProblem&, const DeviceData&, const float*,
+                                            float*, cudaStream_t, Profiler*);
+
+}  // namespace sbm

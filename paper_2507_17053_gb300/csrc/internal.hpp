@@ -43,6 +43,7 @@ struct DeviceData {
   int32_t* face_start = nullptr; // [Nc + 1] per ordered cell, range into the ordered face list
   int32_t* face_kind = nullptr;  // [F] k | (s << 2)
   double* face_phi = nullptr;    // [F * Q * d * n] phi_j(xi_{q,l}) at the shifted points
+  float* face_phi32 = nullptr;   // the same table rounded to FP32
   int32_t* nbr = nullptr;        // DG [Nc * 2d] neighbour rank per (k, s), -1 = surrogate
   double* stage_x = nullptr;     // host-apply staging buffers (allocated on first use)
   double* stage_y = nullptr;
@@ -67,9 +68,21 @@ struct CellLaunch {
 };
 CellLaunch cell_launch_shape(int d, int n);
 
-// FP64 apply, CG: y = A x (memset + one launch per colour).
-cudaError_t launch_cg_apply_f64(const HostProblem& hp, const DeviceData& dd, const double* x,
-                                double* y, cudaStream_t st, Profiler* prof);
+template <typename T> inline const T* face_phi_of(const DeviceData& dd);
+template <> inline const double* face_phi_of<double>(const DeviceData& dd) { return dd.face_phi; }
+template <> inline const float* face_phi_of<float>(const DeviceData& dd) { return dd.face_phi32; }
+
+// Apply, CG: y = A x (memset + one launch per colour); T = double or float.
+template <typename T>
+cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                            cudaStream_t st, Profiler* prof);
+// Apply, DG: one launch.
+template <typename T>
+cudaError_t launch_dg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                            cudaStream_t st, Profiler* prof);
+// FP64 diagonal.
+cudaError_t launch_diag_f64(const HostProblem& hp, const DeviceData& dd, double* diag,
+                            cudaStream_t st);
 
 }  // namespace sbm
 

@@ -1,0 +1,58 @@
+// Krylov drivers on the matrix-free operator (implementation in krylov.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <functional>
+#include <vector>
+
+#include "sbm.h"
+
+namespace sbm {
+
+constexpr int SBM_NOT_DONE = -1;
+
+// y = A x on stream st (all work enqueued; no synchronisation)
+template <typename T>
+using ApplyFn = std::function<cudaError_t(const T* x, T* y, cudaStream_t st)>;
+
+struct SolveInfo {
+  int iters = 0;        // operator applications inside the Krylov iterations
+  double relres = 0.0;  // true relative residual |b - A x| / |b| at exit (FP64 for IR)
+  int restarts = 0;     // CG restarts / GMRES cycles / IR outer steps
+};
+
+struct SolveStatus {
+  int status;
+  cudaError_t cuda;
+};
+
+// Device scratch of one solve; released by the caller.
+struct Workspace {
+  std::vector<void*> bufs;
+  void* host_state = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaError_t alloc(void** p, size_t bytes);
+  void release();
+};
+
+// Conjugate gradients (Jacobi-preconditioned when diag != nullptr), FP64.
+SolveStatus solve_cg(const ApplyFn<double>& apply, int64_t n, const double* b, double* x,
+                     const double* diag, double rtol, int maxit, cudaStream_t st, Workspace& ws,
+                     SolveInfo* info);
+
+// Restarted GMRES(restart) in precision T on x/b of precision TX.
+template <typename T, typename TX>
+SolveStatus solve_gmres(const ApplyFn<T>& apply, int64_t n, const TX* b, TX* x, double rtol,
+                        int maxit, int restart, cudaStream_t st, Workspace& ws, SolveInfo* info,
+                        const ApplyFn<TX>* apply_x);
+
+// FP64 iterative refinement: r = b - A64 x in FP64, inner FP32 GMRES on
+// A32 c = r/|r| to inner_rtol, x += |r| c; maxit outer steps.
+SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply32, int64_t n,
+                     const double* b, double* x, double rtol, int maxit, int restart,
+                     double inner_rtol, int inner_maxit, cudaStream_t st, Workspace& ws,
+                     SolveInfo* info);
+
+}  // namespace sbm

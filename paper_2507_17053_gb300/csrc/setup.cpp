@@ -476,4 +476,111 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
   return SBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Manufactured data, right-hand side, interpolant
+// ---------------------------------------------------------------------------
+
+bool manufactured_ok(int id, int dim) { return id == 0 || (id == 1 && dim == 2); }
+
+double manufactured_u(int id, int dim, const double* x) {
+  const double pi = 3.14159265358979323846;
+  if (id == 0) {
+    double u = 1.0;
+    for (int i = 0; i < dim; ++i) u *= std::sin(pi * x[i]);
+    return u;
+  }
+  return 2.0 * std::cos(x[0]) * std::sin(x[1]);
+}
+
+double manufactured_f(int id, int dim, const double* x) {
+  const double pi = 3.14159265358979323846;
+  if (id == 0) return dim * pi * pi * manufactured_u(id, dim, x);
+  return 2.0 * manufactured_u(id, dim, x);
+}
+
+// global index of local DoF j of active cell c
+static int64_t global_dof(const HostProblem& P, int64_t c, int j) {
+  if (P.desc.dg) return c * P.nd + j;
+  return (int64_t)P.lines[c * P.L + j / P.n] + (j % P.n);
+}
+
+void build_rhs(const HostProblem& P, int id, double* b) {
+  const int d = P.d, n = P.n, nd = P.nd, L = P.L;
+  const double h = P.h;
+  const Tables1D& T = P.tab;
+  for (int64_t i = 0; i < P.n_dofs; ++i) b[i] = 0.0;
+  const int64_t Nc = (int64_t)P.cell_bg.size();
+  std::vector<double> Fq(nd), t1(nd), t2(nd);
+  const double hd = std::pow(h, d);
+  for (int64_t c = 0; c < Nc; ++c) {
+    double lo[3];
+    for (int l = 0; l < d; ++l) lo[l] = -1.0 + h * (double)P.cells[c * d + l];
+    // f h^d w_q at the tensor Gauss points, q = q0 + n q1 (+ n^2 q2)
+    for (int q = 0; q < nd; ++q) {
+      int qq[3] = {q % n, (q / n) % n, q / (n * n)};
+      double x[3], w = hd;
+      for (int l = 0; l < d; ++l) {
+        x[l] = lo[l] + h * T.gpts[qq[l]];
+        w *= T.gwts[qq[l]];
+      }
+      Fq[q] = w * manufactured_f(id, d, x);
+    }
+    // b_K[j] = sum_q Fq[q] prod_l S[q_l][j_l]: one transposed sweep per axis
+    std::vector<double>* src = &Fq;
+    std::vector<double>* dst = &t1;
+    int stride = 1;
+    for (int l = 0; l < d; ++l) {
+      for (int r = 0; r < nd; ++r) {
+        const int jl = (r / stride) % n, base = r - jl * stride;
+        double s = 0.0;
+        for (int q = 0; q < n; ++q) s += T.S[q][jl] * (*src)[base + q * stride];
+        (*dst)[r] = s;
+      }
+      src = dst;
+      dst = (dst == &t1) ? &t2 : &t1;
+      stride *= n;
+    }
+    for (int j = 0; j < nd; ++j) b[global_dof(P, c, j)] += (*src)[j];
+  }
+  // surrogate faces
+  const int64_t F = (int64_t)P.sfaces.size() / 3;
+  const double hd1 = std::pow(h, d - 1);
+  for (int64_t f = 0; f < F; ++f) {
+    const int c = P.sfaces[3 * f], k = P.sfaces[3 * f + 1], s = P.sfaces[3 * f + 2];
+    int tang[2] = {0, 0}, nt = 0;
+    for (int l = 0; l < d; ++l) if (l != k) tang[nt++] = l;
+    const double sg = s ? 1.0 : -1.0;
+    for (int q = 0; q < L; ++q) {
+      const int qa = q % n, qb = q / n;
+      const double W = hd1 * T.gwts[qa] * (d == 3 ? T.gwts[qb] : 1.0);
+      const double g = manufactured_u(id, d, &P.face_x[(f * L + q) * d]);
+      for (int j = 0; j < nd; ++j) {
+        int jj[3] = {j % n, (j / n) % n, j / (n * n)};
+        double tg = T.S[qa][jj[tang[0]]];
+        if (d == 3) tg *= T.S[qb][jj[tang[1]]];
+        const double v = (jj[k] == (s ? n - 1 : 0)) ? tg : 0.0;
+        const double dn = sg / h * (s ? T.D1[jj[k]] : T.D0[jj[k]]) * tg;
+        const double contrib = W * g * (P.sigma * v - dn);
+        if (contrib != 0.0) b[global_dof(P, c, j)] += contrib;
+      }
+    }
+  }
+}
+
+void build_interpolant(const HostProblem& P, int id, double* u) {
+  const int d = P.d, n = P.n, nd = P.nd;
+  const double h = P.h;
+  const int64_t Nc = (int64_t)P.cell_bg.size();
+  for (int64_t c = 0; c < Nc; ++c) {
+    double lo[3];
+    for (int l = 0; l < d; ++l) lo[l] = -1.0 + h * (double)P.cells[c * d + l];
+    for (int j = 0; j < nd; ++j) {
+      int jj[3] = {j % n, (j / n) % n, j / (n * n)};
+      double x[3];
+      for (int l = 0; l < d; ++l) x[l] = lo[l] + h * P.tab.nodes[jj[l]];
+      u[global_dof(P, c, j)] = manufactured_u(id, d, x);
+    }
+  }
+}
+
 }  // namespace sbm

@@ -78,4 +78,17 @@ struct HostProblem {
 // Build everything on the host.  Returns SBM_OK or an error code with *err set.
 int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err);
 
+// Manufactured solutions: 0 = prod_i sin(pi x_i) (f = d pi^2 u),
+// 1 = 2 cos(x_0) sin(x_1) in 2D (f = 2 u).
+bool manufactured_ok(int id, int dim);
+double manufactured_u(int id, int dim, const double* x);
+double manufactured_f(int id, int dim, const double* x);
+
+// Right-hand side of the weak form (Section 2.1):
+//   b_i = int f v_i - int_F (grad v_i . n~) g(x) + int_F sigma g(x) v_i,
+// g = u at the true-boundary point x_q of each surrogate quadrature point.
+void build_rhs(const HostProblem& hp, int id, double* b);
+// Nodal interpolant of the manufactured solution (DoF values at the nodes).
+void build_interpolant(const HostProblem& hp, int id, double* u);
+
 }  // namespace sbm

@@ -95,3 +95,18 @@ def test_host_geometry_matches_oracle(w):
 @pytest.mark.slow
 def test_host_geometry_matches_oracle_full_sphere():
     _compare_geometry(S.SPHERE_3D_Q4)
+
+
+@pytest.mark.parametrize("w", SMALL[:4], ids=lambda w: w.name)
+def test_host_rhs_and_interpolant_match_oracle(w):
+    from oracle.operator import sin_solution
+    O = OracleProblem.from_workload(w)
+    P = G.Problem.from_workload(w, device=False)
+    u, f = sin_solution(w.dim)
+    ref = O.rhs(f, u)
+    assert np.abs(P.rhs(0) - ref).max() <= 1e-13 * np.abs(ref).max()
+    np.testing.assert_allclose(P.interpolate(0), O.interpolate(u), rtol=0, atol=1e-15)
+    if w.dim == 2:
+        u1 = lambda X: 2.0 * np.cos(X[..., 0]) * np.sin(X[..., 1])
+        ref1 = O.rhs(lambda X: 2.0 * u1(X), u1)
+        assert np.abs(P.rhs(1) - ref1).max() <= 1e-13 * np.abs(ref1).max()

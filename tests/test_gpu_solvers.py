@@ -1,0 +1,80 @@
+"""CG, GMRES and mixed-precision iterative refinement on the GPU, against the
+oracle's direct solve of the same assembled system."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import torch
+
+import paper_2507_17053_gb300 as G
+import synthetic as S
+from oracle.operator import Problem as OracleProblem, sin_solution
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _system(w):
+    O = OracleProblem.from_workload(w)
+    P = G.Problem.from_workload(w)
+    u, f = sin_solution(w.dim)
+    b = O.rhs(f, u)
+    xref = spla.spsolve(O.assemble().tocsc(), b)
+    return O, P, b, xref
+
+
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
+@pytest.mark.parametrize("d", [2, 3])
+def test_cg_on_zero_shift_spd_system(d, precond):
+    """Box domain on mesh planes: the shift is zero and A is symmetric
+    positive definite (symmetric Nitsche form), so CG must converge."""
+    w = S._wl("box", d, 2, 8 if d == 3 else 16, S.box((0.0,) * d, (0.5,) * d))
+    O, P, b, xref = _system(w)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    it, rr, ok = G.sbm_cg(P.handle, bd, x, rtol=1e-10, maxit=5000, precond=G.PRECOND[precond])
+    assert ok and rr <= 1e-10 and it > 5
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(xs - xref) <= 1e-8 * np.linalg.norm(xref)
+    # deterministic: a second solve is bitwise identical
+    x2 = torch.zeros_like(bd)
+    G.sbm_cg(P.handle, bd, x2, rtol=1e-10, maxit=5000, precond=G.PRECOND[precond])
+    assert torch.equal(x, x2)
+
+
+def test_cg_reports_failure_on_nonsymmetric_system():
+    """The 2D workload's operator is not symmetric (non-zero shift); CG on it
+    does not reach 1e-10 and must say so instead of hanging or crashing."""
+    O, P, b, xref = _system(S.DISK_2D_Q2)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    it, rr, ok = G.sbm_cg(P.handle, bd, x, rtol=1e-10, maxit=3000)
+    assert not ok and it <= 3000
+    with pytest.raises(G.SbmError) as e:
+        G.sbm_cg(P.handle, bd, torch.zeros_like(bd), rtol=1e-10, maxit=50,
+                 raise_not_converged=True)
+    assert G.STATUS[e.value.status] == "SBM_ERR_NOT_CONVERGED"
+
+
+def test_gmres_disk_workload():
+    O, P, b, xref = _system(S.DISK_2D_Q2)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    it, rr, ok = G.sbm_gmres(P.handle, bd, x, rtol=1e-10, maxit=5000, restart=100)
+    assert ok and rr <= 1e-10
+    assert np.linalg.norm(x.cpu().numpy() - xref) <= 1e-7 * np.linalg.norm(xref)
+
+
+@pytest.mark.parametrize("w", [S.DISK_2D_Q2, S.SPHERE_3D_Q4.resized(8, degree=2)],
+                         ids=lambda w: w.name)
+def test_mixed_precision_ir(w):
+    O, P, b, xref = _system(w)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    it, rr, ok, outer = G.sbm_solve_ir(P.handle, bd, x, rtol=1e-10, max_outer=40, restart=100,
+                                       inner_rtol=1e-4, inner_maxit=3000)
+    assert ok and rr <= 1e-10, (it, rr, outer)
+    assert np.linalg.norm(x.cpu().numpy() - xref) <= 1e-7 * np.linalg.norm(xref)
