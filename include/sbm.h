@@ -25,7 +25,9 @@
  *      DG: active cells in lexicographic order (axis 0 fastest), (p+1)^d
  *          values each, local lexicographic order inside a cell.
  *  - Thread safety: distinct problems may be used from different threads;
- *    one problem must not be used by two threads at once.
+ *    one problem must not be used by two threads at once, and two applies of
+ *    one problem must not run concurrently on different streams (they share
+ *    the problem's per-face scratch buffer).
  */
 #ifndef SBM_H
 #define SBM_H

@@ -93,6 +93,12 @@ static void free_device(DeviceData* dd) {
   cudaFree(dd->cell_rank);
   cudaFree(dd->face_start);
   cudaFree(dd->face_kind);
+  cudaFree(dd->face_cell);
+  cudaFree(dd->face_out);
+  cudaFree(dd->face_out32);
+  cudaFree(dd->dof_colours);
+  cudaFree(dd->ycol);
+  cudaFree(dd->ycol32);
   cudaFree(dd->face_phi);
   cudaFree(dd->face_phi32);
   cudaFree(dd->nbr);
@@ -135,7 +141,7 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   }
   dd->col_start[dd->ncolours] = (int)dd->order.size();
 
-  std::vector<int32_t> lines_o, fstart(Nc + 1, 0), fkind;
+  std::vector<int32_t> lines_o, fstart(Nc + 1, 0), fkind, fcell;
   std::vector<double> fphi;
   if (!hp.desc.dg) lines_o.resize(Nc * L);
   fkind.reserve(F);
@@ -148,6 +154,7 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
     for (int j = 0; j < nf[c]; ++j) {
       const int64_t f = first_face[c] + j;
       fkind.push_back(hp.sfaces[3 * f + 1] | (hp.sfaces[3 * f + 2] << 2));
+      fcell.push_back((int32_t)i);
       for (int q = 0; q < L; ++q)
         for (int l = 0; l < d; ++l) {
           double phi[kMaxN];
@@ -177,6 +184,32 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   if ((e = upload(&dd->cell_rank, dd->order.data(), dd->order.size())) != cudaSuccess) goto err;
   if ((e = upload(&dd->face_start, fstart.data(), fstart.size())) != cudaSuccess) goto err;
   if ((e = upload(&dd->face_kind, fkind.data(), fkind.size())) != cudaSuccess) goto err;
+  if ((e = upload(&dd->face_cell, fcell.data(), fcell.size())) != cudaSuccess) goto err;
+  dd->nface = (int)fkind.size();
+  if (!hp.desc.dg) {
+    // colour mask per DoF and the colour accumulation buffers
+    std::vector<uint8_t> mask(hp.n_dofs, 0);
+    for (int col = 0; col < dd->ncolours; ++col)
+      for (int i = dd->col_start[col]; i < dd->col_start[col + 1]; ++i) {
+        const int c = dd->order[i];
+        for (int line = 0; line < L; ++line) {
+          const int32_t g = hp.lines[(int64_t)c * L + line];
+          for (int m = 0; m < n; ++m) mask[g + m] |= (uint8_t)(1u << col);
+        }
+      }
+    if ((e = upload(&dd->dof_colours, mask.data(), mask.size())) != cudaSuccess) goto err;
+    const size_t nb = (size_t)dd->ncolours * hp.n_dofs;
+    if ((e = cudaMalloc((void**)&dd->ycol, nb * sizeof(double))) != cudaSuccess) goto err;
+    if ((e = cudaMalloc((void**)&dd->ycol32, nb * sizeof(float))) != cudaSuccess) goto err;
+  }
+  if (dd->nface > 0) {
+    if ((e = cudaMalloc((void**)&dd->face_out, (size_t)dd->nface * 2 * L * sizeof(double))) !=
+        cudaSuccess)
+      goto err;
+    if ((e = cudaMalloc((void**)&dd->face_out32, (size_t)dd->nface * 2 * L * sizeof(float))) !=
+        cudaSuccess)
+      goto err;
+  }
   if ((e = upload(&dd->face_phi, fphi.data(), fphi.size())) != cudaSuccess) goto err;
   {
     std::vector<float> f32(fphi.begin(), fphi.end());

@@ -10,7 +10,8 @@
 //      T_v = sigma_F [u] - {dn u}, and the normal-derivative test -[u]/2;
 //    the neighbour's trace comes straight from global memory (each face is
 //    evaluated from both sides: twice the face arithmetic, no write conflict);
-//  * surrogate face: Algorithm 3 as in the CG kernel.
+//  * surrogate face: Algorithm 3, computed for all faces beforehand by the
+//    face kernel (face_kernel.cu) and folded in here from its scratch.
 // Face arithmetic is sum-factorised: nodal traces -> tangential Gauss points
 // -> pointwise terms -> transposed interpolation -> added to the cell result.
 #include "internal.hpp"
@@ -31,7 +32,7 @@ struct DgArgs {
   const int32_t* __restrict__ cell_rank;   // ordered cell -> active-cell rank
   const int32_t* __restrict__ nbr;         // [rank][2k+s] neighbour rank or -1
   const int32_t* __restrict__ face_start;  // ordered cell -> surrogate-face range
-  const T* __restrict__ face_phi;
+  const T* __restrict__ face_out;          // [F][2L] from the face kernel
   int ncell;
   T sigma_f;
 };
@@ -183,8 +184,8 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
       const bool interior = nb >= 0;
       const int kend = s ? N - 1 : 0;
       const T sg = s ? T(1) : T(-1);
-      const T* phi = nullptr;
-      if (act && !interior) phi = a.face_phi + (size_t)(fptr++) * L * D * N;
+      const T* fo = nullptr;
+      if (act && !interior) fo = a.face_out + (size_t)(fptr++) * 2 * L;
       // A. nodal traces (own side and, for interior faces, the neighbour's)
       if (act) {
         T um = Xc[kend * sk + bt], dm = T(0);
@@ -200,8 +201,8 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
           t1[tl] = s ? (um - un) : (un - um);        // [u] = u_K1 - u_K2
           t2[tl] = T(0.5) * (dm + dnb);                 // {d_k u} (reference)
         } else {
-          t1[tl] = um;
-          t2[tl] = dm;
+          t1[tl] = T(0);
+          t2[tl] = T(0);
         }
       }
       __syncthreads();
@@ -252,43 +253,10 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
         if (interior) {
           const T Tv = a.sigma_f * g1 - t.h_inv * g2;
           val = W * sg * Tv;
-          grd = -T(0.5) * W * g1 * t.h_inv;
+          grd = T(-0.5) * W * g1 * t.h_inv;
         } else {
-          T p0[N], pp1[N];
-          const T* pq = phi + (size_t)tl * D * N;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            p0[j] = __ldg(pq + j);
-            pp1[j] = __ldg(pq + N + j);
-          }
-          T e = T(0);
-          if (D == 3) {
-            T pp2[N];
-#pragma unroll
-            for (int j = 0; j < N; ++j) pp2[j] = __ldg(pq + 2 * N + j);
-#pragma unroll
-            for (int j2 = 0; j2 < N; ++j2) {
-              T s1 = T(0);
-#pragma unroll
-              for (int j1 = 0; j1 < N; ++j1) {
-                T s0 = T(0);
-#pragma unroll
-                for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xc[j0 + N * j1 + N * N * j2], s0);
-                s1 = fma(pp1[j1], s0, s1);
-              }
-              e = fma(pp2[j2], s1, e);
-            }
-          } else {
-#pragma unroll
-            for (int j1 = 0; j1 < N; ++j1) {
-              T s0 = T(0);
-#pragma unroll
-              for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xc[j0 + N * j1], s0);
-              e = fma(pp1[j1], s0, e);
-            }
-          }
-          val = W * (t.sigma * e - sg * t.h_inv * g2);
-          grd = -W * e * sg * t.h_inv;
+          val = T(0);
+          grd = T(0);
         }
         p1[tl] = val;
         p2[tl] = grd;
@@ -326,6 +294,10 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
           }
         }
       }
+      if (act && !interior) {           // surrogate face: results of the face kernel
+        rv = __ldg(fo + tl);
+        rg = __ldg(fo + L + tl);
+      }
       if (act) {
         R[kend * sk + bt] += rv;
 #pragma unroll
@@ -358,14 +330,20 @@ static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x,
   a.cell_rank = dd.cell_rank;
   a.nbr = dd.nbr;
   a.face_start = dd.face_start;
-  a.face_phi = face_phi_of<T>(dd);
+  a.face_out = face_out_of<T>(dd);
   a.ncell = dd.col_start[dd.ncolours];
   a.sigma_f = (T)hp.sigma_f;
   if (prof && prof->on && (err = prof->begin(st)) != cudaSuccess) return err;
+  int nlaunch = 1;
+  if (dd.nface > 0) {
+    if ((err = launch_face_kernel<T>(hp, dd, x, face_out_of<T>(dd), st)) != cudaSuccess)
+      return err;
+    nlaunch++;
+  }
   const int grid = (a.ncell + CPB - 1) / CPB;
   dg_apply_kernel<T, D, N><<<grid, CPB * L, smem, st>>>(a, t);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  if (prof && prof->on) return prof->end(st, 1);
+  if (prof && prof->on) return prof->end(st, nlaunch);
   return cudaSuccess;
 }
 

@@ -1,0 +1,227 @@
+// Surrogate-boundary faces (Algorithm 3), all faces of a problem in one launch.
+//
+// For the face (k, s) of cell K (outward normal (2s-1) e_k):
+//  1. traces of u and of the reference normal derivative at the face's
+//     tangential nodes (GLL nodes contain the end points, so the value trace
+//     is the face slice of the tile);
+//  2. interpolation to the tangential Gauss points x~_q (sum factorisation);
+//  3. E u(x~_q) = u_K(x_q): point evaluation of the cell polynomial at the
+//     shifted point from the stored 1D values phi_j(xi_{q,l}) -- the
+//     O((p+1)^(2d-1)) step -- and the pointwise integrands
+//       val_q = W_q (sigma E_q - dn u(x~_q)),  grd_q = -W_q E_q dn-scale;
+//  4. transposed interpolation back to the tangential nodes.
+// The face's contribution to its cell is then fully described by two
+// n^(d-1) vectors per face (value test rv, normal-derivative test rg); the
+// cell kernels fold them into the cell result:
+//   R[node (kend, jt)] += rv[jt],  R[node (j, jt)] += phi_j'(s) rg[jt].
+// Output: out[f * 2L + jt] = rv[jt], out[f * 2L + L + jt] = rg[jt].  Faces
+// write disjoint slots, so there is no ordering hazard and no atomics.
+#include "sweeps.cuh"
+
+namespace sbm {
+
+template <typename T>
+struct FaceArgs {
+  const T* __restrict__ x;
+  const int32_t* __restrict__ lines;       // CG gather (null for DG)
+  const int32_t* __restrict__ cell_rank;   // DG gather
+  const int32_t* __restrict__ face_cell;   // face -> ordered cell position
+  const int32_t* __restrict__ face_kind;   // k | (s << 2)
+  const T* __restrict__ face_phi;          // [F][L][D][N]
+  T* __restrict__ out;                     // [F][2L]
+  int nface;
+  int dg;
+};
+
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(Shape<D, N>::CPB * Shape<D, N>::L)
+sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
+  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, FPB = Shape<D, N>::CPB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);
+  T* SC = X + FPB * ND;            // 6 L per face
+  const int tid = threadIdx.x;
+  const int f0 = blockIdx.x * FPB;
+  const int nf = min(FPB, a.nface - f0);
+  for (int r = tid; r < nf * ND; r += blockDim.x) {
+    const int f = r / ND, loc = r - f * ND;
+    const int cell = __ldg(a.face_cell + f0 + f);
+    size_t g;
+    if (a.dg) g = (size_t)__ldg(a.cell_rank + cell) * ND + loc;
+    else g = (size_t)__ldg(a.lines + (size_t)cell * L + loc / N) + (loc % N);
+    X[r] = __ldg(a.x + g);
+  }
+  __syncthreads();
+  const int fl = tid / L, tl = tid - fl * L;
+  const bool act = fl < nf;
+  const int f = f0 + (act ? fl : 0);
+  const int kind = act ? __ldg(a.face_kind + f) : 0;
+  const int k = kind & 3, s = kind >> 2;
+  const T* Xf = X + fl * ND;
+  T* sc = SC + fl * 6 * L;
+  T* Td = sc;
+  T* Da = sc + L;
+  T* val = sc + 2 * L;
+  T* grd = sc + 3 * L;
+  T* Va = sc + 4 * L;
+  T* Ga = sc + 5 * L;
+  int sk, sa, sb;
+  if (D == 2) {
+    sk = (k == 0) ? 1 : N;
+    sa = (k == 0) ? N : 1;
+    sb = 0;
+  } else {
+    sk = (k == 0) ? 1 : (k == 1 ? N : N * N);
+    sa = (k == 0) ? N : 1;
+    sb = (k == 2) ? N : N * N;
+  }
+  const int kend = s ? (N - 1) : 0;
+  const T sg = s ? T(1) : T(-1);
+  const int bt = (tl % N) * sa + (D == 3 ? (tl / N) * sb : 0);
+
+  // 1. normal-derivative trace at the tangential nodes (the value trace u(x~_q)
+  //    does not enter the operator: only E u at the shifted point does)
+  if (act) {
+    T dsum = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) dsum = fma(s ? t.D1[j] : t.D0[j], Xf[j * sk + bt], dsum);
+    Td[tl] = dsum;
+  }
+  __syncthreads();
+  // 2. to the tangential Gauss points
+  T dg = T(0);
+  if (D == 3) {
+    if (act) {
+      const int qa = tl % N, jb = tl / N;
+      T dv = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) dv = fma(t.S[qa][j], Td[j + N * jb], dv);
+      Da[tl] = dv;
+    }
+    __syncthreads();
+    if (act) {
+      const int qa = tl % N, qb = tl / N;
+#pragma unroll
+      for (int j = 0; j < N; ++j) dg = fma(t.S[qb][j], Da[qa + N * j], dg);
+    }
+  } else {
+    if (act) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) dg = fma(t.S[tl][j], Td[j], dg);
+    }
+  }
+  // 3. point evaluation at the shifted point, pointwise integrands
+  if (act) {
+    const T* pq = a.face_phi + ((size_t)f * L + tl) * D * N;
+    T p0[N], p1[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      p0[j] = __ldg(pq + j);
+      p1[j] = __ldg(pq + N + j);
+    }
+    T e = T(0);
+    if (D == 3) {
+      T p2[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) p2[j] = __ldg(pq + 2 * N + j);
+#pragma unroll
+      for (int j2 = 0; j2 < N; ++j2) {
+        T s1 = T(0);
+#pragma unroll
+        for (int j1 = 0; j1 < N; ++j1) {
+          T s0 = T(0);
+#pragma unroll
+          for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xf[j0 + N * j1 + N * N * j2], s0);
+          s1 = fma(p1[j1], s0, s1);
+        }
+        e = fma(p2[j2], s1, e);
+      }
+    } else {
+#pragma unroll
+      for (int j1 = 0; j1 < N; ++j1) {
+        T s0 = T(0);
+#pragma unroll
+        for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xf[j0 + N * j1], s0);
+        e = fma(p1[j1], s0, e);
+      }
+    }
+    const T W = t.W[tl];
+    val[tl] = W * (t.sigma * e - sg * t.h_inv * dg);
+    grd[tl] = -W * e * sg * t.h_inv;
+  }
+  __syncthreads();
+  // 4. transposed interpolation back to the tangential nodes
+  T rv = T(0), rg = T(0);
+  if (D == 3) {
+    if (act) {
+      const int ja = tl % N, qb = tl / N;
+      T v1 = T(0), v2 = T(0);
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        v1 = fma(t.S[q][ja], val[q + N * qb], v1);
+        v2 = fma(t.S[q][ja], grd[q + N * qb], v2);
+      }
+      Va[tl] = v1;
+      Ga[tl] = v2;
+    }
+    __syncthreads();
+    if (act) {
+      const int ja = tl % N, jb = tl / N;
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        rv = fma(t.S[q][jb], Va[ja + N * q], rv);
+        rg = fma(t.S[q][jb], Ga[ja + N * q], rg);
+      }
+    }
+  } else {
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        rv = fma(t.S[q][tl], val[q], rv);
+        rg = fma(t.S[q][tl], grd[q], rg);
+      }
+    }
+  }
+  if (act) {
+    a.out[(size_t)f * 2 * L + tl] = rv;
+    a.out[(size_t)f * 2 * L + L + tl] = rg;
+  }
+}
+
+template <typename T, int D, int N>
+static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
+                          cudaStream_t st) {
+  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, FPB = Shape<D, N>::CPB;
+  if (dd.nface == 0) return cudaSuccess;
+  const KTab<T> t = make_ktab<T>(hp);
+  FaceArgs<T> a;
+  a.x = x;
+  a.lines = dd.lines;
+  a.cell_rank = dd.cell_rank;
+  a.face_cell = dd.face_cell;
+  a.face_kind = dd.face_kind;
+  a.face_phi = face_phi_of<T>(dd);
+  a.out = out;
+  a.nface = dd.nface;
+  a.dg = hp.desc.dg;
+  const size_t smem = (size_t)(FPB * ND + FPB * 6 * L) * sizeof(T);
+  sface_kernel<T, D, N><<<(dd.nface + FPB - 1) / FPB, FPB * L, smem, st>>>(a, t);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
+                               cudaStream_t st) {
+#define SBM_CASE(DD, NN) \
+  if (hp.d == DD && hp.n == NN) return face_t<T, DD, NN>(hp, dd, x, out, st);
+  SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
+  SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
+#undef SBM_CASE
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_face_kernel<double>(const HostProblem&, const DeviceData&,
+                                                const double*, double*, cudaStream_t);
+template cudaError_t launch_face_kernel<float>(const HostProblem&, const DeviceData&,
+                                               const float*, float*, cudaStream_t);
+
+}  // namespace sbm

@@ -42,6 +42,13 @@ struct DeviceData {
   int32_t* cell_rank = nullptr;  // [Nc] ordered position -> active-cell rank (DG base)
   int32_t* face_start = nullptr; // [Nc + 1] per ordered cell, range into the ordered face list
   int32_t* face_kind = nullptr;  // [F] k | (s << 2)
+  int32_t* face_cell = nullptr;  // [F] ordered cell position of the face's cell
+  int nface = 0;
+  double* face_out = nullptr;    // [F * 2L] per-face results of the face kernel (scratch)
+  float* face_out32 = nullptr;
+  uint8_t* dof_colours = nullptr;  // CG [n_dofs]: bit c set if a cell of colour c touches the DoF
+  double* ycol = nullptr;        // CG [ncolours * n_dofs] colour accumulation buffers (scratch)
+  float* ycol32 = nullptr;
   double* face_phi = nullptr;    // [F * Q * d * n] phi_j(xi_{q,l}) at the shifted points
   float* face_phi32 = nullptr;   // the same table rounded to FP32
   int32_t* nbr = nullptr;        // DG [Nc * 2d] neighbour rank per (k, s), -1 = surrogate
@@ -67,6 +74,19 @@ struct CellLaunch {
   int threads;      // block size
 };
 CellLaunch cell_launch_shape(int d, int n);
+
+template <typename T> inline T* ycol_of(const DeviceData& dd);
+template <> inline double* ycol_of<double>(const DeviceData& dd) { return dd.ycol; }
+template <> inline float* ycol_of<float>(const DeviceData& dd) { return dd.ycol32; }
+
+template <typename T> inline T* face_out_of(const DeviceData& dd);
+template <> inline double* face_out_of<double>(const DeviceData& dd) { return dd.face_out; }
+template <> inline float* face_out_of<float>(const DeviceData& dd) { return dd.face_out32; }
+
+// All surrogate faces into the per-face scratch (face_kernel.cu).
+template <typename T>
+cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
+                               cudaStream_t st);
 
 template <typename T> inline const T* face_phi_of(const DeviceData& dd);
 template <> inline const double* face_phi_of<double>(const DeviceData& dd) { return dd.face_phi; }
