@@ -159,6 +159,35 @@ enum { SBM_FACE_FP32 = 0, SBM_FACE_TF32 = 1, SBM_FACE_BF16 = 2 };
 int sbm_apply_f32(sbm_problem* prob, const float* x, float* y, int face_mode, void* stream);
 
 /*
+ * sbm_apply_f64 for callers that cannot allocate device memory when they
+ * apply the operator (the paper has no counterpart: this is a library
+ * convenience).  Some callers cannot call cudaMalloc at that point -- code
+ * that runs while another component captures a CUDA graph into a memory
+ * pool, real-time loops whose allocator is frozen after start-up, or host
+ * frameworks that only hand out fixed buffers.  This entry point allocates
+ * nothing: the apply's scratch (per-face results and per-colour accumulation
+ * buffers) lives in one static device array of 64 MiB that every GPU loading
+ * the library holds until the process exits.  The problem's set-up data
+ * still comes from sbm_setup_face_data; the caller passes x and y (device,
+ * n_dofs doubles, not overlapping) as for sbm_apply_f64, and gets the same y.
+ * Limits and behaviour:
+ *  - continuous Galerkin problems only (SBM_ERR_UNSUPPORTED for DG);
+ *  - the scratch needed, 2^d * n_dofs * 8 bytes plus the per-face results,
+ *    must fit in 64 MiB (about 1 M DoFs in 3D, 2 M in 2D); larger
+ *    problems get SBM_ERR_ARG with the byte counts in sbm_last_error_detail;
+ *  - the current device must be the problem's device (SBM_ERR_STATE);
+ *  - the first call on a device looks the array's address up
+ *    (cudaGetSymbolAddress) with that device current and caches it: make
+ *    that first call before any stream capture;
+ *  - every call uses the same array: two calls whose work overlaps on the
+ *    GPU (different streams, or different problems on one device) race.
+ *    Nothing in the array needs clearing between calls.
+ * Asynchronous on stream.  Errors: SBM_ERR_ARG, SBM_ERR_STATE,
+ * SBM_ERR_UNSUPPORTED, SBM_ERR_CUDA.
+ */
+int sbm_apply_f64_noalloc(sbm_problem* prob, const double* x, double* y, void* stream);
+
+/*
  * The diagonal of A (FP64, device array of n_dofs), for Jacobi scaling.
  * Asynchronous on stream.
  */

@@ -57,6 +57,7 @@ _SIGS = {
                                            ctypes.c_void_p]),
     "sbm_apply_f64": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "sbm_apply_f64_host": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "sbm_apply_f64_noalloc": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "sbm_diagonal": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "sbm_apply_f32": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_int, ctypes.c_void_p]),
     "sbm_cg": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -182,6 +183,11 @@ def sbm_apply_f64(handle: int, x, y, stream=None) -> None:
 def sbm_apply_f64_host(handle: int, x_host, y_host, stream=None) -> None:
     _check(lib().sbm_apply_f64_host(handle, _ptr(x_host), _ptr(y_host), _stream(stream)),
            "sbm_apply_f64_host")
+
+
+def sbm_apply_f64_noalloc(handle: int, x, y, stream=None) -> None:
+    _check(lib().sbm_apply_f64_noalloc(handle, _ptr(x), _ptr(y), _stream(stream)),
+           "sbm_apply_f64_noalloc")
 
 
 def sbm_diagonal(handle: int, diag, stream=None) -> None:

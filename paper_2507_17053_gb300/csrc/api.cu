@@ -222,6 +222,9 @@ err:
                                         : cuda_fail(e, "upload");
 }
 
+int sbm_fail_detail(int code, const std::string& msg) { return fail(code, msg); }
+int sbm_cuda_fail_detail(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+
 }  // namespace sbm
 
 using namespace sbm;

@@ -162,6 +162,48 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T
   return cudaSuccess;
 }
 
+// The same three launches with caller-provided scratch: per-face results `fo`
+// ([F][2L]) and colour buffers `ycol` ([ncolours][n_dofs]).
+template <typename T, int D, int N>
+static cudaError_t launch_scratch_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                                    T* fo, T* ycol, cudaStream_t st) {
+  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, CPB = Shape<D, N>::CPB;
+  const KTab<T> t = make_ktab<T>(hp);
+  const size_t smem = (size_t)(5 * CPB * ND) * sizeof(T);
+  cudaError_t err;
+  if (dd.nface > 0 && (err = launch_face_kernel<T>(hp, dd, x, fo, st)) != cudaSuccess) return err;
+  CgArgs<T> a;
+  a.x = x;
+  a.ycol = ycol;
+  a.lines = dd.lines;
+  a.face_start = dd.face_start;
+  a.face_kind = dd.face_kind;
+  a.face_out = fo;
+  a.n_dofs = hp.n_dofs;
+  a.ncell = dd.col_start[dd.ncolours];
+  for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
+  cg_apply_kernel<T, D, N><<<(a.ncell + CPB - 1) / CPB, CPB * L, smem, st>>>(a, t);
+  const int64_t n = hp.n_dofs;
+  const int ag = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  assemble_kernel<T><<<ag, 256, 0, st>>>(ycol, dd.dof_colours, y, n, dd.ncolours);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                                    T* face_scratch, T* colour_scratch, cudaStream_t st) {
+#define SBM_CASE(DD, NN)                                                                    \
+  if (hp.d == DD && hp.n == NN)                                                             \
+    return launch_scratch_t<T, DD, NN>(hp, dd, x, y, face_scratch, colour_scratch, st);
+  SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
+  SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
+#undef SBM_CASE
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_cg_apply_scratch<double>(const HostProblem&, const DeviceData&,
+                                                     const double*, double*, double*, double*,
+                                                     cudaStream_t);
+
 template <typename T>
 cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                             cudaStream_t st, Profiler* prof) {

@@ -75,6 +75,10 @@ struct CellLaunch {
 };
 CellLaunch cell_launch_shape(int d, int n);
 
+// Record an error detail for sbm_last_error_detail() and return the code.
+int sbm_fail_detail(int code, const std::string& msg);
+int sbm_cuda_fail_detail(cudaError_t e, const char* where);
+
 template <typename T> inline T* ycol_of(const DeviceData& dd);
 template <> inline double* ycol_of<double>(const DeviceData& dd) { return dd.ycol; }
 template <> inline float* ycol_of<float>(const DeviceData& dd) { return dd.ycol32; }
@@ -96,6 +100,11 @@ template <> inline const float* face_phi_of<float>(const DeviceData& dd) { retur
 template <typename T>
 cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                             cudaStream_t st, Profiler* prof);
+// Apply, CG, with caller-provided scratch (per-face results [F][2L] and the
+// colour buffers [ncolours][n_dofs]) instead of the problem's own.
+template <typename T>
+cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                                    T* face_scratch, T* colour_scratch, cudaStream_t st);
 // Apply, DG: one launch.
 template <typename T>
 cudaError_t launch_dg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
