@@ -34,6 +34,7 @@ import synthetic as S  # noqa: E402
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (CUDA cores) nominal dense rate
 L2_BYTES = 129 * 1024 * 1024
+REF_BUDGET_S = 90.0              # wall-clock budget of the --impl reference run
 
 
 def parse():
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=S.SPHERE_3D_Q4.name)
+    ap.add_argument("--skip-cpu-baseline", action="store_true",
+                    help="leave out the oracle timing (profiling runs)")
     return ap.parse_args()
 
 
@@ -52,19 +55,21 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}; choose from {sorted(S.WORKLOADS)}")
 
 
-def flops_per_apply(d, p, n_cells, n_sfaces):
-    """Floating-point operations of one apply as the kernels compute it.
-
-    Cell term: 7 (3D) or 4 (2D) one-dimensional sweeps of n^(d+1) FMAs.
-    Surrogate face: point evaluation n^(2d-1) + n^(2d-2) + ... FMAs plus
-    11 n^d FMAs of sum-factorised traces and integration (counted per face).
-    """
+def cell_flops(d, p, n_cells):
+    """FLOPs of the cell kernel per apply: 7 (3D) or 4 (2D) one-dimensional
+    sweeps of n^(d+1) FMAs per cell (the tensor-product evaluation of the exact
+    cell stiffness, Algorithm 1)."""
     n = p + 1
-    sweeps = 7 if d == 3 else 4
-    cell = 2 * sweeps * n ** (d + 1)
-    pe = n ** (2 * d - 1) + n ** (2 * d - 2) + (n ** d if d == 3 else 0)
-    face = 2 * (pe + 11 * n ** d)
-    return cell * n_cells + face * n_sfaces
+    return 2 * (7 if d == 3 else 4) * n ** (d + 1) * n_cells
+
+
+def face_flops(d, p, n_sfaces):
+    """FLOPs of the surrogate-face kernel per apply: point evaluation
+    n^(2d-1) + n^(2d-2) + n^d FMAs per face (Algorithm 3's dominant step) plus
+    8 n^d FMAs of sum-factorised trace/interpolation/integration and the fold
+    of the face result into the cell (n^d)."""
+    n = p + 1
+    return 2 * (n ** (2 * d - 1) + n ** (2 * d - 2) + n ** d + 9 * n ** d) * n_sfaces
 
 
 def peaks():
@@ -143,20 +148,40 @@ def cpu_baseline(w, O=None, x=None):
 
 
 def run_reference(args, w):
+    """The oracle (element-by-element FP64 definition) on the host cores.
+
+    Each step applies a bounded sample of the workload: a contiguous block of
+    active cells (with their faces), sized so that the whole --steps/--warmup
+    run takes about REF_BUDGET_S seconds; the blocks cycle through the mesh.
+    GDoF/s counts the sample's share of the DoFs (cells in the sample / all
+    cells x n_dofs).
+    """
     rank, world, dist = dist_init(args.gpus)
     if rank != 0:
         return
     from oracle.operator import Problem as OracleProblem
     O = OracleProblem.from_workload(w)
     x = S.random_vector(w.seed, O.n_dofs, w.dist)
+    nc = len(O.mesh.cells)
+    # calibrate: time one block of 1/64 of the cells
+    blk = max(1, nc // 64)
+    t = time.perf_counter()
+    O.apply_cells(x, np.arange(blk))
+    per_cell = (time.perf_counter() - t) / blk
+    total_steps = args.warmup + args.steps
+    m = int(max(1, min(nc, REF_BUDGET_S / total_steps / per_cell)))
     times = []
-    for i in range(args.warmup + args.steps):
+    start = 0
+    for i in range(total_steps):
+        cells = (np.arange(m) + start) % nc
+        start = (start + m) % nc
         t = time.perf_counter()
-        O.apply(x)
+        O.apply_cells(x, cells)
         if i >= args.warmup:
             times.append(time.perf_counter() - t)
     total = sum(times)
-    v = O.n_dofs * len(times) / total / 1e9
+    units = O.n_dofs * m / nc
+    v = units * len(times) / total / 1e9
     line = {
         "impl": "reference", "metric": "GDoF/s per operator apply (FP64)", "value": v,
         "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -164,10 +189,81 @@ def run_reference(args, w):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n_dofs": O.n_dofs},
         "cpu_baseline": {"value": v, "unit": "GDoF/s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": f"{len(times)} full EBE applies of {w.name}"},
+                         "sample": f"each step: {m} of {nc} active cells (with their faces) "
+                                   f"of {w.name}, EBE"},
         "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def time_applies(P, fn, x, y, steps, warmup, st, dist=None, dev=None, clocks=None):
+    """CUDA-event time of `steps` applies (after `warmup`), per-phase kernel
+    times from the library's profiler, max over ranks."""
+    import torch
+
+    import paper_2507_17053_gb300 as G
+    for _ in range(max(3, warmup)):
+        fn(x, y)
+    torch.cuda.synchronize()
+    G.sbm_profile_read(P.handle)
+    G.sbm_profile_enable(P.handle, True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn(x, y)
+    e1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks is not None else None
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    phases, launches = G.sbm_profile_read(P.handle)
+    G.sbm_profile_enable(P.handle, False)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, [p / steps for p in phases], launches, clk
+
+
+def solve_times(G, torch):
+    """Time-to-1e-10 on the 2D workload (disk, CG Q2, N = 32): CG as named,
+    GMRES(100) in FP64, and FP64 iterative refinement with an FP32 GMRES
+    inner solve.  b from u = sin(pi x) sin(pi y)."""
+    w = S.DISK_2D_Q2
+    P = G.Problem.from_workload(w)
+    b = torch.from_numpy(P.rhs(0)).cuda()
+    out = {"workload": w.name, "n_dofs": P.n_dofs, "rtol": 1e-10}
+
+    def timed(f):
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = f(x)
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t
+
+    for _ in range(2):      # first call builds graphs / warms the path
+        (it, rr, ok), dt = timed(lambda x: G.sbm_cg(P.handle, b, x, rtol=1e-10, maxit=2000))
+    out["cg"] = {"converged": ok, "iters": it, "rel_residual": rr, "seconds": dt,
+                 "note": "operator is nonsymmetric (shifted trial functions); CG diverges"}
+    for _ in range(2):
+        (it, rr, ok), dt = timed(lambda x: G.sbm_gmres(P.handle, b, x, rtol=1e-10, maxit=5000,
+                                                       restart=100))
+    out["gmres_fp64"] = {"converged": ok, "iters": it, "rel_residual": rr, "seconds": dt}
+    for _ in range(2):
+        (it, rr, ok, outer), dt = timed(lambda x: G.sbm_solve_ir(
+            P.handle, b, x, rtol=1e-10, max_outer=30, restart=100, inner_rtol=1e-4,
+            inner_maxit=3000))
+    out["ir_fp32_inner"] = {"converged": ok, "inner_iters": it, "outer": outer,
+                            "rel_residual": rr, "seconds": dt}
+    return out
 
 
 def run_ours(args, w):
@@ -183,43 +279,24 @@ def run_ours(args, w):
     x = torch.from_numpy(x_host).to(dev)
     y = torch.empty_like(x)
     st = torch.cuda.current_stream()
+    n = P.n_dofs
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    for _ in range(max(3, args.warmup)):
-        P.apply_f64(x, y)
-    torch.cuda.synchronize()
-    G.sbm_profile_read(P.handle)
-    G.sbm_profile_enable(P.handle, True)
     clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
-        P.apply_f64(x, y)
-    e1.record(st)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    barrier()
-    ms = e0.elapsed_time(e1)
-    kern_ms, launches = G.sbm_profile_read(P.handle)
-    G.sbm_profile_enable(P.handle, False)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, ph, launches, clk = time_applies(P, lambda a, b: P.apply_f64(a, b), x, y, args.steps,
+                                         args.warmup, st, dist, dev, clocks)
+    # FP32 apply of the same operator (the inner operator of the mixed-precision path)
+    x32 = x.float()
+    y32 = torch.empty_like(x32)
+    ms32, ph32, launches32, _ = time_applies(P, lambda a, b: P.apply_f32(a, b), x32, y32,
+                                             args.steps, args.warmup, st, dist, dev)
 
     # end to end through the C ABI with host buffers (H2D + apply + D2H per step)
     xh = torch.from_numpy(x_host).pin_memory()
-    yh = torch.empty(P.n_dofs, dtype=torch.float64).pin_memory()
+    yh = torch.empty(n, dtype=torch.float64).pin_memory()
     e2e_steps = max(3, min(50, args.steps // 10))
     P.apply_f64_host(xh, yh)
-    barrier()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         P.apply_f64_host(xh, yh)
@@ -231,14 +308,15 @@ def run_ours(args, w):
 
     if rank != 0:
         return
-    n = P.n_dofs
     value = world * n * args.steps / (ms * 1e-3) / 1e9
+    value32 = world * n * args.steps / (ms32 * 1e-3) / 1e9
     pk, pk_src = peaks()
-    flops = flops_per_apply(w.dim, w.degree, P.n_cells, P.n_sfaces)
-    per_launch_ms = kern_ms / launches
-    per_apply_kern_ms = kern_ms / args.steps
-    achieved_tf = flops / (per_apply_kern_ms * 1e-3) / 1e12
-    alg_bytes = 16 * n
+    cflops = cell_flops(w.dim, w.degree, P.n_cells)
+    fflops = face_flops(w.dim, w.degree, P.n_sfaces)
+    cell_ms = ph[1]
+    achieved_tf = cflops / (cell_ms * 1e-3) / 1e12
+    step_s = ms / args.steps * 1e-3
+    step32_s = ms32 / args.steps * 1e-3
     line = {
         "metric": "GDoF/s per operator apply (FP64)",
         "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -246,28 +324,39 @@ def run_ours(args, w):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n_dofs": n, "n_cells": P.n_cells,
                    "n_sfaces": P.n_sfaces, "degree": w.degree, "dim": w.dim,
-                   "l2": f"inputs larger than L2: x and y {2 * 8 * n / 1e6:.0f} MB > 129 MB"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": f"inputs larger than L2: x, y, colour buffers and tables "
+                         f"{(2 * 8 * n + 8 * 8 * n) / 1e6:.0f} MB > 129 MB"},
         "e2e": {"value": world * n * e2e_steps / e2e_s / 1e9, "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
                      "traffic": None,
-                     "kernel": "cg_apply_f64_kernel (all colour launches of one apply)",
-                     "flops_per_apply": flops, "kernel_ms_per_apply": per_apply_kern_ms,
-                     "kernel_ms_per_launch": per_launch_ms,
-                     "peak_note": "FP64 nominal 1.25 TFLOP/s (FMA microbenchmark: 1.007)",
-                     "hbm": {"achieved_gbs": alg_bytes / (ms / args.steps * 1e-3) / 1e9,
+                     "kernel": f"cg_apply_kernel<double,{w.dim},{w.degree + 1}> (cell kernel)",
+                     "flops_per_launch": cflops, "launches_per_step": 1,
+                     "kernel_ms_per_launch": cell_ms,
+                     "peak_note": "FP64 nominal 1.25 TFLOP/s; FP64 FMA microbenchmark 1.007",
+                     "phases_ms_per_step": {"face": ph[0], "cell": ph[1], "assembly": ph[2]},
+                     "face_kernel_tflops": fflops / (ph[0] * 1e-3) / 1e12 if ph[0] > 0 else None,
+                     "hbm": {"bytes_per_dof": 16,
+                             "achieved_gbs": 16 * n / step_s / 1e9,
                              "peak_gbs": pk.get("hbm_gbs"), "peak_src": pk_src,
-                             "frac": alg_bytes / (ms / args.steps * 1e-3) / 1e9 / pk["hbm_gbs"],
-                             "bytes_per_dof": 16}},
+                             "frac": 16 * n / step_s / 1e9 / pk["hbm_gbs"]}},
+        "fp32_apply": {"value": value32, "unit": "GDoF/s", "ms_per_step": ms32 / args.steps,
+                       "launches": launches32,
+                       "phases_ms_per_step": {"face": ph32[0], "cell": ph32[1],
+                                              "assembly": ph32[2]},
+                       "cell_tflops": cflops / (ph32[1] * 1e-3) / 1e12,
+                       "hbm_frac_8B_per_dof": 8 * n / step32_s / 1e9 / pk["hbm_gbs"]},
         "clocks": clk,
     }
-    if world == 1 or rank == 0:
-        try:
-            line["cpu_baseline"] = cpu_baseline(w)
-        except MemoryError:
-            line["cpu_baseline"] = None
+    try:
+        line["solves"] = solve_times(G, torch)
+    except Exception as e:  # noqa: BLE001 -- report, never hide the main number
+        line["solves"] = {"error": str(e)}
+    if not args.skip_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
 
 

@@ -250,15 +250,18 @@ int sbm_rhs(const sbm_problem* prob, int manufactured, double* b_host);
 int sbm_interpolate(const sbm_problem* prob, int manufactured, double* u_host);
 
 /*
- * Kernel timing (diagnostics).  While enabled, every apply records a CUDA
- * event before and after its operator kernels (on the apply's stream, after
- * the y = 0 fill).  sbm_profile_read waits for the recorded events, returns
- * the summed kernel time in milliseconds and the number of operator kernel
- * launches since the previous read, and resets both.  Either output may be
- * NULL.  Enabling adds two event records per apply and nothing else.
+ * Kernel timing (diagnostics).  While enabled, every sbm_apply_f64 /
+ * sbm_apply_f32 records CUDA events on its stream at the boundaries of its
+ * three phases: the surrogate-face kernel, the cell kernel (the DG kernel
+ * for DG), and the assembly of the colour buffers (none for DG).
+ * sbm_profile_read waits for the recorded events and returns, summed over
+ * the applies since the previous read, the milliseconds of each phase in
+ * phase_ms[0..2] (face, cell, assembly) and the number of kernel launches,
+ * then resets.  Either output may be NULL.  Enabling adds four event records
+ * per apply and nothing else.
  */
 int sbm_profile_enable(sbm_problem* prob, int on);
-int sbm_profile_read(sbm_problem* prob, double* kernel_ms, int64_t* launches);
+int sbm_profile_read(sbm_problem* prob, double* phase_ms, int64_t* launches);
 
 /* Human-readable name of a status code (static string). */
 const char* sbm_error_string(int status);

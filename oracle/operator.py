@@ -130,6 +130,34 @@ class Problem:
                 y += np.bincount(dd.ravel(), weights=Yi.ravel(), minlength=self.n_dofs)
         return y
 
+    def apply_cells(self, x, cells):
+        """The contributions of the given active cells (and their surrogate and
+        DG interior faces) to y = A x: the same EBE arithmetic as apply(),
+        restricted to a subset of the cells (a bounded sample of the work)."""
+        x = np.asarray(x, dtype=np.float64)
+        cells = np.asarray(cells)
+        dm = self.dofmap
+        Y = x[dm[cells]] @ self.A_cell.T
+        y = np.bincount(dm[cells].ravel(), weights=Y.ravel(), minlength=self.n_dofs)
+        own = np.zeros(len(dm), dtype=bool)
+        own[cells] = True
+        fsel = np.nonzero(own[self.mesh.sfaces[:, 0]])[0]
+        for s in range(0, len(fsel), 1024):
+            part = fsel[s:s + 1024]
+            Af = self.face_matrices(part)
+            fd = dm[self.mesh.sfaces[part, 0]]
+            Yf = np.einsum("fij,fj->fi", Af, x[fd])
+            y += np.bincount(fd.ravel(), weights=Yf.ravel(), minlength=self.n_dofs)
+        if self.dg and len(self.mesh.ifaces):
+            B = self.dg_blocks()
+            for k in range(self.d):
+                sel = (self.mesh.ifaces[:, 1] == k) & own[self.mesh.ifaces[:, 0]]
+                dd = np.concatenate([dm[self.mesh.ifaces[sel, 0]],
+                                     dm[self.mesh.ifaces[sel, 2]]], axis=1)
+                Yi = x[dd] @ B[k].T
+                y += np.bincount(dd.ravel(), weights=Yi.ravel(), minlength=self.n_dofs)
+        return y
+
     def apply_rows(self, x, rows):
         """(A x)[rows] computed from the local matrices touching those rows only."""
         rows = np.asarray(rows)

@@ -79,7 +79,7 @@ _SIGS = {
     "sbm_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sbm_interpolate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sbm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
-    "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), _c_i64p]),
+    "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_i64p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sbm_last_error_detail": (ctypes.c_char_p, []),
 }
@@ -248,10 +248,11 @@ def sbm_profile_enable(handle: int, on: bool) -> None:
     _check(lib().sbm_profile_enable(handle, int(bool(on))), "sbm_profile_enable")
 
 
-def sbm_profile_read(handle: int) -> tuple[float, int]:
-    ms, n = ctypes.c_double(), ctypes.c_int64()
-    _check(lib().sbm_profile_read(handle, ctypes.byref(ms), ctypes.byref(n)), "sbm_profile_read")
-    return ms.value, n.value
+def sbm_profile_read(handle: int) -> tuple[list, int]:
+    """([face_ms, cell_ms, assembly_ms] summed since the last read, kernel launches)."""
+    ms, n = (ctypes.c_double * 3)(), ctypes.c_int64()
+    _check(lib().sbm_profile_read(handle, ms, ctypes.byref(n)), "sbm_profile_read")
+    return list(ms), n.value
 
 
 class Problem:

@@ -53,23 +53,16 @@ KTab<T> make_ktab(const HostProblem& hp) {
 template KTab<double> make_ktab<double>(const HostProblem&);
 template KTab<float> make_ktab<float>(const HostProblem&);
 
-cudaError_t Profiler::begin(cudaStream_t st) {
-  if (used + 2 > ev.size()) {
-    for (int i = 0; i < 64; ++i) {
+cudaError_t Profiler::mark(cudaStream_t st) {
+  if (used + 1 > ev.size()) {
+    for (int i = 0; i < 64 * kMarks; ++i) {
       cudaEvent_t e;
       cudaError_t err = cudaEventCreate(&e);
       if (err != cudaSuccess) return err;
       ev.push_back(e);
     }
   }
-  return cudaEventRecord(ev[used], st);
-}
-
-cudaError_t Profiler::end(cudaStream_t st, int nlaunch) {
-  cudaError_t err = cudaEventRecord(ev[used + 1], st);
-  used += 2;
-  launches += nlaunch;
-  return err;
+  return cudaEventRecord(ev[used++], st);
 }
 
 void Profiler::release() {
@@ -470,19 +463,22 @@ int sbm_profile_enable(sbm_problem* prob, int on) {
   return SBM_OK;
 }
 
-int sbm_profile_read(sbm_problem* prob, double* kernel_ms, int64_t* launches) {
+int sbm_profile_read(sbm_problem* prob, double* phase_ms, int64_t* launches) {
   if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
   Profiler& pf = prob->prof;
-  double total = 0.0;
-  for (size_t i = 0; i + 1 < pf.used; i += 2) {
-    cudaError_t e = cudaEventSynchronize(pf.ev[i + 1]);
+  double tot[3] = {0.0, 0.0, 0.0};
+  for (size_t g = 0; g + Profiler::kMarks <= pf.used; g += Profiler::kMarks) {
+    cudaError_t e = cudaEventSynchronize(pf.ev[g + Profiler::kMarks - 1]);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-    float ms = 0.f;
-    e = cudaEventElapsedTime(&ms, pf.ev[i], pf.ev[i + 1]);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
-    total += ms;
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, pf.ev[g + k], pf.ev[g + k + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+      tot[k] += ms;
+    }
   }
-  if (kernel_ms) *kernel_ms = total;
+  if (phase_ms)
+    for (int k = 0; k < 3; ++k) phase_ms[k] = tot[k];
   if (launches) *launches = pf.launches;
   pf.used = 0;
   pf.launches = 0;

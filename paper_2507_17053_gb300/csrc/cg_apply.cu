@@ -135,12 +135,14 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T
   T* fo = face_out_of<T>(dd);
   T* ycol = ycol_of<T>(dd);
   cudaError_t err;
-  if (prof && prof->on && (err = prof->begin(st)) != cudaSuccess) return err;
+  const bool pr = prof && prof->on;
+  if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   int nlaunch = 0;
   if (dd.nface > 0) {
     if ((err = launch_face_kernel<T>(hp, dd, x, fo, st)) != cudaSuccess) return err;
     nlaunch++;
   }
+  if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   CgArgs<T> a;
   a.x = x;
   a.ycol = ycol;
@@ -153,12 +155,16 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T
   for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
   cg_apply_kernel<T, D, N><<<(a.ncell + CPB - 1) / CPB, CPB * L, smem, st>>>(a, t);
   nlaunch++;
+  if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   const int64_t n = hp.n_dofs;
   const int ag = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
   assemble_kernel<T><<<ag, 256, 0, st>>>(ycol, dd.dof_colours, y, n, dd.ncolours);
   nlaunch++;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  if (prof && prof->on) return prof->end(st, nlaunch);
+  if (pr) {
+    prof->count(nlaunch);
+    return prof->mark(st);
+  }
   return cudaSuccess;
 }
 

@@ -333,17 +333,23 @@ static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x,
   a.face_out = face_out_of<T>(dd);
   a.ncell = dd.col_start[dd.ncolours];
   a.sigma_f = (T)hp.sigma_f;
-  if (prof && prof->on && (err = prof->begin(st)) != cudaSuccess) return err;
+  const bool pr = prof && prof->on;
+  if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   int nlaunch = 1;
   if (dd.nface > 0) {
     if ((err = launch_face_kernel<T>(hp, dd, x, face_out_of<T>(dd), st)) != cudaSuccess)
       return err;
     nlaunch++;
   }
+  if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   const int grid = (a.ncell + CPB - 1) / CPB;
   dg_apply_kernel<T, D, N><<<grid, CPB * L, smem, st>>>(a, t);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  if (prof && prof->on) return prof->end(st, nlaunch);
+  if (pr) {
+    prof->count(nlaunch);
+    if ((err = prof->mark(st)) != cudaSuccess) return err;   // cell phase ends
+    return prof->mark(st);                                   // no assembly phase
+  }
   return cudaSuccess;
 }
 

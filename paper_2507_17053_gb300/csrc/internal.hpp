@@ -56,15 +56,17 @@ struct DeviceData {
   double* stage_y = nullptr;
 };
 
-// Optional kernel timing: a pair of CUDA events around the operator kernels
-// of every apply (after the y = 0 memset), read back by sbm_profile_read.
+// Optional kernel timing: CUDA events on the apply's stream at the phase
+// boundaries of every apply (start | face kernel | cell kernel | assembly),
+// read back by sbm_profile_read.
 struct Profiler {
+  static constexpr int kMarks = 4;
   bool on = false;
-  std::vector<cudaEvent_t> ev;   // start/stop pairs
+  std::vector<cudaEvent_t> ev;   // groups of kMarks events
   size_t used = 0;               // events recorded since the last read
   int64_t launches = 0;          // operator kernel launches since the last read
-  cudaError_t begin(cudaStream_t st);
-  cudaError_t end(cudaStream_t st, int nlaunch);
+  cudaError_t mark(cudaStream_t st);   // record the next boundary
+  void count(int nlaunch) { launches += nlaunch; }
   void release();
 };
 

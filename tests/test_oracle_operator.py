@@ -273,3 +273,14 @@ def test_workload_sizes_disk():
     for c, k, s in P.mesh.sfaces:
         nsum[k] += 2 * s - 1
     assert np.all(nsum == 0)
+
+
+def test_apply_cells_partition_sums_to_apply():
+    """The cell-subset apply (used to time bounded samples) partitions A x."""
+    for case in TINY:
+        P = _prob(case)
+        x = S.uniform_pm1(3, P.n_dofs)
+        nc = len(P.mesh.cells)
+        parts = np.array_split(np.arange(nc), 3)
+        y = sum(P.apply_cells(x, c) for c in parts)
+        np.testing.assert_allclose(y, P.apply(x), atol=1e-12 * np.abs(P.apply(x)).max())
