@@ -56,11 +56,24 @@ def workload(name):
 
 
 def cell_flops(d, p, n_cells):
-    """FLOPs of the cell kernel per apply: 7 (3D) or 4 (2D) one-dimensional
-    sweeps of n^(d+1) FMAs per cell (the tensor-product evaluation of the exact
-    cell stiffness, Algorithm 1)."""
+    """FLOPs the cell kernel executes per apply (an FMA counts 2, an add 1).
+
+    The exact cell stiffness is applied as 7 (3D) or 4 (2D) one-dimensional
+    matrix applications per line of the tile (Algorithm 1 in tensor-product
+    form).  For n = p+1 >= 5 each application uses the even/odd split of the
+    centrosymmetric 1D matrices: ((n+1)/2)^2 + (n/2)^2 FMAs, plus 2 (n/2)
+    additions for every folded input line and every unfolded output line
+    (3D: 5 folds and 5 unfolds per line triple; 2D: 3 and 3)."""
     n = p + 1
-    return 2 * (7 if d == 3 else 4) * n ** (d + 1) * n_cells
+    lines = n ** (d - 1)
+    mats = 7 if d == 3 else 4
+    if n >= 5:
+        h, he = n // 2, (n + 1) // 2
+        fma = mats * (he * he + h * h)
+        adds = (10 if d == 3 else 6) * 2 * h
+    else:
+        fma, adds = mats * n * n, 0
+    return (2 * fma + adds) * lines * n_cells
 
 
 def face_flops(d, p, n_sfaces):

@@ -48,6 +48,19 @@ KTab<T> make_ktab(const HostProblem& hp) {
   }
   t.h_inv = (T)(1.0 / hp.h);
   t.sigma = (T)hp.sigma;
+  auto fold = [n](const double (&A)[kMaxN][kMaxN], double scale, Folded<T>* f) {
+    const int H = n / 2, HE = (n + 1) / 2;
+    for (int i = 0; i < HE; ++i)
+      for (int j = 0; j < HE; ++j) {
+        const bool mid = (n & 1) && j == n / 2;
+        f->E[i][j] = (T)(scale * (mid ? A[i][j] : 0.5 * (A[i][j] + A[i][n - 1 - j])));
+        if (i < H && j < H) f->O[i][j] = (T)(scale * 0.5 * (A[i][j] - A[i][n - 1 - j]));
+      }
+  };
+  fold(tb.M, 1.0, &t.fM);
+  fold(tb.K, 1.0, &t.fK);
+  fold(tb.M, hd2, &t.fMh);
+  fold(tb.K, hd2, &t.fKh);
   return t;
 }
 template KTab<double> make_ktab<double>(const HostProblem&);

@@ -112,18 +112,22 @@ cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
   }
 }
 
-// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order
+// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order.  One DoF
+// per thread (all of its loads in flight at once); the buffers are read once.
 template <typename T>
 __global__ void assemble_kernel(const T* __restrict__ ycol, const uint8_t* __restrict__ mask,
                                 T* __restrict__ y, int64_t n, int ncol) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned m = __ldg(mask + i);
-    T acc = T(0);
-    for (int c = 0; c < ncol; ++c)
-      if (m & (1u << c)) acc += __ldg(ycol + (size_t)c * n + i);
-    y[i] = acc;
-  }
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned m = __ldg(mask + i);
+  T v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    v[c] = (c < ncol && (m & (1u << c))) ? __ldcs(ycol + (size_t)c * n + i) : T(0);
+  T acc = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc += v[c];
+  __stcs(y + i, acc);
 }
 
 template <typename T, int D, int N>
@@ -157,8 +161,8 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T
   nlaunch++;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   const int64_t n = hp.n_dofs;
-  const int ag = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  assemble_kernel<T><<<ag, 256, 0, st>>>(ycol, dd.dof_colours, y, n, dd.ncolours);
+  assemble_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ycol, dd.dof_colours, y, n,
+                                                                   dd.ncolours);
   nlaunch++;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (pr) {
@@ -190,8 +194,8 @@ static cudaError_t launch_scratch_t(const HostProblem& hp, const DeviceData& dd,
   for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
   cg_apply_kernel<T, D, N><<<(a.ncell + CPB - 1) / CPB, CPB * L, smem, st>>>(a, t);
   const int64_t n = hp.n_dofs;
-  const int ag = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  assemble_kernel<T><<<ag, 256, 0, st>>>(ycol, dd.dof_colours, y, n, dd.ncolours);
+  assemble_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ycol, dd.dof_colours, y, n,
+                                                                   dd.ncolours);
   return cudaGetLastError();
 }
 

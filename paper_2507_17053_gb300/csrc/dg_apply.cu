@@ -14,7 +14,7 @@
 //    face kernel (face_kernel.cu) and folded in here from its scratch.
 // Face arithmetic is sum-factorised: nodal traces -> tangential Gauss points
 // -> pointwise terms -> transposed interpolation -> added to the cell result.
-#include "internal.hpp"
+#include "sweeps.cuh"
 
 namespace sbm {
 
@@ -68,90 +68,11 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
   T* Xc = X + c * ND;
   T* R = A + c * ND;
   {
-    // cell term, then park the x-line result in R (A is free after the syncs)
-    constexpr int NN = N;
-    T out[NN];
-    if (act) {
-      if (D == 3) {
-        const int base = c * ND + (tl % N) + N * (tl / N);
-        T v[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = X[base + N * N * j];
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          T s0 = T(0), s1 = T(0);
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            s0 = fma(t.M[m][j], v[j], s0);
-            s1 = fma(t.K[m][j], v[j], s1);
-          }
-          A[base + N * N * m] = s0;
-          E[base + N * N * m] = s1;
-        }
-      } else {
-        const int base = c * ND + tl;
-        T v[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) v[j] = X[base + N * j];
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          T s0 = T(0), s1 = T(0);
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            s0 = fma(t.M[m][j], v[j], s0);
-            s1 = fma(t.K[m][j], v[j], s1);
-          }
-          A[base + N * m] = s0;
-          E[base + N * m] = s1;
-        }
-      }
-    }
-    __syncthreads();
-    if (D == 3) {
-      if (act) {
-        const int base = c * ND + (tl % N) + N * N * (tl / N);
-        T va[N], ve[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          va[j] = A[base + N * j];
-          ve[j] = E[base + N * j];
-        }
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          T b = T(0), g = T(0);
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            b = fma(t.M[m][j], va[j], b);
-            g = fma(t.K[m][j], va[j], g);
-            g = fma(t.M[m][j], ve[j], g);
-          }
-          B[base + N * m] = b;
-          G[base + N * m] = g;
-        }
-      }
-      __syncthreads();
-    }
-    if (act) {
-      const T* P = (D == 3) ? B : A;
-      const T* Q = (D == 3) ? G : E;
-      const int base = c * ND + N * tl;
-      T vb[N], vg[N];
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        vb[j] = P[base + j];
-        vg[j] = Q[base + j];
-      }
-#pragma unroll
-      for (int m = 0; m < N; ++m) {
-        T o = T(0);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          o = fma(t.Kh[m][j], vb[j], o);
-          o = fma(t.Mh[m][j], vg[j], o);
-        }
-        out[m] = o;
-      }
-    }
+    // cell term (Algorithm 1), then park the x-line result in R (A is free
+    // once every thread is past the sweeps)
+    T out[N];
+    if (D == 3) cell_sweeps_3d<T, N>(t, X, A, E, B, G, c, tl, act, out);
+    else cell_sweeps_2d<T, N>(t, X, A, E, c, tl, act, out);
     __syncthreads();
     if (act) {
 #pragma unroll

@@ -13,6 +13,20 @@ namespace sbm {
 
 // 1D operator tables handed to kernels by value (kernel parameter space is a
 // constant bank: every FMA with a table operand reads it for free).
+constexpr int kMaxH = (kMaxN + 1) / 2;
+
+// A centrosymmetric n x n matrix (A[i][j] = A[n-1-i][n-1-j]) split into its
+// even and odd parts: with e_j = v_j + v_{n-1-j}, o_j = v_j - v_{n-1-j} (and
+// e_mid = v_mid for odd n), s_i = sum_j E[i][j] e_j, d_i = sum_j O[i][j] o_j,
+// the product is y_i = s_i + d_i, y_{n-1-i} = s_i - d_i (y_mid = s_mid), where
+// E[i][j] = (A[i][j] + A[i][n-1-j]) / 2, E[i][mid] = A[i][mid] and
+// O[i][j] = (A[i][j] - A[i][n-1-j]) / 2.
+template <typename T>
+struct Folded {
+  T E[kMaxH][kMaxH];
+  T O[kMaxH][kMaxH];
+};
+
 template <typename T>
 struct KTab {
   T M[kMaxN][kMaxN];     // 1D mass on [0,1]
@@ -25,6 +39,7 @@ struct KTab {
   T W[kMaxN * kMaxN];    // face weights h^(d-1) w_qa w_qb (tangential Gauss index q)
   T h_inv;
   T sigma;
+  Folded<T> fM, fK, fMh, fKh;  // even/odd parts of M, K, Mh, Kh (GLL nodes are symmetric)
 };
 
 template <typename T>

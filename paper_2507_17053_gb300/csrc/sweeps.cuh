@@ -23,6 +23,165 @@ struct Shape {
   static constexpr int CPB = (128 / L) > 0 ? (128 / L) : 1;
 };
 
+// ---- 1D line operations ------------------------------------------------------
+//
+// For n >= 5 the 1D matrices are applied in even/odd form (see Folded): an
+// n x n product costs (n/2)^2 + ((n+1)/2)^2 multiply-adds plus 2n additions
+// instead of n^2, and the folding of an input line is shared by every matrix
+// applied to it.  For n <= 4 the plain product is as cheap and is used.
+
+template <typename T, int N>
+struct LineFold {
+  static constexpr int H = N / 2, HE = (N + 1) / 2;
+  T e[HE];
+  T o[H > 0 ? H : 1];
+  __device__ __forceinline__ explicit LineFold(const T (&v)[N]) {
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      e[j] = v[j] + v[N - 1 - j];
+      o[j] = v[j] - v[N - 1 - j];
+    }
+    if (N & 1) e[H] = v[H];
+  }
+};
+
+template <typename T, int N>
+struct LineAcc {
+  static constexpr int H = N / 2, HE = (N + 1) / 2;
+  T s[HE];
+  T d[H > 0 ? H : 1];
+  __device__ __forceinline__ LineAcc() {
+#pragma unroll
+    for (int i = 0; i < HE; ++i) s[i] = T(0);
+#pragma unroll
+    for (int i = 0; i < H; ++i) d[i] = T(0);
+  }
+  __device__ __forceinline__ void mac(const Folded<T>& A, const LineFold<T, N>& f) {
+#pragma unroll
+    for (int i = 0; i < HE; ++i)
+#pragma unroll
+      for (int j = 0; j < HE; ++j) s[i] = fma(A.E[i][j], f.e[j], s[i]);
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+#pragma unroll
+      for (int j = 0; j < H; ++j) d[i] = fma(A.O[i][j], f.o[j], d[i]);
+  }
+  __device__ __forceinline__ void unfold(T (&y)[N]) const {
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      y[i] = s[i] + d[i];
+      y[N - 1 - i] = s[i] - d[i];
+    }
+    if (N & 1) y[H] = s[H];
+  }
+};
+
+template <int N>
+struct UseFold {
+  static constexpr bool value = N >= 5;
+};
+
+// y = A v
+template <typename T, int N>
+__device__ __forceinline__ void line_apply(const T (&A)[kMaxN][kMaxN], const Folded<T>& F,
+                                           const T (&v)[N], T (&y)[N]) {
+  if constexpr (UseFold<N>::value) {
+    LineFold<T, N> f(v);
+    LineAcc<T, N> acc;
+    acc.mac(F, f);
+    acc.unfold(y);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      T a = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) a = fma(A[m][j], v[j], a);
+      y[m] = a;
+    }
+  }
+}
+
+// y1 = A1 v, y2 = A2 v
+template <typename T, int N>
+__device__ __forceinline__ void line_apply2(const T (&A1)[kMaxN][kMaxN], const Folded<T>& F1,
+                                            const T (&A2)[kMaxN][kMaxN], const Folded<T>& F2,
+                                            const T (&v)[N], T (&y1)[N], T (&y2)[N]) {
+  if constexpr (UseFold<N>::value) {
+    LineFold<T, N> f(v);
+    LineAcc<T, N> a1, a2;
+    a1.mac(F1, f);
+    a2.mac(F2, f);
+    a1.unfold(y1);
+    a2.unfold(y2);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      T a = T(0), b = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        a = fma(A1[m][j], v[j], a);
+        b = fma(A2[m][j], v[j], b);
+      }
+      y1[m] = a;
+      y2[m] = b;
+    }
+  }
+}
+
+// y = A1 v1 + A2 v2
+template <typename T, int N>
+__device__ __forceinline__ void line_apply_sum(const T (&A1)[kMaxN][kMaxN], const Folded<T>& F1,
+                                               const T (&v1)[N], const T (&A2)[kMaxN][kMaxN],
+                                               const Folded<T>& F2, const T (&v2)[N],
+                                               T (&y)[N]) {
+  if constexpr (UseFold<N>::value) {
+    LineFold<T, N> f1(v1), f2(v2);
+    LineAcc<T, N> acc;
+    acc.mac(F1, f1);
+    acc.mac(F2, f2);
+    acc.unfold(y);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      T a = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        a = fma(A1[m][j], v1[j], a);
+        a = fma(A2[m][j], v2[j], a);
+      }
+      y[m] = a;
+    }
+  }
+}
+
+// b = M a, g = K a + M e (phase 2: the input a is folded once)
+template <typename T, int N>
+__device__ __forceinline__ void line_phase2(const KTab<T>& t, const T (&va)[N], const T (&ve)[N],
+                                            T (&b)[N], T (&g)[N]) {
+  if constexpr (UseFold<N>::value) {
+    LineFold<T, N> fa(va), fe(ve);
+    LineAcc<T, N> ab, ag;
+    ab.mac(t.fM, fa);
+    ag.mac(t.fK, fa);
+    ag.mac(t.fM, fe);
+    ab.unfold(b);
+    ag.unfold(g);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      T bb = T(0), gg = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        bb = fma(t.M[m][j], va[j], bb);
+        gg = fma(t.K[m][j], va[j], gg);
+        gg = fma(t.M[m][j], ve[j], gg);
+      }
+      b[m] = bb;
+      g[m] = gg;
+    }
+  }
+}
+
 // ---- cell term -------------------------------------------------------------
 
 // 3D: three phases over z-, y- and x-lines.  `X` holds ncells tiles; the x-line
@@ -33,41 +192,30 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, T* 
   constexpr int ND = N * N * N;
   if (act) {
     const int base = c * ND + (tl % N) + N * (tl / N);      // z-line (j0, j1)
-    T v[N];
+    T v[N], a[N], e[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = X[base + N * N * j];
+    line_apply2<T, N>(t.M, t.fM, t.K, t.fK, v, a, e);
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      T a = T(0), e = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        a = fma(t.M[m][j], v[j], a);
-        e = fma(t.K[m][j], v[j], e);
-      }
-      A[base + N * N * m] = a;
-      E[base + N * N * m] = e;
+      A[base + N * N * m] = a[m];
+      E[base + N * N * m] = e[m];
     }
   }
   __syncthreads();
   if (act) {
     const int base = c * ND + (tl % N) + N * N * (tl / N);  // y-line (j0, j2)
-    T va[N], ve[N];
+    T va[N], ve[N], b[N], g[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       va[j] = A[base + N * j];
       ve[j] = E[base + N * j];
     }
+    line_phase2<T, N>(t, va, ve, b, g);
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      T b = T(0), g = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        b = fma(t.M[m][j], va[j], b);
-        g = fma(t.K[m][j], va[j], g);
-        g = fma(t.M[m][j], ve[j], g);
-      }
-      B[base + N * m] = b;
-      G[base + N * m] = g;
+      B[base + N * m] = b[m];
+      G[base + N * m] = g[m];
     }
   }
   __syncthreads();
@@ -79,16 +227,7 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, T* 
       vb[j] = B[base + j];
       vg[j] = G[base + j];
     }
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-      T o = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        o = fma(t.Kh[m][j], vb[j], o);
-        o = fma(t.Mh[m][j], vg[j], o);
-      }
-      out[m] = o;
-    }
+    line_apply_sum<T, N>(t.Kh, t.fKh, vb, t.Mh, t.fMh, vg, out);
   }
 }
 
@@ -99,19 +238,14 @@ __device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X, T* 
   constexpr int ND = N * N;
   if (act) {
     const int base = c * ND + tl;                           // y-line j0 = tl
-    T v[N];
+    T v[N], a[N], e[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = X[base + N * j];
+    line_apply2<T, N>(t.M, t.fM, t.K, t.fK, v, a, e);
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      T a = T(0), e = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        a = fma(t.M[m][j], v[j], a);
-        e = fma(t.K[m][j], v[j], e);
-      }
-      A[base + N * m] = a;
-      E[base + N * m] = e;
+      A[base + N * m] = a[m];
+      E[base + N * m] = e[m];
     }
   }
   __syncthreads();
@@ -123,16 +257,7 @@ __device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X, T* 
       va[j] = A[base + j];
       ve[j] = E[base + j];
     }
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-      T o = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        o = fma(t.Kh[m][j], va[j], o);
-        o = fma(t.Mh[m][j], ve[j], o);
-      }
-      out[m] = o;
-    }
+    line_apply_sum<T, N>(t.Kh, t.fKh, va, t.Mh, t.fMh, ve, out);
   }
 }
 
