@@ -193,6 +193,47 @@ int sbm_apply_f64_noalloc(sbm_problem* prob, const double* x, double* y, void* s
  */
 int sbm_diagonal(sbm_problem* prob, double* diag, void* stream);
 
+/* ---- batches of problems ------------------------------------------------ */
+typedef struct sbm_batch sbm_batch;
+
+/*
+ * A batch of independent continuous Galerkin problems (any sizes, degrees,
+ * geometries), each with nrhs right-hand sides, applied together: every
+ * problem's right-hand sides go through one launch of each of its kernels
+ * (grid.y = right-hand side), the problems run on a pool of streams, and the
+ * whole batch is one CUDA-graph launch (captured on the first call for a
+ * given set of vector pointers, replayed afterwards).
+ * probs: nprob problems, all set up (sbm_setup_face_data) on the current
+ * device; the batch keeps the pointers (do not destroy a problem before its
+ * batch).  autotune_shapes != 0 times the cell kernel's two tile shapes (128
+ * or 256 threads' worth of cell lines per block) on the largest problem of
+ * every degree and keeps the faster one for all problems of that degree.
+ * Device scratch: nrhs copies of each problem's per-face results and colour
+ * buffers, per precision, allocated on first use.  Synchronous.
+ * Errors: SBM_ERR_ARG, SBM_ERR_STATE, SBM_ERR_UNSUPPORTED (DG problem),
+ * SBM_ERR_OOM, SBM_ERR_CUDA.
+ */
+int sbm_batch_create(sbm_problem* const* probs, int nprob, int nrhs, int autotune_shapes,
+                     sbm_batch** out);
+
+/*
+ * y_k = A_k x_k for every problem k and right-hand side: x[k] and y[k] are
+ * device arrays of nrhs * n_dofs_k values (right-hand side r at offset
+ * r * n_dofs_k), x[k] != y[k].  The same operator and arithmetic as
+ * sbm_apply_f32 / sbm_apply_f64 (bitwise-equal results).  Asynchronous on
+ * stream; two batch applies must not overlap (shared scratch).
+ */
+int sbm_batch_apply_f32(sbm_batch* batch, const float* const* x, float* const* y, void* stream);
+int sbm_batch_apply_f64(sbm_batch* batch, const double* const* x, double* const* y,
+                        void* stream);
+
+/* Tile shape (0 or 1) in use for a problem; override it (drops cached graphs). */
+int sbm_batch_tile_shape(const sbm_batch* batch, int problem, int* variant);
+int sbm_batch_set_tile_shape(sbm_batch* batch, int problem, int variant);
+
+/* Free the batch (not its problems). */
+void sbm_batch_destroy(sbm_batch* batch);
+
 /* ---- solvers (the paper gives none; these drive the operator) ----------- */
 enum { SBM_PRECOND_NONE = 0, SBM_PRECOND_JACOBI = 1 };
 

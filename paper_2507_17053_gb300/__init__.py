@@ -78,6 +78,14 @@ _SIGS = {
                                                               ctypes.c_void_p]),
     "sbm_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sbm_interpolate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sbm_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "sbm_batch_apply_f32": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "sbm_batch_apply_f64": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "sbm_batch_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]),
+    "sbm_batch_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "sbm_batch_destroy": (None, [ctypes.c_void_p]),
     "sbm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_i64p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -253,6 +261,55 @@ def sbm_profile_read(handle: int) -> tuple[list, int]:
     ms, n = (ctypes.c_double * 3)(), ctypes.c_int64()
     _check(lib().sbm_profile_read(handle, ms, ctypes.byref(n)), "sbm_profile_read")
     return list(ms), n.value
+
+
+class Batch:
+    """Owning wrapper around an sbm_batch (the problems must outlive it)."""
+
+    def __init__(self, problems, nrhs, autotune=True):
+        self.problems = list(problems)
+        self.nrhs = nrhs
+        arr = (ctypes.c_void_p * len(self.problems))(*[p.handle for p in self.problems])
+        h = ctypes.c_void_p()
+        _check(lib().sbm_batch_create(arr, len(self.problems), nrhs, int(bool(autotune)),
+                                      ctypes.byref(h)), "sbm_batch_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, xs, ys, stream=None):
+        """ys[k] = A_k xs[k] (tensors of nrhs * n_dofs_k, float32 or float64)."""
+        import torch
+        n = len(self.problems)
+        xa = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ya = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        for p, x, y in zip(self.problems, xs, ys):
+            if x.numel() != p.n_dofs * self.nrhs or y.numel() != x.numel() or x.dtype != y.dtype:
+                raise ValueError("batch vector has the wrong size or dtype")
+        if xs[0].dtype == torch.float32:
+            _check(lib().sbm_batch_apply_f32(self.handle, xa, ya, _stream(stream)),
+                   "sbm_batch_apply_f32")
+        else:
+            _check(lib().sbm_batch_apply_f64(self.handle, xa, ya, _stream(stream)),
+                   "sbm_batch_apply_f64")
+        return ys
+
+    def tile_shape(self, k):
+        v = ctypes.c_int()
+        _check(lib().sbm_batch_tile_shape(self.handle, k, ctypes.byref(v)), "sbm_batch_tile_shape")
+        return v.value
+
+    def set_tile_shape(self, k, variant):
+        _check(lib().sbm_batch_set_tile_shape(self.handle, k, variant), "sbm_batch_set_tile_shape")
 
 
 class Problem:

@@ -37,6 +37,9 @@ struct CgArgs {
   int64_t n_dofs;
   int ncell;                               // all active cells
   int col_start[9];                        // ordered cells are grouped by colour
+  // right-hand side blockIdx.y of a multi-RHS launch: offsets of its x, its
+  // colour buffers and its face results (0 for a single right-hand side)
+  int64_t ldx, ld_ycol, ld_face;
 };
 
 // Add the contributions of surrogate face (k, s) to the x-line result out[]
@@ -68,10 +71,10 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
   }
 }
 
-template <typename T, int D, int N>
-__global__ void __launch_bounds__(Shape<D, N>::CPB * Shape<D, N>::L)
+template <typename T, int D, int N, int CPB = Shape<D, N>::CPB>
+__global__ void __launch_bounds__(CPB * Shape<D, N>::L)
 cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
-  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, CPB = Shape<D, N>::CPB;
+  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);
   T* A = X + CPB * ND;
@@ -86,10 +89,11 @@ cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
   // each thread gathers its own x-line: one index load, N independent value
   // loads; the index is kept for the scatter
   const int g0 = act ? __ldg(a.lines + (size_t)(first + c) * L + tl) : 0;
+  const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
   if (act) {
     T v[N];
 #pragma unroll
-    for (int m = 0; m < N; ++m) v[m] = __ldg(a.x + g0 + m);
+    for (int m = 0; m < N; ++m) v[m] = __ldg(xr + g0 + m);
 #pragma unroll
     for (int m = 0; m < N; ++m) X[c * ND + N * tl + m] = v[m];
   }
@@ -100,13 +104,14 @@ cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
   if (act) {
     const int cell = first + c;
     const int fs = __ldg(a.face_start + cell), fe = __ldg(a.face_start + cell + 1);
+    const T* fo = a.face_out + blockIdx.y * a.ld_face;
     for (int f = fs; f < fe; ++f) {
       const int kind = __ldg(a.face_kind + f);
-      fold_face<T, D, N>(t, a.face_out + (size_t)f * 2 * L, kind & 3, kind >> 2, tl, out);
+      fold_face<T, D, N>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, tl, out);
     }
     int col = 0;
     while (cell >= a.col_start[col + 1]) ++col;
-    T* yc = a.ycol + (size_t)col * a.n_dofs + g0;
+    T* yc = a.ycol + blockIdx.y * a.ld_ycol + (size_t)col * a.n_dofs + g0;
 #pragma unroll
     for (int m = 0; m < N; ++m) yc[m] = out[m];
   }
@@ -116,9 +121,12 @@ cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
 // per thread (all of its loads in flight at once); the buffers are read once.
 template <typename T>
 __global__ void assemble_kernel(const T* __restrict__ ycol, const uint8_t* __restrict__ mask,
-                                T* __restrict__ y, int64_t n, int ncol) {
+                                T* __restrict__ y, int64_t n, int ncol, int64_t ld_ycol = 0,
+                                int64_t ldy = 0) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  ycol += blockIdx.y * ld_ycol;
+  y += blockIdx.y * ldy;
   const unsigned m = __ldg(mask + i);
   T v[8];
 #pragma unroll
@@ -157,6 +165,7 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T
   a.n_dofs = hp.n_dofs;
   a.ncell = dd.col_start[dd.ncolours];
   for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
+  a.ldx = a.ld_ycol = a.ld_face = 0;
   cg_apply_kernel<T, D, N><<<(a.ncell + CPB - 1) / CPB, CPB * L, smem, st>>>(a, t);
   nlaunch++;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
@@ -192,6 +201,7 @@ static cudaError_t launch_scratch_t(const HostProblem& hp, const DeviceData& dd,
   a.n_dofs = hp.n_dofs;
   a.ncell = dd.col_start[dd.ncolours];
   for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
+  a.ldx = a.ld_ycol = a.ld_face = 0;
   cg_apply_kernel<T, D, N><<<(a.ncell + CPB - 1) / CPB, CPB * L, smem, st>>>(a, t);
   const int64_t n = hp.n_dofs;
   assemble_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ycol, dd.dof_colours, y, n,
@@ -213,6 +223,77 @@ cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd,
 template cudaError_t launch_cg_apply_scratch<double>(const HostProblem&, const DeviceData&,
                                                      const double*, double*, double*, double*,
                                                      cudaStream_t);
+
+// nrhs right-hand sides in one set of launches (grid.y = right-hand side):
+// x and y hold nrhs vectors of n_dofs each, ld apart; the scratch holds nrhs
+// copies.  variant 0/1 picks the cells-per-block of the cell kernel (128 or
+// 256 threads' worth of lines), chosen by the autotuner.
+template <typename T, int D, int N, int CPB>
+static cudaError_t multi_cell_t(const HostProblem& hp, const DeviceData& dd, const T* x, int64_t ld,
+                                int nrhs, T* fo, T* ycol, cudaStream_t st) {
+  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
+  const KTab<T> t = make_ktab<T>(hp);
+  const size_t smem = (size_t)(5 * CPB * ND) * sizeof(T);
+  cudaError_t err;
+  if (smem > 48 * 1024 &&
+      (err = cudaFuncSetAttribute(cg_apply_kernel<T, D, N, CPB>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+          cudaSuccess)
+    return err;
+  CgArgs<T> a;
+  a.x = x;
+  a.ycol = ycol;
+  a.lines = dd.lines;
+  a.face_start = dd.face_start;
+  a.face_kind = dd.face_kind;
+  a.face_out = fo;
+  a.n_dofs = hp.n_dofs;
+  a.ncell = dd.col_start[dd.ncolours];
+  for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
+  a.ldx = ld;
+  a.ld_ycol = (int64_t)dd.ncolours * hp.n_dofs;
+  a.ld_face = (int64_t)dd.nface * 2 * L;
+  cg_apply_kernel<T, D, N, CPB><<<dim3((a.ncell + CPB - 1) / CPB, nrhs), CPB * L, smem, st>>>(a, t);
+  return cudaGetLastError();
+}
+
+template <typename T, int D, int N>
+static cudaError_t multi_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                           int64_t ld, int nrhs, T* fo, T* ycol, int variant, cudaStream_t st) {
+  constexpr int L = Shape<D, N>::L;
+  cudaError_t err;
+  if (dd.nface > 0 &&
+      (err = launch_face_kernel_multi<T>(hp, dd, x, ld, nrhs, fo, st)) != cudaSuccess)
+    return err;
+  if (variant == 1 && 256 / L > Shape<D, N>::CPB)
+    err = multi_cell_t<T, D, N, (256 / L > 0 ? 256 / L : 1)>(hp, dd, x, ld, nrhs, fo, ycol, st);
+  else
+    err = multi_cell_t<T, D, N, Shape<D, N>::CPB>(hp, dd, x, ld, nrhs, fo, ycol, st);
+  if (err != cudaSuccess) return err;
+  const int64_t n = hp.n_dofs;
+  assemble_kernel<T><<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(
+      ycol, dd.dof_colours, y, n, dd.ncolours, (int64_t)dd.ncolours * n, ld);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_apply_multi(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                                  int64_t ld, int nrhs, T* face_scratch, T* colour_scratch,
+                                  int variant, cudaStream_t st) {
+#define SBM_CASE(DD, NN)                                                                   \
+  if (hp.d == DD && hp.n == NN)                                                            \
+    return multi_t<T, DD, NN>(hp, dd, x, y, ld, nrhs, face_scratch, colour_scratch, variant, st);
+  SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
+  SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
+#undef SBM_CASE
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_cg_apply_multi<double>(const HostProblem&, const DeviceData&,
+                                                   const double*, double*, int64_t, int, double*,
+                                                   double*, int, cudaStream_t);
+template cudaError_t launch_cg_apply_multi<float>(const HostProblem&, const DeviceData&,
+                                                  const float*, float*, int64_t, int, float*,
+                                                  float*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,

@@ -31,12 +31,15 @@ struct FaceArgs {
   T* __restrict__ out;                     // [F][2L]
   int nface;
   int dg;
+  int64_t ldx, ld_out;                     // right-hand side blockIdx.y offsets
 };
 
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(Shape<D, N>::CPB * Shape<D, N>::L)
 sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, FPB = Shape<D, N>::CPB;
+  const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
+  T* __restrict__ outr = a.out + blockIdx.y * a.ld_out;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);
   T* SC = X + FPB * ND;            // 6 L per face
@@ -49,7 +52,7 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
     size_t g;
     if (a.dg) g = (size_t)__ldg(a.cell_rank + cell) * ND + loc;
     else g = (size_t)__ldg(a.lines + (size_t)cell * L + loc / N) + (loc % N);
-    X[r] = __ldg(a.x + g);
+    X[r] = __ldg(xr + g);
   }
   __syncthreads();
   const int fl = tid / L, tl = tid - fl * L;
@@ -183,14 +186,14 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
     }
   }
   if (act) {
-    a.out[(size_t)f * 2 * L + tl] = rv;
-    a.out[(size_t)f * 2 * L + L + tl] = rg;
+    outr[(size_t)f * 2 * L + tl] = rv;
+    outr[(size_t)f * 2 * L + L + tl] = rg;
   }
 }
 
 template <typename T, int D, int N>
 static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
-                          cudaStream_t st) {
+                          cudaStream_t st, int64_t ldx = 0, int nrhs = 1) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, FPB = Shape<D, N>::CPB;
   if (dd.nface == 0) return cudaSuccess;
   const KTab<T> t = make_ktab<T>(hp);
@@ -204,8 +207,10 @@ static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* 
   a.out = out;
   a.nface = dd.nface;
   a.dg = hp.desc.dg;
+  a.ldx = ldx;
+  a.ld_out = (int64_t)dd.nface * 2 * L;
   const size_t smem = (size_t)(FPB * ND + FPB * 6 * L) * sizeof(T);
-  sface_kernel<T, D, N><<<(dd.nface + FPB - 1) / FPB, FPB * L, smem, st>>>(a, t);
+  sface_kernel<T, D, N><<<dim3((dd.nface + FPB - 1) / FPB, nrhs), FPB * L, smem, st>>>(a, t);
   return cudaGetLastError();
 }
 
@@ -221,6 +226,23 @@ cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, cons
 }
 template cudaError_t launch_face_kernel<double>(const HostProblem&, const DeviceData&,
                                                 const double*, double*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_face_kernel_multi(const HostProblem& hp, const DeviceData& dd, const T* x,
+                                     int64_t ldx, int nrhs, T* out, cudaStream_t st) {
+#define SBM_CASE(DD, NN) \
+  if (hp.d == DD && hp.n == NN) return face_t<T, DD, NN>(hp, dd, x, out, st, ldx, nrhs);
+  SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
+  SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
+#undef SBM_CASE
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_face_kernel_multi<double>(const HostProblem&, const DeviceData&,
+                                                      const double*, int64_t, int, double*,
+                                                      cudaStream_t);
+template cudaError_t launch_face_kernel_multi<float>(const HostProblem&, const DeviceData&,
+                                                     const float*, int64_t, int, float*,
+                                                     cudaStream_t);
 template cudaError_t launch_face_kernel<float>(const HostProblem&, const DeviceData&,
                                                const float*, float*, cudaStream_t);
 

@@ -108,6 +108,17 @@ template <> inline float* face_out_of<float>(const DeviceData& dd) { return dd.f
 template <typename T>
 cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
                                cudaStream_t st);
+// The same for nrhs right-hand sides (x: nrhs vectors ldx apart; out: nrhs
+// copies of the per-face scratch).
+template <typename T>
+cudaError_t launch_face_kernel_multi(const HostProblem& hp, const DeviceData& dd, const T* x,
+                                     int64_t ldx, int nrhs, T* out, cudaStream_t st);
+// CG apply of nrhs right-hand sides with caller scratch (face: nrhs*F*2L,
+// colour: nrhs*ncolours*n_dofs); variant = cell-kernel tile shape (0 or 1).
+template <typename T>
+cudaError_t launch_cg_apply_multi(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                                  int64_t ld, int nrhs, T* face_scratch, T* colour_scratch,
+                                  int variant, cudaStream_t st);
 
 template <typename T> inline const T* face_phi_of(const DeviceData& dd);
 template <> inline const double* face_phi_of<double>(const DeviceData& dd) { return dd.face_phi; }
