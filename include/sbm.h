@@ -152,9 +152,15 @@ enum { SBM_FACE_FP32 = 0, SBM_FACE_TF32 = 1, SBM_FACE_BF16 = 2 };
  * Matrix-free apply in FP32 (same operator and algorithm as sbm_apply_f64;
  * the 1D tables and the per-face shifted-point tables rounded to FP32):
  * y = A x with x, y device arrays of n_dofs floats.  face_mode selects the
- * face arithmetic (SBM_FACE_*).  Asynchronous on stream.
- * Errors: SBM_ERR_ARG, SBM_ERR_STATE, SBM_ERR_UNSUPPORTED (face mode not
- * available), SBM_ERR_CUDA.
+ * arithmetic of the surrogate faces' shifted point evaluation (Algorithm 3's
+ * O((p+1)^(2d-1)) step): SBM_FACE_FP32 on the CUDA cores, or SBM_FACE_TF32 /
+ * SBM_FACE_BF16 on the tensor cores (tcgen05, FP32 accumulation; 3D only),
+ * where the Lagrange values at the shifted points and the cell values are
+ * rounded to TF32 / BF16.  Asynchronous on stream.  A tensor-core apply whose
+ * bounded wait expired records SBM_ERR_TIMEOUT, reported by
+ * sbm_device_status.
+ * Errors: SBM_ERR_ARG, SBM_ERR_STATE, SBM_ERR_UNSUPPORTED (tensor-core mode on
+ * a 2D problem), SBM_ERR_CUDA.
  */
 int sbm_apply_f32(sbm_problem* prob, const float* x, float* y, int face_mode, void* stream);
 
@@ -268,6 +274,7 @@ int sbm_gmres(sbm_problem* prob, const double* b, double* x, double rtol, int ma
  * Mixed precision: FP64 iterative refinement (defect correction).  Each
  * outer step computes r = b - A x with the FP64 apply, then solves
  * A c = r/|r| approximately with FP32 GMRES(restart) on the FP32 apply
+ * (face arithmetic face_mode, as in sbm_apply_f32)
  * (relative tolerance inner_rtol, at most inner_maxit iterations), and
  * updates x += |r| c in FP64.  Stops when |b - A x|/|b| <= rtol (FP64) or
  * after max_outer steps.  *iters = FP32 inner iterations in total,
@@ -303,6 +310,13 @@ int sbm_interpolate(const sbm_problem* prob, int manufactured, double* u_host);
  */
 int sbm_profile_enable(sbm_problem* prob, int on);
 int sbm_profile_read(sbm_problem* prob, double* phase_ms, int64_t* launches);
+
+/*
+ * Synchronise the device and report (then clear) the problem's device error
+ * word: SBM_ERR_TIMEOUT if a bounded device-side wait of an earlier call
+ * expired, SBM_OK otherwise.
+ */
+int sbm_device_status(sbm_problem* prob);
 
 /* Human-readable name of a status code (static string). */
 const char* sbm_error_string(int status);

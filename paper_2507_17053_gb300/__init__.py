@@ -88,6 +88,7 @@ _SIGS = {
     "sbm_batch_destroy": (None, [ctypes.c_void_p]),
     "sbm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_i64p]),
+    "sbm_device_status": (ctypes.c_int, [ctypes.c_void_p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sbm_last_error_detail": (ctypes.c_char_p, []),
 }
@@ -250,6 +251,10 @@ def sbm_rhs(handle: int, manufactured: int, b_host) -> None:
 
 def sbm_interpolate(handle: int, manufactured: int, u_host) -> None:
     _check(lib().sbm_interpolate(handle, int(manufactured), _ptr(u_host)), "sbm_interpolate")
+
+
+def sbm_device_status(handle: int) -> None:
+    _check(lib().sbm_device_status(handle), "sbm_device_status")
 
 
 def sbm_profile_enable(handle: int, on: bool) -> None:

@@ -103,6 +103,7 @@ static void free_device(DeviceData* dd) {
   cudaFree(dd->face_out);
   cudaFree(dd->face_out32);
   cudaFree(dd->dof_colours);
+  cudaFree(dd->err_flag);
   cudaFree(dd->ycol);
   cudaFree(dd->ycol32);
   cudaFree(dd->face_phi);
@@ -192,6 +193,8 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   if ((e = upload(&dd->face_kind, fkind.data(), fkind.size())) != cudaSuccess) goto err;
   if ((e = upload(&dd->face_cell, fcell.data(), fcell.size())) != cudaSuccess) goto err;
   dd->nface = (int)fkind.size();
+  if ((e = cudaMalloc((void**)&dd->err_flag, sizeof(int))) != cudaSuccess) goto err;
+  if ((e = cudaMemset(dd->err_flag, 0, sizeof(int))) != cudaSuccess) goto err;
   if (!hp.desc.dg) {
     // colour mask per DoF and the colour accumulation buffers
     std::vector<uint8_t> mask(hp.n_dofs, 0);
@@ -362,10 +365,15 @@ int sbm_apply_f32(sbm_problem* prob, const float* x, float* y, int face_mode, vo
   if (!prob || !x || !y) return fail(SBM_ERR_ARG, "NULL argument");
   if (x == y) return fail(SBM_ERR_ARG, "x and y must not overlap");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
-  if (face_mode != SBM_FACE_FP32) return fail(SBM_ERR_UNSUPPORTED, "face mode not built");
+  if (face_mode != SBM_FACE_FP32 && face_mode != SBM_FACE_TF32 && face_mode != SBM_FACE_BF16)
+    return fail(SBM_ERR_ARG, "unknown face mode");
+  if (face_mode != SBM_FACE_FP32 && prob->hp.d != 3)
+    return fail(SBM_ERR_UNSUPPORTED, "tensor-core face modes are built for 3D problems");
   cudaError_t e = prob->hp.desc.dg
-      ? launch_dg_apply<float>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof)
-      : launch_cg_apply<float>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof);
+      ? launch_dg_apply<float>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof,
+                               face_mode)
+      : launch_cg_apply<float>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof,
+                               face_mode);
   if (e != cudaSuccess) return cuda_fail(e, "sbm_apply_f32");
   return SBM_OK;
 }
@@ -377,10 +385,11 @@ static ApplyFn<double> apply64_fn(sbm_problem* prob) {
   };
 }
 
-static ApplyFn<float> apply32_fn(sbm_problem* prob) {
-  return [prob](const float* x, float* y, cudaStream_t st) {
-    return prob->hp.desc.dg ? launch_dg_apply<float>(prob->hp, prob->dd, x, y, st, nullptr)
-                            : launch_cg_apply<float>(prob->hp, prob->dd, x, y, st, nullptr);
+static ApplyFn<float> apply32_fn(sbm_problem* prob, int face_mode = SBM_FACE_FP32) {
+  return [prob, face_mode](const float* x, float* y, cudaStream_t st) {
+    return prob->hp.desc.dg
+               ? launch_dg_apply<float>(prob->hp, prob->dd, x, y, st, nullptr, face_mode)
+               : launch_cg_apply<float>(prob->hp, prob->dd, x, y, st, nullptr, face_mode);
   };
 }
 
@@ -444,11 +453,14 @@ int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int
   if (!(rtol > 0) || max_outer < 0 || restart < 1 || restart > 1000 || !(inner_rtol > 0) ||
       inner_maxit < 1)
     return fail(SBM_ERR_ARG, "bad solver parameter");
-  if (face_mode != SBM_FACE_FP32) return fail(SBM_ERR_UNSUPPORTED, "face mode not built");
+  if (face_mode != SBM_FACE_FP32 && face_mode != SBM_FACE_TF32 && face_mode != SBM_FACE_BF16)
+    return fail(SBM_ERR_ARG, "unknown face mode");
+  if (face_mode != SBM_FACE_FP32 && prob->hp.d != 3)
+    return fail(SBM_ERR_UNSUPPORTED, "tensor-core face modes are built for 3D problems");
   cudaStream_t st = (cudaStream_t)stream;
   Workspace ws;
   SolveInfo info;
-  SolveStatus s = solve_ir(apply64_fn(prob), apply32_fn(prob), prob->hp.n_dofs, b, x, rtol,
+  SolveStatus s = solve_ir(apply64_fn(prob), apply32_fn(prob, face_mode), prob->hp.n_dofs, b, x, rtol,
                            max_outer, restart, inner_rtol, inner_maxit, st, ws, &info);
   cudaStreamSynchronize(st);
   ws.release();
@@ -467,6 +479,21 @@ int sbm_interpolate(const sbm_problem* prob, int manufactured, double* u_host) {
   if (!prob || !u_host) return fail(SBM_ERR_ARG, "NULL argument");
   if (!manufactured_ok(manufactured, prob->hp.d)) return fail(SBM_ERR_ARG, "unknown solution id");
   build_interpolant(prob->hp, manufactured, u_host);
+  return SBM_OK;
+}
+
+int sbm_device_status(sbm_problem* prob) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  if (!prob->on_device) return SBM_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  int v = 0;
+  if ((e = cudaMemcpy(&v, prob->dd.err_flag, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "read device error word");
+  if (v != 0) {
+    cudaMemset(prob->dd.err_flag, 0, sizeof(int));
+    return fail(v, "a bounded device-side wait expired");
+  }
   return SBM_OK;
 }
 

@@ -53,9 +53,11 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
   const int kend = s ? N - 1 : 0;
   if (k == 0) {                       // tangential index = the line itself
     const T v = __ldg(rv + tl), g = __ldg(rg + tl);
-    out[kend] += v;
 #pragma unroll
-    for (int m = 0; m < N; ++m) out[m] = fma(s ? t.D1[m] : t.D0[m], g, out[m]);
+    for (int m = 0; m < N; ++m) {
+      out[m] = fma(s ? t.D1[m] : t.D0[m], g, out[m]);
+      if (m == kend) out[m] += v;       // compile-time index: out stays in registers
+    }
   } else {
     // k == 1: line tl = (j1, j2), tangential (m, j2);  k == 2: tangential (m, j1)
     const int jk = (D == 2 || k == 1) ? tl % N : tl / N;
@@ -71,6 +73,10 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
   }
 }
 
+// Every block walks over tiles of CPB cells (tile = blockIdx.x, then +
+// gridDim.x, ...).  While a tile is in the sweeps, the x-lines of the block's
+// next tile are already being loaded into registers, so the gather latency
+// of one tile hides behind the arithmetic of the previous one.
 template <typename T, int D, int N, int CPB = Shape<D, N>::CPB>
 __global__ void __launch_bounds__(CPB * Shape<D, N>::L)
 cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
@@ -82,65 +88,112 @@ cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
   T* B = E + CPB * ND;
   T* G = B + CPB * ND;
   const int tid = threadIdx.x;
-  const int first = blockIdx.x * CPB;
-  const int ncells = min(CPB, a.ncell - first);
   const int c = tid / L, tl = tid - c * L;
-  const bool act = c < ncells;
-  // each thread gathers its own x-line: one index load, N independent value
-  // loads; the index is kept for the scatter
-  const int g0 = act ? __ldg(a.lines + (size_t)(first + c) * L + tl) : 0;
+  const int ntiles = (a.ncell + CPB - 1) / CPB;
   const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
+  const T* fo = a.face_out + blockIdx.y * a.ld_face;
+  T* ycb = a.ycol + blockIdx.y * a.ld_ycol;
+
+  // registers of the tile in flight: its x-line, its index, its face range
+  int tile = blockIdx.x;
+  int cell = tile * CPB + c;
+  bool act = tile < ntiles && cell < a.ncell;
+  int g0 = 0, fs = 0, fe = 0;
+  T v[N];
   if (act) {
-    T v[N];
+    g0 = __ldg(a.lines + (size_t)cell * L + tl);
 #pragma unroll
     for (int m = 0; m < N; ++m) v[m] = __ldg(xr + g0 + m);
-#pragma unroll
-    for (int m = 0; m < N; ++m) X[c * ND + N * tl + m] = v[m];
+    fs = __ldg(a.face_start + cell);
+    fe = __ldg(a.face_start + cell + 1);
   }
-  __syncthreads();
-  T out[N];
-  if (D == 3) cell_sweeps_3d<T, N>(t, X, A, E, B, G, c, tl, act, out);
-  else cell_sweeps_2d<T, N>(t, X, A, E, c, tl, act, out);
-  if (act) {
-    const int cell = first + c;
-    const int fs = __ldg(a.face_start + cell), fe = __ldg(a.face_start + cell + 1);
-    const T* fo = a.face_out + blockIdx.y * a.ld_face;
-    for (int f = fs; f < fe; ++f) {
-      const int kind = __ldg(a.face_kind + f);
-      fold_face<T, D, N>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, tl, out);
+  while (tile < ntiles) {
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < N; ++m) X[c * ND + N * tl + m] = v[m];
     }
-    int col = 0;
-    while (cell >= a.col_start[col + 1]) ++col;
-    T* yc = a.ycol + blockIdx.y * a.ld_ycol + (size_t)col * a.n_dofs + g0;
+    __syncthreads();
+    // prefetch the next tile
+    const int ntile = tile + gridDim.x;
+    const int ncell_ = ntile * CPB + c;
+    const bool nact = ntile < ntiles && ncell_ < a.ncell;
+    int ng0 = 0, nfs = 0, nfe = 0;
+    if (nact) {
+      ng0 = __ldg(a.lines + (size_t)ncell_ * L + tl);
 #pragma unroll
-    for (int m = 0; m < N; ++m) yc[m] = out[m];
+      for (int m = 0; m < N; ++m) v[m] = __ldg(xr + ng0 + m);
+      nfs = __ldg(a.face_start + ncell_);
+      nfe = __ldg(a.face_start + ncell_ + 1);
+    }
+    T out[N];
+    if (D == 3) cell_sweeps_3d<T, N>(t, X, A, E, B, G, c, tl, act, out);
+    else cell_sweeps_2d<T, N>(t, X, A, E, c, tl, act, out);
+    if (act) {
+      for (int f = fs; f < fe; ++f) {
+        const int kind = __ldg(a.face_kind + f);
+        fold_face<T, D, N>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, tl, out);
+      }
+      int col = 0;             // cells are ordered by colour; unrolled: no local copy
+#pragma unroll
+      for (int k = 1; k < 8; ++k) col += (cell >= a.col_start[k]) ? 1 : 0;
+      T* yc = ycb + (size_t)col * a.n_dofs + g0;
+#pragma unroll
+      for (int m = 0; m < N; ++m) yc[m] = out[m];
+    }
+    tile = ntile;
+    cell = ncell_;
+    act = nact;
+    g0 = ng0;
+    fs = nfs;
+    fe = nfe;
   }
+}
+
+// Blocks of the cell kernel: enough to fill every SM at the kernel's
+// occupancy (so each block walks over several tiles), capped by the tiles.
+template <typename T, int D, int N, int CPB>
+static int cell_grid(int ntiles, size_t smem) {
+  static int per_sm = 0, sms = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_apply_kernel<T, D, N, CPB>,
+                                                      CPB * Shape<D, N>::L, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  const int g = per_sm * sms;
+  return ntiles < g ? ntiles : g;
 }
 
 // y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order.  One DoF
 // per thread (all of its loads in flight at once); the buffers are read once.
+// Adding 0.0 is exact, so y_i equals the plain sum over the set colours; the
+// additions of a colour that no lane of the warp has are skipped (on GB300
+// every double addition costs an FP64-pipe slot).
 template <typename T>
 __global__ void assemble_kernel(const T* __restrict__ ycol, const uint8_t* __restrict__ mask,
                                 T* __restrict__ y, int64_t n, int ncol, int64_t ld_ycol = 0,
                                 int64_t ldy = 0) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
   ycol += blockIdx.y * ld_ycol;
   y += blockIdx.y * ldy;
-  const unsigned m = __ldg(mask + i);
+  const unsigned m = (i < n) ? (unsigned)__ldg(mask + i) : 0u;
   T v[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c)
     v[c] = (c < ncol && (m & (1u << c))) ? __ldcs(ycol + (size_t)c * n + i) : T(0);
   T acc = T(0);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) acc += v[c];
-  __stcs(y + i, acc);
+  for (int c = 0; c < 8; ++c)
+    if (__any_sync(0xffffffffu, (m >> c) & 1u)) acc += v[c];
+  if (i < n) __stcs(y + i, acc);
 }
 
 template <typename T, int D, int N>
 static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            cudaStream_t st, Profiler* prof) {
+                            cudaStream_t st, Profiler* prof, int face_mode) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, CPB = Shape<D, N>::CPB;
   const KTab<T> t = make_ktab<T>(hp);
   const size_t smem = (size_t)(5 * CPB * ND) * sizeof(T);
@@ -151,7 +204,7 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   int nlaunch = 0;
   if (dd.nface > 0) {
-    if ((err = launch_face_kernel<T>(hp, dd, x, fo, st)) != cudaSuccess) return err;
+    if ((err = launch_faces<T>(hp, dd, x, fo, face_mode, st)) != cudaSuccess) return err;
     nlaunch++;
   }
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
@@ -166,7 +219,8 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T
   a.ncell = dd.col_start[dd.ncolours];
   for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
   a.ldx = a.ld_ycol = a.ld_face = 0;
-  cg_apply_kernel<T, D, N><<<(a.ncell + CPB - 1) / CPB, CPB * L, smem, st>>>(a, t);
+  cg_apply_kernel<T, D, N><<<cell_grid<T, D, N, CPB>((a.ncell + CPB - 1) / CPB, smem), CPB * L, smem,
+                             st>>>(a, t);
   nlaunch++;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   const int64_t n = hp.n_dofs;
@@ -202,7 +256,8 @@ static cudaError_t launch_scratch_t(const HostProblem& hp, const DeviceData& dd,
   a.ncell = dd.col_start[dd.ncolours];
   for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
   a.ldx = a.ld_ycol = a.ld_face = 0;
-  cg_apply_kernel<T, D, N><<<(a.ncell + CPB - 1) / CPB, CPB * L, smem, st>>>(a, t);
+  cg_apply_kernel<T, D, N><<<cell_grid<T, D, N, CPB>((a.ncell + CPB - 1) / CPB, smem), CPB * L, smem,
+                             st>>>(a, t);
   const int64_t n = hp.n_dofs;
   assemble_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ycol, dd.dof_colours, y, n,
                                                                    dd.ncolours);
@@ -253,7 +308,9 @@ static cudaError_t multi_cell_t(const HostProblem& hp, const DeviceData& dd, con
   a.ldx = ld;
   a.ld_ycol = (int64_t)dd.ncolours * hp.n_dofs;
   a.ld_face = (int64_t)dd.nface * 2 * L;
-  cg_apply_kernel<T, D, N, CPB><<<dim3((a.ncell + CPB - 1) / CPB, nrhs), CPB * L, smem, st>>>(a, t);
+  cg_apply_kernel<T, D, N, CPB>
+      <<<dim3(cell_grid<T, D, N, CPB>((a.ncell + CPB - 1) / CPB, smem), nrhs), CPB * L, smem, st>>>(
+          a, t);
   return cudaGetLastError();
 }
 
@@ -297,17 +354,18 @@ template cudaError_t launch_cg_apply_multi<float>(const HostProblem&, const Devi
 
 template <typename T>
 cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            cudaStream_t st, Profiler* prof) {
+                            cudaStream_t st, Profiler* prof, int face_mode) {
 #define SBM_CASE(DD, NN) \
-  if (hp.d == DD && hp.n == NN) return launch_t<T, DD, NN>(hp, dd, x, y, st, prof);
+  if (hp.d == DD && hp.n == NN) return launch_t<T, DD, NN>(hp, dd, x, y, st, prof, face_mode);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_cg_apply<double>(const HostProblem&, const DeviceData&,
-                                             const double*, double*, cudaStream_t, Profiler*);
+                                             const double*, double*, cudaStream_t, Profiler*,
+                                             int);
 template cudaError_t launch_cg_apply<float>(const HostProblem&, const DeviceData&, const float*,
-                                            float*, cudaStream_t, Profiler*);
+                                            float*, cudaStream_t, Profiler*, int);
 
 }  // namespace sbm

@@ -235,7 +235,7 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
 
 template <typename T, int D, int N>
 static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                        cudaStream_t st, Profiler* prof) {
+                        cudaStream_t st, Profiler* prof, int face_mode) {
   constexpr int L = DgShape<D, N>::L, ND = DgShape<D, N>::ND, CPB = DgShape<D, N>::CPB;
   const KTab<T> t = make_ktab<T>(hp);
   const size_t smem = (size_t)(5 * CPB * ND + 6 * CPB * L) * sizeof(T);
@@ -258,7 +258,7 @@ static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x,
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   int nlaunch = 1;
   if (dd.nface > 0) {
-    if ((err = launch_face_kernel<T>(hp, dd, x, face_out_of<T>(dd), st)) != cudaSuccess)
+    if ((err = launch_faces<T>(hp, dd, x, face_out_of<T>(dd), face_mode, st)) != cudaSuccess)
       return err;
     nlaunch++;
   }
@@ -276,17 +276,18 @@ static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x,
 
 template <typename T>
 cudaError_t launch_dg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            cudaStream_t st, Profiler* prof) {
+                            cudaStream_t st, Profiler* prof, int face_mode) {
 #define SBM_CASE(DD, NN) \
-  if (hp.d == DD && hp.n == NN) return dg_t<T, DD, NN>(hp, dd, x, y, st, prof);
+  if (hp.d == DD && hp.n == NN) return dg_t<T, DD, NN>(hp, dd, x, y, st, prof, face_mode);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_dg_apply<double>(const HostProblem&, const DeviceData&,
-                                             const double*, double*, cudaStream_t, Profiler*);
+                                             const double*, double*, cudaStream_t, Profiler*,
+                                             int);
 template cudaError_t launch_dg_apply<float>(const HostProblem&, const DeviceData&, const float*,
-                                            float*, cudaStream_t, Profiler*);
+                                            float*, cudaStream_t, Profiler*, int);
 
 }  // namespace sbm

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -61,6 +63,7 @@ struct DeviceData {
   int nface = 0;
   double* face_out = nullptr;    // [F * 2L] per-face results of the face kernel (scratch)
   float* face_out32 = nullptr;
+  int* err_flag = nullptr;       // device error word (SBM_ERR_TIMEOUT from bounded waits)
   uint8_t* dof_colours = nullptr;  // CG [n_dofs]: bit c set if a cell of colour c touches the DoF
   double* ycol = nullptr;        // CG [ncolours * n_dofs] colour accumulation buffers (scratch)
   float* ycol32 = nullptr;
@@ -124,10 +127,16 @@ template <typename T> inline const T* face_phi_of(const DeviceData& dd);
 template <> inline const double* face_phi_of<double>(const DeviceData& dd) { return dd.face_phi; }
 template <> inline const float* face_phi_of<float>(const DeviceData& dd) { return dd.face_phi32; }
 
-// Apply, CG: y = A x (memset + one launch per colour); T = double or float.
+// Surrogate faces on the tensor cores (3D, FP32 apply): face_mode
+// SBM_FACE_TF32 or SBM_FACE_BF16; same output as launch_face_kernel.
+cudaError_t launch_tc_face_kernel(const HostProblem& hp, const DeviceData& dd, const float* x,
+                                  float* out, int face_mode, cudaStream_t st);
+
+// Apply, CG: face kernel, cell kernel, assembly; T = double or float
+// (face_mode applies to float: SBM_FACE_FP32 / TF32 / BF16).
 template <typename T>
 cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            cudaStream_t st, Profiler* prof);
+                            cudaStream_t st, Profiler* prof, int face_mode = 0);
 // Apply, CG, with caller-provided scratch (per-face results [F][2L] and the
 // colour buffers [ncolours][n_dofs]) instead of the problem's own.
 template <typename T>
@@ -136,7 +145,18 @@ cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd,
 // Apply, DG: one launch.
 template <typename T>
 cudaError_t launch_dg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            cudaStream_t st, Profiler* prof);
+                            cudaStream_t st, Profiler* prof, int face_mode = 0);
+
+// the face stage of an apply: CUDA-core kernel, or the tensor-core kernel for
+// an FP32 apply in TF32 / BF16 face mode
+template <typename T>
+inline cudaError_t launch_faces(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
+                                int face_mode, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (face_mode != 0) return launch_tc_face_kernel(hp, dd, x, out, face_mode, st);
+  }
+  return launch_face_kernel<T>(hp, dd, x, out, st);
+}
 // FP64 diagonal.
 cudaError_t launch_diag_f64(const HostProblem& hp, const DeviceData& dd, double* diag,
                             cudaStream_t st);
