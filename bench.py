@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--workload", default=S.SPHERE_3D_Q4.name)
     ap.add_argument("--skip-cpu-baseline", action="store_true",
                     help="leave out the oracle timing (profiling runs)")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="only the headline workload (no other workloads, batch, solves)")
+    ap.add_argument("--profile-applies", choices=["f64", "f32", "tf32", "bf16"], default=None,
+                    help="run --steps applies of the workload in this precision and exit "
+                         "(a fixed launch sequence for ncu captures; prints no JSON)")
     return ap.parse_args()
 
 
@@ -279,6 +284,96 @@ def solve_times(G, torch):
     return out
 
 
+def other_workloads(G, torch, steps=40):
+    """FP64 / FP32 / TF32-face / BF16-face applies of the 3D Q6 ellipsoid and
+    the DG Q3 torus: GDoF/s (CUDA events) and the FP32-path error against the
+    FP64 apply of the same x."""
+    out = {}
+    for w in (S.ELLIPSOID_3D_Q6, S.TORUS_3D_DG_Q3):
+        P = G.Problem.from_workload(w)
+        x = torch.from_numpy(S.random_vector(w.seed, P.n_dofs, w.dist)).cuda()
+        y = torch.empty_like(x)
+        x32 = x.float()
+        y32 = torch.empty_like(x32)
+        ref = P.apply_f64(x).clone()
+        res = {"n_dofs": P.n_dofs, "n_cells": P.n_cells, "n_sfaces": P.n_sfaces}
+        for name, fn, xx, yy in (("f64", lambda a, b: P.apply_f64(a, b), x, y),
+                                 ("f32", lambda a, b: P.apply_f32(a, b), x32, y32),
+                                 ("tf32_faces", lambda a, b: P.apply_f32(a, b, face_mode="tf32"),
+                                  x32, y32),
+                                 ("bf16_faces", lambda a, b: P.apply_f32(a, b, face_mode="bf16"),
+                                  x32, y32)):
+            for _ in range(3):
+                fn(xx, yy)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                fn(xx, yy)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            r = {"gdofs": P.n_dofs / ms / 1e6, "ms": ms}
+            if name != "f64":
+                r["rel_err_vs_f64"] = float((yy.double() - ref).abs().max() / ref.abs().max())
+            res[name] = r
+        G.sbm_device_status(P.handle)
+        out[w.name] = res
+    return out
+
+
+def batched(G, torch, steps=10):
+    """64 rotated-ellipsoid CG problems (N ~ U{16..48}, p ~ U{2..6}), 8
+    right-hand sides each, one CUDA-graph launch per batched apply."""
+    ws = S.batched_ellipsoids()
+    ps = [G.Problem.from_workload(w) for w in ws]
+    nrhs = 8
+    B = G.Batch(ps, nrhs, autotune=True)
+    tot = sum(p.n_dofs for p in ps) * nrhs
+    res = {"problems": len(ps), "nrhs": nrhs, "dof_rhs_per_apply": tot,
+           "tile_shape_by_degree": {str(w.degree): B.tile_shape(k) for k, w in enumerate(ws)}}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        xs = [torch.from_numpy(np.concatenate([S.random_vector(w.seed + r, p.n_dofs, "uniform")
+                                               for r in range(nrhs)])).to("cuda", dt)
+              for w, p in zip(ws, ps)]
+        ys = [torch.empty_like(v) for v in xs]
+        for _ in range(3):
+            B.apply(xs, ys)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            B.apply(xs, ys)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"gdofs": tot / ms / 1e6, "ms": ms}
+        del xs, ys
+    B.close()
+    return res
+
+
+def profile_applies(args, w):
+    import torch
+
+    import paper_2507_17053_gb300 as G
+    P = G.Problem.from_workload(w)
+    x = torch.from_numpy(S.random_vector(w.seed, P.n_dofs, w.dist)).cuda()
+    if args.profile_applies != "f64":
+        x = x.float()
+    y = torch.empty_like(x)
+    for _ in range(args.steps):
+        if args.profile_applies == "f64":
+            P.apply_f64(x, y)
+        else:
+            P.apply_f32(x, y, face_mode={"f32": "fp32", "tf32": "tf32",
+                                         "bf16": "bf16"}[args.profile_applies])
+    torch.cuda.synchronize()
+    G.sbm_device_status(P.handle)
+
+
 def run_ours(args, w):
     import torch
 
@@ -364,10 +459,13 @@ def run_ours(args, w):
                        "hbm_frac_8B_per_dof": 8 * n / step32_s / 1e9 / pk["hbm_gbs"]},
         "clocks": clk,
     }
-    try:
-        line["solves"] = solve_times(G, torch)
-    except Exception as e:  # noqa: BLE001 -- report, never hide the main number
-        line["solves"] = {"error": str(e)}
+    if not args.skip_extras:
+        for key, fn in (("solves", solve_times), ("other_workloads", other_workloads),
+                        ("batched_64x8", batched)):
+            try:
+                line[key] = fn(G, torch)
+            except Exception as e:  # noqa: BLE001 -- report, never hide the main number
+                line[key] = {"error": str(e)}
     if not args.skip_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -378,6 +476,8 @@ def main():
     w = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, w)
+    elif args.profile_applies:
+        profile_applies(args, w)
     else:
         run_ours(args, w)
 
