@@ -318,6 +318,15 @@ int sbm_profile_read(sbm_problem* prob, double* phase_ms, int64_t* launches);
  */
 int sbm_device_status(sbm_problem* prob);
 
+/*
+ * Diagnostic of the failure path (the paper has no counterpart): enqueue one
+ * device-side bounded wait on a barrier that nothing releases.  The wait
+ * gives up after a fixed number of polls (well under a second), records
+ * SBM_ERR_TIMEOUT in the problem's device error word and returns; the next
+ * sbm_device_status reports it.  No fault, no hang; the context stays usable.
+ */
+int sbm_selftest_timeout(sbm_problem* prob, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* sbm_error_string(int status);
 

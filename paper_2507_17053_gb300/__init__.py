@@ -89,6 +89,7 @@ _SIGS = {
     "sbm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_i64p]),
     "sbm_device_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "sbm_selftest_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sbm_last_error_detail": (ctypes.c_char_p, []),
 }
@@ -255,6 +256,10 @@ def sbm_interpolate(handle: int, manufactured: int, u_host) -> None:
 
 def sbm_device_status(handle: int) -> None:
     _check(lib().sbm_device_status(handle), "sbm_device_status")
+
+
+def sbm_selftest_timeout(handle: int, stream=None) -> None:
+    _check(lib().sbm_selftest_timeout(handle, _stream(stream)), "sbm_selftest_timeout")
 
 
 def sbm_profile_enable(handle: int, on: bool) -> None:

@@ -497,6 +497,14 @@ int sbm_device_status(sbm_problem* prob) {
   return SBM_OK;
 }
 
+int sbm_selftest_timeout(sbm_problem* prob, void* stream) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  cudaError_t e = launch_timeout_selftest(prob->dd.err_flag, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sbm_selftest_timeout");
+  return SBM_OK;
+}
+
 int sbm_profile_enable(sbm_problem* prob, int on) {
   if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
   prob->prof.on = (on != 0);

@@ -81,12 +81,11 @@ template <typename T, int D, int N, int CPB = Shape<D, N>::CPB>
 __global__ void __launch_bounds__(CPB * Shape<D, N>::L)
 cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
+  using P2 = typename PairOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* X = reinterpret_cast<T*>(smem_raw);
-  T* A = X + CPB * ND;
-  T* E = A + CPB * ND;
-  T* B = E + CPB * ND;
-  T* G = B + CPB * ND;
+  P2* AE = reinterpret_cast<P2*>(smem_raw);     // pair arrays first: 8/16-byte aligned
+  P2* BG = AE + CPB * ND;
+  T* X = reinterpret_cast<T*>(BG + CPB * ND);
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
   const int ntiles = (a.ncell + CPB - 1) / CPB;
@@ -126,8 +125,8 @@ cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
       nfe = __ldg(a.face_start + ncell_ + 1);
     }
     T out[N];
-    if (D == 3) cell_sweeps_3d<T, N>(t, X, A, E, B, G, c, tl, act, out);
-    else cell_sweeps_2d<T, N>(t, X, A, E, c, tl, act, out);
+    if (D == 3) cell_sweeps_3d<T, N>(t, X, AE, BG, c, tl, act, out);
+    else cell_sweeps_2d<T, N>(t, X, AE, c, tl, act, out);
     if (act) {
       for (int f = fs; f < fe; ++f) {
         const int kind = __ldg(a.face_kind + f);

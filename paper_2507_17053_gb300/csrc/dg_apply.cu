@@ -41,13 +41,13 @@ template <typename T, int D, int N>
 __global__ void __launch_bounds__(DgShape<D, N>::CPB * DgShape<D, N>::L)
 dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
   constexpr int L = DgShape<D, N>::L, ND = DgShape<D, N>::ND, CPB = DgShape<D, N>::CPB;
+  using Pair2 = typename PairOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* X = reinterpret_cast<T*>(smem_raw);   // CPB tiles
-  T* A = X + CPB * ND;         // sweep buffers; A becomes the result tile
-  T* E = A + CPB * ND;
-  T* B = E + CPB * ND;
-  T* G = B + CPB * ND;
-  T* T1 = G + CPB * ND;        // face scratch, CPB * L each
+  Pair2* AE = reinterpret_cast<Pair2*>(smem_raw);  // sweep pairs; their storage then holds the result
+  Pair2* BG = AE + CPB * ND;
+  T* X = reinterpret_cast<T*>(BG + CPB * ND);   // CPB tiles
+  T* A = reinterpret_cast<T*>(AE);             // result tile (after the sweeps)
+  T* T1 = X + CPB * ND;        // face scratch, CPB * L each
   T* T2 = T1 + CPB * L;
   T* U1 = T2 + CPB * L;
   T* U2 = U1 + CPB * L;
@@ -71,8 +71,8 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
     // cell term (Algorithm 1), then park the x-line result in R (A is free
     // once every thread is past the sweeps)
     T out[N];
-    if (D == 3) cell_sweeps_3d<T, N>(t, X, A, E, B, G, c, tl, act, out);
-    else cell_sweeps_2d<T, N>(t, X, A, E, c, tl, act, out);
+    if (D == 3) cell_sweeps_3d<T, N>(t, X, AE, BG, c, tl, act, out);
+    else cell_sweeps_2d<T, N>(t, X, AE, c, tl, act, out);
     __syncthreads();
     if (act) {
 #pragma unroll

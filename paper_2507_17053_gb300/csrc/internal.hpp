@@ -131,6 +131,8 @@ template <> inline const float* face_phi_of<float>(const DeviceData& dd) { retur
 // SBM_FACE_TF32 or SBM_FACE_BF16; same output as launch_face_kernel.
 cudaError_t launch_tc_face_kernel(const HostProblem& hp, const DeviceData& dd, const float* x,
                                   float* out, int face_mode, cudaStream_t st);
+// One bounded mbarrier wait that expires (diagnostic of the timeout path).
+cudaError_t launch_timeout_selftest(int* err, cudaStream_t st);
 
 // Apply, CG: face kernel, cell kernel, assembly; T = double or float
 // (face_mode applies to float: SBM_FACE_FP32 / TF32 / BF16).

@@ -183,12 +183,30 @@ __device__ __forceinline__ void line_phase2(const KTab<T>& t, const T (&va)[N], 
 }
 
 // ---- cell term -------------------------------------------------------------
+//
+// Each phase produces two arrays for the next one ((a, e), then (b, g)); they
+// are stored interleaved as pairs, so one 8-byte (FP32) or 16-byte (FP64)
+// shared-memory access moves both values of a node.
 
-// 3D: three phases over z-, y- and x-lines.  `X` holds ncells tiles; the x-line
-// result of line `tl` of cell `c` is returned in out[].
+template <typename T>
+struct PairOf;
+template <>
+struct PairOf<float> {
+  using type = float2;
+};
+template <>
+struct PairOf<double> {
+  using type = double2;
+};
+
+// 3D: three phases over z-, y- and x-lines.  X holds ncells tiles; AE and BG
+// hold pairs.  The x-line result of line `tl` of cell `c` is returned in out[].
 template <typename T, int N>
-__device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, T* A, T* E, T* B,
-                                               T* G, int c, int tl, bool act, T (&out)[N]) {
+__device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X,
+                                               typename PairOf<T>::type* AE,
+                                               typename PairOf<T>::type* BG, int c, int tl,
+                                               bool act, T (&out)[N]) {
+  using P2 = typename PairOf<T>::type;
   constexpr int ND = N * N * N;
   if (act) {
     const int base = c * ND + (tl % N) + N * (tl / N);      // z-line (j0, j1)
@@ -197,10 +215,7 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, T* 
     for (int j = 0; j < N; ++j) v[j] = X[base + N * N * j];
     line_apply2<T, N>(t.M, t.fM, t.K, t.fK, v, a, e);
 #pragma unroll
-    for (int m = 0; m < N; ++m) {
-      A[base + N * N * m] = a[m];
-      E[base + N * N * m] = e[m];
-    }
+    for (int m = 0; m < N; ++m) AE[base + N * N * m] = P2{a[m], e[m]};
   }
   __syncthreads();
   if (act) {
@@ -208,15 +223,13 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, T* 
     T va[N], ve[N], b[N], g[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      va[j] = A[base + N * j];
-      ve[j] = E[base + N * j];
+      const P2 p = AE[base + N * j];
+      va[j] = p.x;
+      ve[j] = p.y;
     }
     line_phase2<T, N>(t, va, ve, b, g);
 #pragma unroll
-    for (int m = 0; m < N; ++m) {
-      B[base + N * m] = b[m];
-      G[base + N * m] = g[m];
-    }
+    for (int m = 0; m < N; ++m) BG[base + N * m] = P2{b[m], g[m]};
   }
   __syncthreads();
   if (act) {
@@ -224,8 +237,9 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, T* 
     T vb[N], vg[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      vb[j] = B[base + j];
-      vg[j] = G[base + j];
+      const P2 p = BG[base + j];
+      vb[j] = p.x;
+      vg[j] = p.y;
     }
     line_apply_sum<T, N>(t.Kh, t.fKh, vb, t.Mh, t.fMh, vg, out);
   }
@@ -233,8 +247,10 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, T* 
 
 // 2D: y-lines then x-lines.
 template <typename T, int N>
-__device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X, T* A, T* E, int c,
-                                               int tl, bool act, T (&out)[N]) {
+__device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X,
+                                               typename PairOf<T>::type* AE, int c, int tl,
+                                               bool act, T (&out)[N]) {
+  using P2 = typename PairOf<T>::type;
   constexpr int ND = N * N;
   if (act) {
     const int base = c * ND + tl;                           // y-line j0 = tl
@@ -243,10 +259,7 @@ __device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X, T* 
     for (int j = 0; j < N; ++j) v[j] = X[base + N * j];
     line_apply2<T, N>(t.M, t.fM, t.K, t.fK, v, a, e);
 #pragma unroll
-    for (int m = 0; m < N; ++m) {
-      A[base + N * m] = a[m];
-      E[base + N * m] = e[m];
-    }
+    for (int m = 0; m < N; ++m) AE[base + N * m] = P2{a[m], e[m]};
   }
   __syncthreads();
   if (act) {
@@ -254,8 +267,9 @@ __device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X, T* 
     T va[N], ve[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) {
-      va[j] = A[base + j];
-      ve[j] = E[base + j];
+      const P2 p = AE[base + j];
+      va[j] = p.x;
+      ve[j] = p.y;
     }
     line_apply_sum<T, N>(t.Kh, t.fKh, va, t.Mh, t.fMh, ve, out);
   }

@@ -293,6 +293,31 @@ tc_face_kernel(const TcArgs<float> a, const __grid_constant__ KTab<float> t) {
                  "r"(tc::kTmemCols));
 }
 
+// Diagnostic: wait (bounded, `limit` polls) on an mbarrier that nothing ever
+// arrives on, so the wait expires and the device error word gets
+// SBM_ERR_TIMEOUT -- the same path the tensor-core kernel takes when an MMA
+// never completes.  Exercises failure detection without faulting the GPU.
+__global__ void timeout_selftest_kernel(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    uint32_t ok = 0;
+    for (long long it = 0; it < limit && !ok; ++it)
+      asm volatile(
+          "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+          "selp.b32 %0, 1, 0, P1;\n\t}\n"
+          : "=r"(ok)
+          : "r"(smem_u32(&bar)), "r"(0u)
+          : "memory");
+    if (!ok) atomicExch(err, SBM_ERR_TIMEOUT);
+  }
+}
+
+cudaError_t launch_timeout_selftest(int* err, cudaStream_t st) {
+  timeout_selftest_kernel<<<1, 32, 0, st>>>(err, 1ll << 14);
+  return cudaGetLastError();
+}
+
 template <int KIND, int N>
 static cudaError_t tc_t(const HostProblem& hp, const DeviceData& dd, const float* x, float* out,
                         cudaStream_t st) {
