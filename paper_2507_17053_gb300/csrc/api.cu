@@ -102,7 +102,12 @@ static void free_device(DeviceData* dd) {
   cudaFree(dd->face_cell);
   cudaFree(dd->face_out);
   cudaFree(dd->face_out32);
-  cudaFree(dd->dof_colours);
+  for (auto& ct : dd->chunks) {
+    cudaFree(ct.first);
+    cudaFree(ct.colour);
+    cudaFree(ct.dof_mask);
+  }
+  cudaFree(dd->diag_pos);
   cudaFree(dd->err_flag);
   cudaFree(dd->ycol);
   cudaFree(dd->ycol32);
@@ -131,22 +136,48 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   dd->col_nint.assign(dd->ncolours, 0);
   dd->order.clear();
   dd->order.reserve(Nc);
-  for (int col = 0; col < dd->ncolours; ++col) {
-    dd->col_start[col] = (int)dd->order.size();
+  // CG chunk tables (host side): chunk start positions and colours
+  std::vector<int32_t> ch_first[2];
+  std::vector<uint8_t> ch_col[2];
+  if (hp.desc.dg) {
+    // DG: one launch over all cells, interior cells first
     for (int pass = 0; pass < 2; ++pass)
-      for (int64_t c = 0; c < Nc; ++c) {
-        int cc = 0;
-        if (!hp.desc.dg)
-          for (int l = 0; l < d; ++l) cc |= (hp.cells[c * d + l] & 1) << l;
-        if (cc != col) continue;
+      for (int64_t c = 0; c < Nc; ++c)
         if ((pass == 0) == (nf[c] == 0)) dd->order.push_back((int32_t)c);
-      }
     int nint = 0;
-    for (int i = dd->col_start[col]; i < (int)dd->order.size(); ++i)
-      if (nf[dd->order[i]] == 0) nint++;
-    dd->col_nint[col] = nint;
+    for (int64_t c = 0; c < Nc; ++c)
+      if (nf[c] == 0) nint++;
+    dd->col_nint[0] = nint;
+  } else {
+    // CG: cells in row-run order (rows lexicographic, x fastest); each run of
+    // consecutive active cells along x is cut into chunks of R (resp. R/2)
+    // cells; chunk colour = (index of the chunk within its run) mod 2 |
+    // (cy mod 2) << 1 | (cz mod 2) << 2
+    const int N = hp.N;
+    const int Rs[2] = {chunk_cells(d, n), std::max(1, chunk_cells(d, n) / 2)};
+    const int64_t nrows = (d == 3) ? (int64_t)N * N : N;
+    for (int64_t row = 0; row < nrows; ++row) {
+      const int cy = (int)(row % N), cz = (d == 3) ? (int)(row / N) : 0;
+      int cx = 0;
+      while (cx < N) {
+        if (hp.bg_to_cell[row * N + cx] < 0) { ++cx; continue; }
+        const int run0 = (int)dd->order.size();
+        while (cx < N && hp.bg_to_cell[row * N + cx] >= 0) {
+          dd->order.push_back(hp.bg_to_cell[row * N + cx]);
+          ++cx;
+        }
+        const int runlen = (int)dd->order.size() - run0;
+        for (int v = 0; v < 2; ++v)
+          for (int k = 0; k * Rs[v] < runlen; ++k) {
+            ch_first[v].push_back(run0 + k * Rs[v]);
+            ch_col[v].push_back((uint8_t)((k & 1) | ((cy & 1) << 1) | ((cz & 1) << 2)));
+          }
+      }
+    }
+    for (int v = 0; v < 2; ++v) ch_first[v].push_back((int32_t)dd->order.size());
   }
   dd->col_start[dd->ncolours] = (int)dd->order.size();
+  for (int col = 1; col < dd->ncolours; ++col) dd->col_start[col] = dd->col_start[dd->ncolours];
 
   std::vector<int32_t> lines_o, fstart(Nc + 1, 0), fkind, fcell;
   std::vector<double> fphi;
@@ -196,17 +227,43 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   if ((e = cudaMalloc((void**)&dd->err_flag, sizeof(int))) != cudaSuccess) goto err;
   if ((e = cudaMemset(dd->err_flag, 0, sizeof(int))) != cudaSuccess) goto err;
   if (!hp.desc.dg) {
-    // colour mask per DoF and the colour accumulation buffers
-    std::vector<uint8_t> mask(hp.n_dofs, 0);
-    for (int col = 0; col < dd->ncolours; ++col)
-      for (int i = dd->col_start[col]; i < dd->col_start[col + 1]; ++i) {
-        const int c = dd->order[i];
-        for (int line = 0; line < L; ++line) {
-          const int32_t g = hp.lines[(int64_t)c * L + line];
-          for (int m = 0; m < n; ++m) mask[g + m] |= (uint8_t)(1u << col);
+    // per chunking: chunk tables and the per-DoF colour masks
+    for (int v = 0; v < 2; ++v) {
+      std::vector<uint8_t> mask(hp.n_dofs, 0);
+      const int nch = (int)ch_col[v].size();
+      for (int k = 0; k < nch; ++k)
+        for (int i = ch_first[v][k]; i < ch_first[v][k + 1]; ++i) {
+          const int c = dd->order[i];
+          for (int line = 0; line < L; ++line) {
+            const int32_t g = hp.lines[(int64_t)c * L + line];
+            for (int m = 0; m < n; ++m) mask[g + m] |= (uint8_t)(1u << ch_col[v][k]);
+          }
+        }
+      dd->chunks[v].n = nch;
+      if ((e = upload(&dd->chunks[v].first, ch_first[v].data(), ch_first[v].size())) !=
+          cudaSuccess)
+        goto err;
+      if ((e = upload(&dd->chunks[v].colour, ch_col[v].data(), ch_col[v].size())) != cudaSuccess)
+        goto err;
+      if ((e = upload(&dd->chunks[v].dof_mask, mask.data(), mask.size())) != cudaSuccess)
+        goto err;
+    }
+    // ordered positions grouped by the parity colour of the cell (diagonal kernel)
+    {
+      std::vector<int32_t> pos;
+      dd->diag_col_start.assign(dd->ncolours + 1, 0);
+      for (int col = 0; col < dd->ncolours; ++col) {
+        dd->diag_col_start[col] = (int)pos.size();
+        for (int64_t i = 0; i < Nc; ++i) {
+          const int c = dd->order[i];
+          int cc = 0;
+          for (int l = 0; l < d; ++l) cc |= (hp.cells[(int64_t)c * d + l] & 1) << l;
+          if (cc == col) pos.push_back((int32_t)i);
         }
       }
-    if ((e = upload(&dd->dof_colours, mask.data(), mask.size())) != cudaSuccess) goto err;
+      dd->diag_col_start[dd->ncolours] = (int)pos.size();
+      if ((e = upload(&dd->diag_pos, pos.data(), pos.size())) != cudaSuccess) goto err;
+    }
     const size_t nb = (size_t)dd->ncolours * hp.n_dofs;
     if ((e = cudaMalloc((void**)&dd->ycol, nb * sizeof(double))) != cudaSuccess) goto err;
     if ((e = cudaMalloc((void**)&dd->ycol32, nb * sizeof(float))) != cudaSuccess) goto err;

@@ -1,42 +1,57 @@
 // Matrix-free apply (FP64 or FP32) of the continuous Galerkin SBM operator.
 //
 // One apply = three launches:
-//  1. the surrogate-face kernel (face_kernel.cu): every face into per-face
-//     scratch;
-//  2. the cell kernel over ALL active cells: gather, cell sweeps
-//     (Algorithm 1), fold in the cell's surrogate faces, and a plain store of
-//     the local result into the accumulation buffer of the cell's colour.
-//     Colours are the 2^d parity patterns of the cell indices; two cells of
-//     one colour share no DoF, so every store has a single writer;
+//  1. the surrogate-face kernel (face_kernel.cu, or tc_face.cu on the tensor
+//     cores): every face into per-face scratch;
+//  2. the chunk kernel.  Active cells are cut into chunks: up to R
+//     consecutive active cells of one x-row of the mesh.  In the compact DoF
+//     numbering the x-lines of consecutive active cells continue each other,
+//     so the chunk's line (j1, j2) is one contiguous run of p*nc + 1 values:
+//     the block gathers those runs coalesced, runs the cell sweeps
+//     (Algorithm 1) for each cell, folds in the cells' surrogate faces, sums
+//     the values of the x-face nodes its consecutive cells share in shared
+//     memory, and writes each run once, coalesced, into the accumulation
+//     buffer of the chunk's colour.  A chunk's colour is (its parity within
+//     its row run, cy mod 2[, cz mod 2]); chunks of one colour share no DoF,
+//     so every buffer element has a single writer;
 //  3. the assembly kernel: y_i = sum over the colours that touch DoF i (a
 //     per-DoF bit mask) of buffer_c[i], in fixed colour order.
 // No atomics, no read-modify-write, no y = 0 fill; repeated applies are
-// bitwise equal.  One launch over all cells keeps many independent blocks in
-// flight, so the gather latency of some overlaps the arithmetic of others.
+// bitwise equal.
 #include <algorithm>
 
 #include "sweeps.cuh"
 
 namespace sbm {
 
+template <int D, int N>
+struct ChunkShape {
+  static constexpr int L = Shape<D, N>::L;
+  static constexpr int R = (256 / L) > 0 ? (256 / L) : 1;     // cells per chunk
+};
+
+int chunk_cells(int d, int n) {
+  const int L = (d == 3) ? n * n : n;
+  return (256 / L) > 0 ? (256 / L) : 1;
+}
+
 CellLaunch cell_launch_shape(int d, int n) {
-  int L = (d == 3) ? n * n : n;
-  int cpb = 128 / L;
-  if (cpb < 1) cpb = 1;
-  return CellLaunch{d, n, cpb, cpb * L};
+  const int r = chunk_cells(d, n);
+  return CellLaunch{d, n, r, r * ((d == 3) ? n * n : n)};
 }
 
 template <typename T>
-struct CgArgs {
+struct ChunkArgs {
   const T* __restrict__ x;
   T* __restrict__ ycol;                    // [ncolours][n_dofs] accumulation buffers
   const int32_t* __restrict__ lines;       // ordered cells x L
   const int32_t* __restrict__ face_start;  // ordered cells + 1
   const int32_t* __restrict__ face_kind;
   const T* __restrict__ face_out;          // [F][2L] from the face kernel
+  const int32_t* __restrict__ chunk_first; // [nchunk + 1] first ordered cell of each chunk
+  const uint8_t* __restrict__ chunk_col;   // [nchunk] colour of each chunk
   int64_t n_dofs;
-  int ncell;                               // all active cells
-  int col_start[9];                        // ordered cells are grouped by colour
+  int nchunk;
   // right-hand side blockIdx.y of a multi-RHS launch: offsets of its x, its
   // colour buffers and its face results (0 for a single right-hand side)
   int64_t ldx, ld_ycol, ld_face;
@@ -73,102 +88,78 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
   }
 }
 
-// Every block walks over tiles of CPB cells (tile = blockIdx.x, then +
-// gridDim.x, ...).  While a tile is in the sweeps, the x-lines of the block's
-// next tile are already being loaded into registers, so the gather latency
-// of one tile hides behind the arithmetic of the previous one.
-template <typename T, int D, int N, int CPB = Shape<D, N>::CPB>
-__global__ void __launch_bounds__(CPB * Shape<D, N>::L)
-cg_apply_kernel(const CgArgs<T> a, const __grid_constant__ KTab<T> t) {
-  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
+template <typename T, int D, int N, int R>
+struct ChunkSmem {
+  static constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
+  static constexpr int SM0 = (N - 1) * R + 1;
+  static constexpr int SM = (SM0 % 2) ? SM0 : SM0 + 1;        // odd row stride of the runs
+  static constexpr size_t bytes = (size_t)(4 * R * ND + L * SM + R * L * N) * sizeof(T);
+};
+
+template <typename T, int D, int N, int R>
+__global__ void __launch_bounds__(R * Shape<D, N>::L)
+cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
+  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, P = N - 1;
+  constexpr int SM = ChunkSmem<T, D, N, R>::SM;
   using P2 = typename PairOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  P2* AE = reinterpret_cast<P2*>(smem_raw);     // pair arrays first: 8/16-byte aligned
-  P2* BG = AE + CPB * ND;
-  T* X = reinterpret_cast<T*>(BG + CPB * ND);
+  P2* AE = reinterpret_cast<P2*>(smem_raw);   // pair tiles first (8/16-byte aligned)
+  P2* BG = AE + R * ND;
+  T* Xs = reinterpret_cast<T*>(BG + R * ND);  // [L][SM] the chunk's x-line runs
+  T* Z = Xs + L * SM;                         // [R][L][N] per-cell x-line results
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
-  const int ntiles = (a.ncell + CPB - 1) / CPB;
   const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
   const T* fo = a.face_out + blockIdx.y * a.ld_face;
   T* ycb = a.ycol + blockIdx.y * a.ld_ycol;
 
-  // registers of the tile in flight: its x-line, its index, its face range
-  int tile = blockIdx.x;
-  int cell = tile * CPB + c;
-  bool act = tile < ntiles && cell < a.ncell;
-  int g0 = 0, fs = 0, fe = 0;
-  T v[N];
-  if (act) {
-    g0 = __ldg(a.lines + (size_t)cell * L + tl);
-#pragma unroll
-    for (int m = 0; m < N; ++m) v[m] = __ldg(xr + g0 + m);
-    fs = __ldg(a.face_start + cell);
-    fe = __ldg(a.face_start + cell + 1);
-  }
-  while (tile < ntiles) {
-    if (act) {
-#pragma unroll
-      for (int m = 0; m < N; ++m) X[c * ND + N * tl + m] = v[m];
+  for (int ch = blockIdx.x; ch < a.nchunk; ch += gridDim.x) {
+    const int first = __ldg(a.chunk_first + ch);
+    const int nc = __ldg(a.chunk_first + ch + 1) - first;
+    const int S = P * nc + 1;                 // values per x-line run
+    const int* lines0 = a.lines + (size_t)first * L;
+    // coalesced gather of the L runs
+    for (int idx = tid; idx < L * S; idx += blockDim.x) {
+      const int l = idx / S, kk = idx - l * S;
+      Xs[l * SM + kk] = __ldg(xr + __ldg(lines0 + l) + kk);
     }
     __syncthreads();
-    // prefetch the next tile
-    const int ntile = tile + gridDim.x;
-    const int ncell_ = ntile * CPB + c;
-    const bool nact = ntile < ntiles && ncell_ < a.ncell;
-    int ng0 = 0, nfs = 0, nfe = 0;
-    if (nact) {
-      ng0 = __ldg(a.lines + (size_t)ncell_ * L + tl);
-#pragma unroll
-      for (int m = 0; m < N; ++m) v[m] = __ldg(xr + ng0 + m);
-      nfs = __ldg(a.face_start + ncell_);
-      nfe = __ldg(a.face_start + ncell_ + 1);
-    }
+    const bool act = c < nc;
     T out[N];
-    if (D == 3) cell_sweeps_3d<T, N>(t, X, AE, BG, c, tl, act, out);
-    else cell_sweeps_2d<T, N>(t, X, AE, c, tl, act, out);
+    if (D == 3)
+      cell_sweeps_3d<T, N>(t, Xs, (tl / N) * SM + P * c + (tl % N), N * SM, AE, BG, c, tl, act,
+                           out);
+    else
+      cell_sweeps_2d<T, N>(t, Xs, P * c + tl, SM, AE, c, tl, act, out);
     if (act) {
+      const int pos = first + c;
+      const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);
       for (int f = fs; f < fe; ++f) {
         const int kind = __ldg(a.face_kind + f);
         fold_face<T, D, N>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, tl, out);
       }
-      int col = 0;             // cells are ordered by colour; unrolled: no local copy
 #pragma unroll
-      for (int k = 1; k < 8; ++k) col += (cell >= a.col_start[k]) ? 1 : 0;
-      T* yc = ycb + (size_t)col * a.n_dofs + g0;
-#pragma unroll
-      for (int m = 0; m < N; ++m) yc[m] = out[m];
+      for (int m = 0; m < N; ++m) Z[(c * L + tl) * N + m] = out[m];
     }
-    tile = ntile;
-    cell = ncell_;
-    act = nact;
-    g0 = ng0;
-    fs = nfs;
-    fe = nfe;
+    __syncthreads();
+    // runs of the result: the node shared by cells c-1 and c is the sum of
+    // their two values (fixed order), then one coalesced store per run
+    T* yc = ycb + (size_t)__ldg(a.chunk_col + ch) * a.n_dofs;
+    for (int idx = tid; idx < L * S; idx += blockDim.x) {
+      const int l = idx / S, kk = idx - l * S;
+      const int cc = kk / P, m = kk - cc * P;
+      T v;
+      if (cc == nc) v = Z[((nc - 1) * L + l) * N + P];
+      else if (m == 0 && cc > 0) v = Z[((cc - 1) * L + l) * N + P] + Z[(cc * L + l) * N];
+      else v = Z[(cc * L + l) * N + m];
+      yc[__ldg(lines0 + l) + kk] = v;
+    }
+    __syncthreads();                          // Xs / Z are reused by the next chunk
   }
 }
 
-// Blocks of the cell kernel: enough to fill every SM at the kernel's
-// occupancy (so each block walks over several tiles), capped by the tiles.
-template <typename T, int D, int N, int CPB>
-static int cell_grid(int ntiles, size_t smem) {
-  static int per_sm = 0, sms = 0;
-  if (per_sm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_apply_kernel<T, D, N, CPB>,
-                                                      CPB * Shape<D, N>::L, smem) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
-  }
-  const int g = per_sm * sms;
-  return ntiles < g ? ntiles : g;
-}
-
-// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order.  One DoF
-// per thread (all of its loads in flight at once); the buffers are read once.
-// Adding 0.0 is exact, so y_i equals the plain sum over the set colours; the
+// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order.  Adding
+// 0.0 is exact, so this equals the plain sum over the set colours; the
 // additions of a colour that no lane of the warp has are skipped (on GB300
 // every double addition costs an FP64-pipe slot).
 template <typename T>
@@ -190,41 +181,73 @@ __global__ void assemble_kernel(const T* __restrict__ ycol, const uint8_t* __res
   if (i < n) __stcs(y + i, acc);
 }
 
-template <typename T, int D, int N>
-static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            cudaStream_t st, Profiler* prof, int face_mode) {
-  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, CPB = Shape<D, N>::CPB;
+// Blocks of the chunk kernel: 4 x (resident blocks per SM) x SMs at most
+// (each block walks over several chunks), capped by the number of chunks.
+template <typename T, int D, int N, int R>
+static cudaError_t chunk_prepare(int* grid_cap) {
+  static int per_sm = 0, sms = 0;
+  static cudaError_t attr = cudaSuccess;
+  constexpr size_t smem = ChunkSmem<T, D, N, R>::bytes;
+  if (per_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > 48 * 1024)
+      attr = cudaFuncSetAttribute(cg_chunk_kernel<T, D, N, R>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_chunk_kernel<T, D, N, R>,
+                                                      R * Shape<D, N>::L, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  *grid_cap = 4 * per_sm * sms;
+  return attr;
+}
+
+// face stage + chunk kernel + assembly, with explicit scratch and nrhs
+// right-hand sides (x, y: nrhs vectors ld apart).
+template <typename T, int D, int N, int R>
+static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const ChunkTable& ct,
+                           const T* x, T* y, int64_t ld, int nrhs, T* fo, T* ycol, int face_mode,
+                           cudaStream_t st, Profiler* prof) {
+  constexpr int L = Shape<D, N>::L;
   const KTab<T> t = make_ktab<T>(hp);
-  const size_t smem = (size_t)(5 * CPB * ND) * sizeof(T);
-  T* fo = face_out_of<T>(dd);
-  T* ycol = ycol_of<T>(dd);
+  constexpr size_t smem = ChunkSmem<T, D, N, R>::bytes;
   cudaError_t err;
   const bool pr = prof && prof->on;
-  if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   int nlaunch = 0;
+  if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   if (dd.nface > 0) {
-    if ((err = launch_faces<T>(hp, dd, x, fo, face_mode, st)) != cudaSuccess) return err;
+    err = (nrhs == 1) ? launch_faces<T>(hp, dd, x, fo, face_mode, st)
+                      : launch_face_kernel_multi<T>(hp, dd, x, ld, nrhs, fo, st);
+    if (err != cudaSuccess) return err;
     nlaunch++;
   }
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
-  CgArgs<T> a;
+  int cap = 0;
+  if ((err = chunk_prepare<T, D, N, R>(&cap)) != cudaSuccess) return err;
+  ChunkArgs<T> a;
   a.x = x;
   a.ycol = ycol;
   a.lines = dd.lines;
   a.face_start = dd.face_start;
   a.face_kind = dd.face_kind;
   a.face_out = fo;
+  a.chunk_first = ct.first;
+  a.chunk_col = ct.colour;
   a.n_dofs = hp.n_dofs;
-  a.ncell = dd.col_start[dd.ncolours];
-  for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
-  a.ldx = a.ld_ycol = a.ld_face = 0;
-  cg_apply_kernel<T, D, N><<<cell_grid<T, D, N, CPB>((a.ncell + CPB - 1) / CPB, smem), CPB * L, smem,
-                             st>>>(a, t);
+  a.nchunk = ct.n;
+  a.ldx = ld;
+  a.ld_ycol = (int64_t)dd.ncolours * hp.n_dofs;
+  a.ld_face = (int64_t)dd.nface * 2 * L;
+  const int grid = std::min(ct.n, cap);
+  cg_chunk_kernel<T, D, N, R><<<dim3(grid, nrhs), R * L, smem, st>>>(a, t);
   nlaunch++;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   const int64_t n = hp.n_dofs;
-  assemble_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ycol, dd.dof_colours, y, n,
-                                                                   dd.ncolours);
+  assemble_kernel<T><<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(
+      ycol, ct.dof_mask, y, n, dd.ncolours, (int64_t)dd.ncolours * n, ld);
   nlaunch++;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (pr) {
@@ -234,115 +257,66 @@ static cudaError_t launch_t(const HostProblem& hp, const DeviceData& dd, const T
   return cudaSuccess;
 }
 
-// The same three launches with caller-provided scratch: per-face results `fo`
-// ([F][2L]) and colour buffers `ycol` ([ncolours][n_dofs]).
+// variant 0: R cells per chunk; variant 1: R/2 (a second tile shape for the
+// autotuner).  Both chunkings are built at set-up with the same colouring
+// rule, so the two variants give bitwise-equal results.
 template <typename T, int D, int N>
-static cudaError_t launch_scratch_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                                    T* fo, T* ycol, cudaStream_t st) {
-  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, CPB = Shape<D, N>::CPB;
-  const KTab<T> t = make_ktab<T>(hp);
-  const size_t smem = (size_t)(5 * CPB * ND) * sizeof(T);
-  cudaError_t err;
-  if (dd.nface > 0 && (err = launch_face_kernel<T>(hp, dd, x, fo, st)) != cudaSuccess) return err;
-  CgArgs<T> a;
-  a.x = x;
-  a.ycol = ycol;
-  a.lines = dd.lines;
-  a.face_start = dd.face_start;
-  a.face_kind = dd.face_kind;
-  a.face_out = fo;
-  a.n_dofs = hp.n_dofs;
-  a.ncell = dd.col_start[dd.ncolours];
-  for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
-  a.ldx = a.ld_ycol = a.ld_face = 0;
-  cg_apply_kernel<T, D, N><<<cell_grid<T, D, N, CPB>((a.ncell + CPB - 1) / CPB, smem), CPB * L, smem,
-                             st>>>(a, t);
-  const int64_t n = hp.n_dofs;
-  assemble_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ycol, dd.dof_colours, y, n,
-                                                                   dd.ncolours);
-  return cudaGetLastError();
+static cudaError_t apply_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                           int64_t ld, int nrhs, T* fo, T* ycol, int face_mode, int variant,
+                           cudaStream_t st, Profiler* prof) {
+  constexpr int R = ChunkShape<D, N>::R;
+  constexpr int RH = (R / 2) > 0 ? R / 2 : 1;
+  if (variant == 1 && RH < R)
+    return apply_r<T, D, N, RH>(hp, dd, dd.chunks[1], x, y, ld, nrhs, fo, ycol, face_mode, st,
+                                prof);
+  return apply_r<T, D, N, R>(hp, dd, dd.chunks[0], x, y, ld, nrhs, fo, ycol, face_mode, st,
+                             prof);
 }
 
 template <typename T>
-cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                                    T* face_scratch, T* colour_scratch, cudaStream_t st) {
-#define SBM_CASE(DD, NN)                                                                    \
-  if (hp.d == DD && hp.n == NN)                                                             \
-    return launch_scratch_t<T, DD, NN>(hp, dd, x, y, face_scratch, colour_scratch, st);
+static cudaError_t dispatch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                            int64_t ld, int nrhs, T* fo, T* ycol, int face_mode, int variant,
+                            cudaStream_t st, Profiler* prof) {
+#define SBM_CASE(DD, NN)                                                                  \
+  if (hp.d == DD && hp.n == NN)                                                           \
+    return apply_t<T, DD, NN>(hp, dd, x, y, ld, nrhs, fo, ycol, face_mode, variant, st, prof);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE
   return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                            cudaStream_t st, Profiler* prof, int face_mode) {
+  return dispatch<T>(hp, dd, x, y, 0, 1, face_out_of<T>(dd), ycol_of<T>(dd), face_mode, 0, st,
+                     prof);
+}
+template cudaError_t launch_cg_apply<double>(const HostProblem&, const DeviceData&,
+                                             const double*, double*, cudaStream_t, Profiler*,
+                                             int);
+template cudaError_t launch_cg_apply<float>(const HostProblem&, const DeviceData&, const float*,
+                                            float*, cudaStream_t, Profiler*, int);
+
+// The same launches with caller-provided scratch: per-face results
+// ([F][2L]) and colour buffers ([ncolours][n_dofs]).
+template <typename T>
+cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                                    T* face_scratch, T* colour_scratch, cudaStream_t st) {
+  return dispatch<T>(hp, dd, x, y, 0, 1, face_scratch, colour_scratch, 0, 0, st, nullptr);
 }
 template cudaError_t launch_cg_apply_scratch<double>(const HostProblem&, const DeviceData&,
                                                      const double*, double*, double*, double*,
                                                      cudaStream_t);
 
-// nrhs right-hand sides in one set of launches (grid.y = right-hand side):
-// x and y hold nrhs vectors of n_dofs each, ld apart; the scratch holds nrhs
-// copies.  variant 0/1 picks the cells-per-block of the cell kernel (128 or
-// 256 threads' worth of lines), chosen by the autotuner.
-template <typename T, int D, int N, int CPB>
-static cudaError_t multi_cell_t(const HostProblem& hp, const DeviceData& dd, const T* x, int64_t ld,
-                                int nrhs, T* fo, T* ycol, cudaStream_t st) {
-  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
-  const KTab<T> t = make_ktab<T>(hp);
-  const size_t smem = (size_t)(5 * CPB * ND) * sizeof(T);
-  cudaError_t err;
-  if (smem > 48 * 1024 &&
-      (err = cudaFuncSetAttribute(cg_apply_kernel<T, D, N, CPB>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-          cudaSuccess)
-    return err;
-  CgArgs<T> a;
-  a.x = x;
-  a.ycol = ycol;
-  a.lines = dd.lines;
-  a.face_start = dd.face_start;
-  a.face_kind = dd.face_kind;
-  a.face_out = fo;
-  a.n_dofs = hp.n_dofs;
-  a.ncell = dd.col_start[dd.ncolours];
-  for (int c = 0; c < 9; ++c) a.col_start[c] = dd.col_start[c < dd.ncolours ? c : dd.ncolours];
-  a.ldx = ld;
-  a.ld_ycol = (int64_t)dd.ncolours * hp.n_dofs;
-  a.ld_face = (int64_t)dd.nface * 2 * L;
-  cg_apply_kernel<T, D, N, CPB>
-      <<<dim3(cell_grid<T, D, N, CPB>((a.ncell + CPB - 1) / CPB, smem), nrhs), CPB * L, smem, st>>>(
-          a, t);
-  return cudaGetLastError();
-}
-
-template <typename T, int D, int N>
-static cudaError_t multi_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                           int64_t ld, int nrhs, T* fo, T* ycol, int variant, cudaStream_t st) {
-  constexpr int L = Shape<D, N>::L;
-  cudaError_t err;
-  if (dd.nface > 0 &&
-      (err = launch_face_kernel_multi<T>(hp, dd, x, ld, nrhs, fo, st)) != cudaSuccess)
-    return err;
-  if (variant == 1 && 256 / L > Shape<D, N>::CPB)
-    err = multi_cell_t<T, D, N, (256 / L > 0 ? 256 / L : 1)>(hp, dd, x, ld, nrhs, fo, ycol, st);
-  else
-    err = multi_cell_t<T, D, N, Shape<D, N>::CPB>(hp, dd, x, ld, nrhs, fo, ycol, st);
-  if (err != cudaSuccess) return err;
-  const int64_t n = hp.n_dofs;
-  assemble_kernel<T><<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(
-      ycol, dd.dof_colours, y, n, dd.ncolours, (int64_t)dd.ncolours * n, ld);
-  return cudaGetLastError();
-}
-
+// nrhs right-hand sides in one set of launches (grid.y = right-hand side);
+// variant 0/1: R or R/2 cells per chunk (chosen by the autotuner).
 template <typename T>
 cudaError_t launch_cg_apply_multi(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                                   int64_t ld, int nrhs, T* face_scratch, T* colour_scratch,
                                   int variant, cudaStream_t st) {
-#define SBM_CASE(DD, NN)                                                                   \
-  if (hp.d == DD && hp.n == NN)                                                            \
-    return multi_t<T, DD, NN>(hp, dd, x, y, ld, nrhs, face_scratch, colour_scratch, variant, st);
-  SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
-  SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
-#undef SBM_CASE
-  return cudaErrorInvalidValue;
+  return dispatch<T>(hp, dd, x, y, ld, nrhs, face_scratch, colour_scratch, 0, variant, st,
+                     nullptr);
 }
 template cudaError_t launch_cg_apply_multi<double>(const HostProblem&, const DeviceData&,
                                                    const double*, double*, int64_t, int, double*,
@@ -350,21 +324,5 @@ template cudaError_t launch_cg_apply_multi<double>(const HostProblem&, const Dev
 template cudaError_t launch_cg_apply_multi<float>(const HostProblem&, const DeviceData&,
                                                   const float*, float*, int64_t, int, float*,
                                                   float*, int, cudaStream_t);
-
-template <typename T>
-cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            cudaStream_t st, Profiler* prof, int face_mode) {
-#define SBM_CASE(DD, NN) \
-  if (hp.d == DD && hp.n == NN) return launch_t<T, DD, NN>(hp, dd, x, y, st, prof, face_mode);
-  SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
-  SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
-#undef SBM_CASE
-  return cudaErrorInvalidValue;
-}
-template cudaError_t launch_cg_apply<double>(const HostProblem&, const DeviceData&,
-                                             const double*, double*, cudaStream_t, Profiler*,
-                                             int);
-template cudaError_t launch_cg_apply<float>(const HostProblem&, const DeviceData&, const float*,
-                                            float*, cudaStream_t, Profiler*, int);
 
 }  // namespace sbm

@@ -71,8 +71,10 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
     // cell term (Algorithm 1), then park the x-line result in R (A is free
     // once every thread is past the sweeps)
     T out[N];
-    if (D == 3) cell_sweeps_3d<T, N>(t, X, AE, BG, c, tl, act, out);
-    else cell_sweeps_2d<T, N>(t, X, AE, c, tl, act, out);
+    if (D == 3)
+      cell_sweeps_3d<T, N>(t, X, c * ND + (tl % N) + N * (tl / N), N * N, AE, BG, c, tl, act, out);
+    else
+      cell_sweeps_2d<T, N>(t, X, c * ND + tl, N, AE, c, tl, act, out);
     __syncthreads();
     if (act) {
 #pragma unroll

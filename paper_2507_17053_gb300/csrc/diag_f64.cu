@@ -20,6 +20,7 @@ struct DiagArgs {
   const int32_t* __restrict__ face_kind;
   const double* __restrict__ face_phi;
   const int32_t* __restrict__ nbr;         // DG neighbours (null for CG)
+  const int32_t* __restrict__ pos;         // CG: ordered positions of this colour's cells
   int cell0, ncell, dg;
   double sigma_f;                          // DG interior penalty
 };
@@ -27,7 +28,7 @@ struct DiagArgs {
 template <int D, int N>
 __global__ void diag_f64_kernel(const DiagArgs a, const __grid_constant__ KTab<double> t) {
   constexpr int L = (D == 3) ? N * N : N, ND = L * N;
-  const int cell = a.cell0 + blockIdx.x;
+  const int cell = a.pos ? a.pos[a.cell0 + blockIdx.x] : a.cell0 + blockIdx.x;
   for (int j = threadIdx.x; j < ND; j += blockDim.x) {
     int jj[3] = {j % N, (j / N) % N, (D == 3) ? j / (N * N) : 0};
     // cell term: h^(d-2) sum_k prod_l (k == l ? K : M)
@@ -97,8 +98,9 @@ static cudaError_t diag_t(const HostProblem& hp, const DeviceData& dd, double* d
     err = cudaMemsetAsync(diag, 0, (size_t)hp.n_dofs * sizeof(double), st);
     if (err != cudaSuccess) return err;
   }
+  const std::vector<int>& cs = hp.desc.dg ? dd.col_start : dd.diag_col_start;
   for (int c = 0; c < dd.ncolours; ++c) {
-    const int n = dd.col_start[c + 1] - dd.col_start[c];
+    const int n = cs[c + 1] - cs[c];
     if (n == 0) continue;
     DiagArgs a;
     a.diag = diag;
@@ -108,7 +110,8 @@ static cudaError_t diag_t(const HostProblem& hp, const DeviceData& dd, double* d
     a.face_kind = dd.face_kind;
     a.face_phi = dd.face_phi;
     a.nbr = dd.nbr;
-    a.cell0 = dd.col_start[c];
+    a.cell0 = cs[c];
+    a.pos = hp.desc.dg ? nullptr : dd.diag_pos;
     a.ncell = n;
     a.dg = hp.desc.dg;
     a.sigma_f = hp.sigma_f;

@@ -47,6 +47,14 @@ struct KTab {
 template <typename T>
 KTab<T> make_ktab(const HostProblem& hp);
 
+// CG chunking: runs of up to R consecutive active cells of one x-row.
+struct ChunkTable {
+  int n = 0;
+  int32_t* first = nullptr;      // [n + 1] first ordered cell of each chunk
+  uint8_t* colour = nullptr;     // [n] colour of each chunk
+  uint8_t* dof_mask = nullptr;   // [n_dofs] bit c set if a chunk of colour c touches the DoF
+};
+
 // Device-resident set-up data of one problem.
 struct DeviceData {
   // cells in kernel order: for each colour (CG) -- interior cells, then cells
@@ -64,7 +72,9 @@ struct DeviceData {
   double* face_out = nullptr;    // [F * 2L] per-face results of the face kernel (scratch)
   float* face_out32 = nullptr;
   int* err_flag = nullptr;       // device error word (SBM_ERR_TIMEOUT from bounded waits)
-  uint8_t* dof_colours = nullptr;  // CG [n_dofs]: bit c set if a cell of colour c touches the DoF
+  ChunkTable chunks[2];          // CG: R and R/2 cells per chunk (two tile shapes)
+  int32_t* diag_pos = nullptr;   // CG: ordered positions grouped by cell parity (diagonal)
+  std::vector<int> diag_col_start;
   double* ycol = nullptr;        // CG [ncolours * n_dofs] colour accumulation buffers (scratch)
   float* ycol32 = nullptr;
   double* face_phi = nullptr;    // [F * Q * d * n] phi_j(xi_{q,l}) at the shifted points
@@ -94,6 +104,7 @@ struct CellLaunch {
   int threads;      // block size
 };
 CellLaunch cell_launch_shape(int d, int n);
+int chunk_cells(int d, int n);    // R: cells per chunk of the CG chunk kernel
 
 // Record an error detail for sbm_last_error_detail() and return the code.
 int sbm_fail_detail(int code, const std::string& msg);

@@ -199,10 +199,12 @@ struct PairOf<double> {
   using type = double2;
 };
 
-// 3D: three phases over z-, y- and x-lines.  X holds ncells tiles; AE and BG
-// hold pairs.  The x-line result of line `tl` of cell `c` is returned in out[].
+// 3D: three phases over z-, y- and x-lines.  The z-line (j0, j1) = line tl of
+// cell c is read from X[xb + xs * j2] (the caller's tile layout); AE and BG
+// hold per-cell pair tiles.  The x-line result of line `tl` of cell `c` is
+// returned in out[].
 template <typename T, int N>
-__device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X,
+__device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, int xb, int xs,
                                                typename PairOf<T>::type* AE,
                                                typename PairOf<T>::type* BG, int c, int tl,
                                                bool act, T (&out)[N]) {
@@ -212,7 +214,7 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X,
     const int base = c * ND + (tl % N) + N * (tl / N);      // z-line (j0, j1)
     T v[N], a[N], e[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = X[base + N * N * j];
+    for (int j = 0; j < N; ++j) v[j] = X[xb + xs * j];
     line_apply2<T, N>(t.M, t.fM, t.K, t.fK, v, a, e);
 #pragma unroll
     for (int m = 0; m < N; ++m) AE[base + N * N * m] = P2{a[m], e[m]};
@@ -245,9 +247,10 @@ __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X,
   }
 }
 
-// 2D: y-lines then x-lines.
+// 2D: y-lines then x-lines; the y-line j0 = tl of cell c is read from
+// X[xb + xs * j1].
 template <typename T, int N>
-__device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X,
+__device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X, int xb, int xs,
                                                typename PairOf<T>::type* AE, int c, int tl,
                                                bool act, T (&out)[N]) {
   using P2 = typename PairOf<T>::type;
@@ -256,7 +259,7 @@ __device__ __forceinline__ void cell_sweeps_2d(const KTab<T>& t, const T* X,
     const int base = c * ND + tl;                           // y-line j0 = tl
     T v[N], a[N], e[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = X[base + N * j];
+    for (int j = 0; j < N; ++j) v[j] = X[xb + xs * j];
     line_apply2<T, N>(t.M, t.fM, t.K, t.fK, v, a, e);
 #pragma unroll
     for (int m = 0; m < N; ++m) AE[base + N * m] = P2{a[m], e[m]};
