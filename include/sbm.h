@@ -319,6 +319,18 @@ int sbm_profile_read(sbm_problem* prob, double* phase_ms, int64_t* launches);
 int sbm_device_status(sbm_problem* prob);
 
 /*
+ * Tile-shape autotuner for the single applies (continuous Galerkin; a no-op
+ * for DG): times the cell kernel with chunks of R and of R/2 cells, in FP64
+ * and in FP32, on this problem (temporary device buffers of n_dofs doubles,
+ * freed before returning), and keeps the faster shape per precision.  Both
+ * shapes compute the same operator; results differ only in the rounding of
+ * the few shared nodes that one shape sums in shared memory and the other in
+ * the assembly.  *shape64 / *shape32 (may be NULL) receive the choices (0 or
+ * 1).  Synchronous, legacy default stream.
+ */
+int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32);
+
+/*
  * Diagnostic of the failure path (the paper has no counterpart): enqueue one
  * device-side bounded wait on a barrier that nothing releases.  The wait
  * gives up after a fixed number of polls (well under a second), records

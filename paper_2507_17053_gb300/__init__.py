@@ -89,6 +89,8 @@ _SIGS = {
     "sbm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_i64p]),
     "sbm_device_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "sbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]),
     "sbm_selftest_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sbm_last_error_detail": (ctypes.c_char_p, []),
@@ -256,6 +258,12 @@ def sbm_interpolate(handle: int, manufactured: int, u_host) -> None:
 
 def sbm_device_status(handle: int) -> None:
     _check(lib().sbm_device_status(handle), "sbm_device_status")
+
+
+def sbm_autotune(handle: int) -> tuple[int, int]:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sbm_autotune(handle, ctypes.byref(a), ctypes.byref(b)), "sbm_autotune")
+    return a.value, b.value
 
 
 def sbm_selftest_timeout(handle: int, stream=None) -> None:

@@ -554,6 +554,59 @@ int sbm_device_status(sbm_problem* prob) {
   return SBM_OK;
 }
 
+// time both tile shapes of the single apply, in FP64 and FP32, on the
+// problem itself, and keep the faster of each
+int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (prob->hp.desc.dg) {
+    if (shape64) *shape64 = 0;
+    if (shape32) *shape32 = 0;
+    return SBM_OK;
+  }
+  const size_t n = (size_t)prob->hp.n_dofs;
+  void *x = nullptr, *y = nullptr;
+  cudaError_t e = cudaMalloc(&x, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&y, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(x, 0, n * sizeof(double));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int prec = 0; prec < 2 && e == cudaSuccess; ++prec) {
+    float best = 1e30f;
+    int bestv = 0;
+    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+      prob->dd.variant[prec] = v;
+      float tot = 0.f;
+      for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, 0);
+        e = prec == 0 ? launch_cg_apply<double>(prob->hp, prob->dd, (const double*)x, (double*)y,
+                                                0, nullptr)
+                      : launch_cg_apply<float>(prob->hp, prob->dd, (const float*)x, (float*)y, 0,
+                                               nullptr);
+        cudaEventRecord(e1, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep >= 2) tot += ms;
+      }
+      if (tot < best) {
+        best = tot;
+        bestv = v;
+      }
+    }
+    prob->dd.variant[prec] = bestv;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  if (e != cudaSuccess) return cuda_fail(e, "sbm_autotune");
+  if (shape64) *shape64 = prob->dd.variant[0];
+  if (shape32) *shape32 = prob->dd.variant[1];
+  return SBM_OK;
+}
+
 int sbm_selftest_timeout(sbm_problem* prob, void* stream) {
   if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");

@@ -289,8 +289,8 @@ static cudaError_t dispatch(const HostProblem& hp, const DeviceData& dd, const T
 template <typename T>
 cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                             cudaStream_t st, Profiler* prof, int face_mode) {
-  return dispatch<T>(hp, dd, x, y, 0, 1, face_out_of<T>(dd), ycol_of<T>(dd), face_mode, 0, st,
-                     prof);
+  return dispatch<T>(hp, dd, x, y, 0, 1, face_out_of<T>(dd), ycol_of<T>(dd), face_mode,
+                     dd.variant[std::is_same<T, float>::value ? 1 : 0], st, prof);
 }
 template cudaError_t launch_cg_apply<double>(const HostProblem&, const DeviceData&,
                                              const double*, double*, cudaStream_t, Profiler*,

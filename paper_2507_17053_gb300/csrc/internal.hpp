@@ -73,6 +73,7 @@ struct DeviceData {
   float* face_out32 = nullptr;
   int* err_flag = nullptr;       // device error word (SBM_ERR_TIMEOUT from bounded waits)
   ChunkTable chunks[2];          // CG: R and R/2 cells per chunk (two tile shapes)
+  int variant[2] = {0, 0};       // tile shape of the single applies: [FP64, FP32]
   int32_t* diag_pos = nullptr;   // CG: ordered positions grouped by cell parity (diagonal)
   std::vector<int> diag_col_start;
   double* ycol = nullptr;        // CG [ncolours * n_dofs] colour accumulation buffers (scratch)

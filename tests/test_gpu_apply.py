@@ -104,3 +104,18 @@ def test_full_size_sampled_rows(w):
     ref = O.apply_rows(x, rows)
     scale = np.abs(ref).max()
     assert np.abs(y[rows] - ref).max() <= TOL * scale
+
+
+@pytest.mark.parametrize("w", [S.SPHERE_3D_Q4.resized(12), S.ELLIPSOID_3D_Q6.resized(9),
+                               S.DISK_2D_Q2], ids=lambda w: w.name)
+def test_autotuned_tile_shapes_keep_parity(w):
+    """Both cell-kernel tile shapes (chunks of R and R/2 cells) match the oracle."""
+    O, P = _pair(w)
+    x = S.random_vector(w.seed, O.n_dofs, w.dist)
+    xd = torch.from_numpy(x).cuda()
+    ref = O.apply(x)
+    shapes = G.sbm_autotune(P.handle)
+    assert all(s in (0, 1) for s in shapes)
+    assert _rel(P.apply_f64(xd).cpu().numpy(), ref) <= TOL
+    y32 = P.apply_f32(xd.float()).double().cpu().numpy()
+    assert _rel(y32, O.apply(x.astype(np.float32).astype(np.float64))) <= 1e-5 * w.degree
