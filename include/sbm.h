@@ -271,18 +271,47 @@ int sbm_gmres(sbm_problem* prob, const double* b, double* x, double rtol, int ma
               int* iters, double* relres, void* stream);
 
 /*
+ * BiCGStab (van der Vorst's stabilised bi-conjugate gradients) on A x = b,
+ * for the nonsymmetric SBM operator (no preconditioner: the SBM diagonal has
+ * negative entries near the surrogate boundary, and Jacobi scaling turns the
+ * spectrum indefinite): two operator applications per
+ * iteration, every scalar in FP64 on the device, BI_CHUNK = 8 iterations per
+ * CUDA-graph launch, deterministic reductions.  sbm_bicgstab works on FP64
+ * vectors with the FP64 apply; sbm_bicgstab_f32 on FP32 vectors with the
+ * FP32 apply (face arithmetic face_mode, as in sbm_apply_f32) and FP64
+ * scalars.  Same conventions as sbm_cg (x = initial guess in, iterate out;
+ * true-residual stop test; device vectors of n_dofs).  A recursive residual
+ * that the true one does not confirm restarts from the current iterate; a
+ * breakdown, divergence or the iteration cap continues (or ends) from the
+ * iterate of least recursive residual seen at a chunk end (at most 50
+ * restarts).  *iters counts iterations, maxit
+ * bounds them.  Device workspace: 7 vectors of n_dofs, allocated and freed
+ * by the call.
+ * Errors: SBM_ERR_ARG, SBM_ERR_STATE, SBM_ERR_UNSUPPORTED (tensor-core face
+ * mode on a 2D problem), SBM_ERR_NOT_CONVERGED, SBM_ERR_CUDA.
+ */
+int sbm_bicgstab(sbm_problem* prob, const double* b, double* x, double rtol, int maxit,
+                 int* iters, double* relres, void* stream);
+int sbm_bicgstab_f32(sbm_problem* prob, const float* b, float* x, double rtol, int maxit,
+                     int face_mode, int* iters, double* relres, void* stream);
+
+/* Inner solver of the mixed-precision refinement. */
+enum { SBM_INNER_GMRES = 0, SBM_INNER_BICGSTAB = 1 };
+
+/*
  * Mixed precision: FP64 iterative refinement (defect correction).  Each
  * outer step computes r = b - A x with the FP64 apply, then solves
- * A c = r/|r| approximately with FP32 GMRES(restart) on the FP32 apply
- * (face arithmetic face_mode, as in sbm_apply_f32)
- * (relative tolerance inner_rtol, at most inner_maxit iterations), and
- * updates x += |r| c in FP64.  Stops when |b - A x|/|b| <= rtol (FP64) or
- * after max_outer steps.  *iters = FP32 inner iterations in total,
- * *outer = outer steps; same conventions otherwise.
+ * A c = r/|r| approximately in FP32 on the FP32 apply (face arithmetic
+ * face_mode, as in sbm_apply_f32) with the inner solver inner_solver:
+ * GMRES(restart), or BiCGStab (restart unused) (relative tolerance
+ * inner_rtol, at most inner_maxit iterations), and updates x += |r| c in
+ * FP64.  Stops when |b - A x|/|b| <= rtol (FP64) or after max_outer steps.
+ * *iters = FP32 inner iterations in total (a BiCGStab iteration applies the
+ * operator twice), *outer = outer steps; same conventions otherwise.
  */
 int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int max_outer,
-                 int restart, double inner_rtol, int inner_maxit, int face_mode, int* iters,
-                 int* outer, double* relres, void* stream);
+                 int restart, double inner_rtol, int inner_maxit, int face_mode,
+                 int inner_solver, int* iters, int* outer, double* relres, void* stream);
 
 /*
  * Manufactured data (host, FP64; no CUDA call).  manufactured = 0:

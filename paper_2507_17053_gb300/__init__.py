@@ -69,9 +69,19 @@ _SIGS = {
                                                            ctypes.POINTER(ctypes.c_int),
                                                            ctypes.POINTER(ctypes.c_double),
                                                            ctypes.c_void_p]),
+    "sbm_bicgstab": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int,
+                                                              ctypes.POINTER(ctypes.c_int),
+                                                              ctypes.POINTER(ctypes.c_double),
+                                                              ctypes.c_void_p]),
+    "sbm_bicgstab_f32": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int,
+                                                                  ctypes.c_int,
+                                                                  ctypes.POINTER(ctypes.c_int),
+                                                                  ctypes.POINTER(ctypes.c_double),
+                                                                  ctypes.c_void_p]),
     "sbm_solve_ir": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int,
                                                               ctypes.c_int, ctypes.c_double,
                                                               ctypes.c_int, ctypes.c_int,
+                                                              ctypes.c_int,
                                                               ctypes.POINTER(ctypes.c_int),
                                                               ctypes.POINTER(ctypes.c_int),
                                                               ctypes.POINTER(ctypes.c_double),
@@ -208,6 +218,7 @@ def sbm_diagonal(handle: int, diag, stream=None) -> None:
 
 FACE_MODE = {"fp32": 0, "tf32": 1, "bf16": 2}
 PRECOND = {"none": 0, "jacobi": 1}
+INNER = {"gmres": 0, "bicgstab": 1}
 
 
 def sbm_apply_f32(handle: int, x, y, face_mode=0, stream=None) -> None:
@@ -238,12 +249,29 @@ def sbm_gmres(handle: int, b, x, rtol=1e-10, maxit=10000, restart=100, stream=No
     return _solve_call("sbm_gmres", st, it, rr, raise_not_converged)
 
 
+def sbm_bicgstab(handle: int, b, x, rtol=1e-10, maxit=10000, stream=None,
+                 raise_not_converged=False):
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    st = lib().sbm_bicgstab(handle, _ptr(b), _ptr(x), rtol, maxit, ctypes.byref(it),
+                            ctypes.byref(rr), _stream(stream))
+    return _solve_call("sbm_bicgstab", st, it, rr, raise_not_converged)
+
+
+def sbm_bicgstab_f32(handle: int, b, x, rtol=1e-5, maxit=10000, face_mode=0, stream=None,
+                     raise_not_converged=False):
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    st = lib().sbm_bicgstab_f32(handle, _ptr(b), _ptr(x), rtol, maxit, int(face_mode),
+                                ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    return _solve_call("sbm_bicgstab_f32", st, it, rr, raise_not_converged)
+
+
 def sbm_solve_ir(handle: int, b, x, rtol=1e-10, max_outer=30, restart=100, inner_rtol=1e-4,
-                 inner_maxit=2000, face_mode=0, stream=None, raise_not_converged=False):
+                 inner_maxit=2000, face_mode=0, inner_solver=0, stream=None,
+                 raise_not_converged=False):
     it, outer, rr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     st = lib().sbm_solve_ir(handle, _ptr(b), _ptr(x), rtol, max_outer, restart, inner_rtol,
-                            inner_maxit, int(face_mode), ctypes.byref(it), ctypes.byref(outer),
-                            ctypes.byref(rr), _stream(stream))
+                            inner_maxit, int(face_mode), int(inner_solver), ctypes.byref(it),
+                            ctypes.byref(outer), ctypes.byref(rr), _stream(stream))
     res = _solve_call("sbm_solve_ir", st, it, rr, raise_not_converged)
     return res + (outer.value,)
 

@@ -418,14 +418,20 @@ int sbm_diagonal(sbm_problem* prob, double* diag, void* stream) {
   return SBM_OK;
 }
 
-int sbm_apply_f32(sbm_problem* prob, const float* x, float* y, int face_mode, void* stream) {
-  if (!prob || !x || !y) return fail(SBM_ERR_ARG, "NULL argument");
-  if (x == y) return fail(SBM_ERR_ARG, "x and y must not overlap");
-  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+static int check_face_mode(const sbm_problem* prob, int face_mode) {
   if (face_mode != SBM_FACE_FP32 && face_mode != SBM_FACE_TF32 && face_mode != SBM_FACE_BF16)
     return fail(SBM_ERR_ARG, "unknown face mode");
   if (face_mode != SBM_FACE_FP32 && prob->hp.d != 3)
     return fail(SBM_ERR_UNSUPPORTED, "tensor-core face modes are built for 3D problems");
+  return SBM_OK;
+}
+
+int sbm_apply_f32(sbm_problem* prob, const float* x, float* y, int face_mode, void* stream) {
+  if (!prob || !x || !y) return fail(SBM_ERR_ARG, "NULL argument");
+  if (x == y) return fail(SBM_ERR_ARG, "x and y must not overlap");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  const int fm = check_face_mode(prob, face_mode);
+  if (fm != SBM_OK) return fm;
   cudaError_t e = prob->hp.desc.dg
       ? launch_dg_apply<float>(prob->hp, prob->dd, x, y, (cudaStream_t)stream, &prob->prof,
                                face_mode)
@@ -502,23 +508,58 @@ int sbm_gmres(sbm_problem* prob, const double* b, double* x, double rtol, int ma
   return solve_result(s, info, iters, relres, "sbm_gmres");
 }
 
+extern "C++" template <typename T>
+int run_bicgstab(sbm_problem* prob, const ApplyFn<T>& ap, const T* b, T* x, double rtol,
+                        int maxit, int* iters, double* relres, cudaStream_t st,
+                        const char* what) {
+  Workspace ws;
+  SolveInfo info;
+  Bicgstab<T> bi;
+  SolveStatus s{SBM_OK, cudaSuccess};
+  cudaError_t e = bi.setup(ap, prob->hp.n_dofs, b, x, ws);
+  if (e != cudaSuccess) s = {SBM_ERR_CUDA, e};
+  else s = bi.solve(false, rtol, maxit, st, &info);
+  cudaStreamSynchronize(st);
+  bi.destroy();
+  ws.release();
+  return solve_result(s, info, iters, relres, what);
+}
+
+int sbm_bicgstab(sbm_problem* prob, const double* b, double* x, double rtol, int maxit,
+                 int* iters, double* relres, void* stream) {
+  if (!prob || !b || !x || b == x) return fail(SBM_ERR_ARG, "bad vector argument");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (!(rtol > 0) || maxit < 1) return fail(SBM_ERR_ARG, "bad solver parameter");
+  return run_bicgstab<double>(prob, apply64_fn(prob), b, x, rtol, maxit, iters, relres,
+                              (cudaStream_t)stream, "sbm_bicgstab");
+}
+
+int sbm_bicgstab_f32(sbm_problem* prob, const float* b, float* x, double rtol, int maxit,
+                     int face_mode, int* iters, double* relres, void* stream) {
+  if (!prob || !b || !x || b == x) return fail(SBM_ERR_ARG, "bad vector argument");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (!(rtol > 0) || maxit < 1) return fail(SBM_ERR_ARG, "bad solver parameter");
+  const int fm = check_face_mode(prob, face_mode);
+  if (fm != SBM_OK) return fm;
+  return run_bicgstab<float>(prob, apply32_fn(prob, face_mode), b, x, rtol, maxit, iters, relres, (cudaStream_t)stream, "sbm_bicgstab_f32");
+}
+
 int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int max_outer,
-                 int restart, double inner_rtol, int inner_maxit, int face_mode, int* iters,
-                 int* outer, double* relres, void* stream) {
+                 int restart, double inner_rtol, int inner_maxit, int face_mode,
+                 int inner_solver, int* iters, int* outer, double* relres, void* stream) {
   if (!prob || !b || !x || b == x) return fail(SBM_ERR_ARG, "bad vector argument");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
   if (!(rtol > 0) || max_outer < 0 || restart < 1 || restart > 1000 || !(inner_rtol > 0) ||
-      inner_maxit < 1)
+      inner_maxit < 1 || (inner_solver != SBM_INNER_GMRES && inner_solver != SBM_INNER_BICGSTAB))
     return fail(SBM_ERR_ARG, "bad solver parameter");
-  if (face_mode != SBM_FACE_FP32 && face_mode != SBM_FACE_TF32 && face_mode != SBM_FACE_BF16)
-    return fail(SBM_ERR_ARG, "unknown face mode");
-  if (face_mode != SBM_FACE_FP32 && prob->hp.d != 3)
-    return fail(SBM_ERR_UNSUPPORTED, "tensor-core face modes are built for 3D problems");
+  const int fm = check_face_mode(prob, face_mode);
+  if (fm != SBM_OK) return fm;
   cudaStream_t st = (cudaStream_t)stream;
   Workspace ws;
   SolveInfo info;
   SolveStatus s = solve_ir(apply64_fn(prob), apply32_fn(prob, face_mode), prob->hp.n_dofs, b, x, rtol,
-                           max_outer, restart, inner_rtol, inner_maxit, st, ws, &info);
+                           max_outer, restart, inner_rtol, inner_maxit, inner_solver, st, ws,
+                           &info);
   cudaStreamSynchronize(st);
   ws.release();
   if (outer) *outer = info.restarts;

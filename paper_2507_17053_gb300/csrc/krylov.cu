@@ -1,5 +1,5 @@
 // Krylov drivers on the matrix-free operator: conjugate gradients, restarted
-// GMRES, and FP64 iterative refinement around an FP32 inner solve.
+// GMRES, BiCGStab, and FP64 iterative refinement around an FP32 inner solve.
 //
 // The paper gives no solver; it states that the mat-vec dominates iterative
 // solvers (Section 4.2).  These drivers keep every vector on the device:
@@ -525,12 +525,317 @@ template SolveStatus solve_gmres<float, float>(const ApplyFn<float>&, int64_t, c
                                                float*, double, int, int, cudaStream_t, Workspace&,
                                                SolveInfo*, const ApplyFn<float>*);
 
-// ---- FP64 iterative refinement around an FP32 inner GMRES ------------------
+// ---- BiCGStab ----------------------------------------------------------------
+//
+// van der Vorst's stabilised bi-conjugate gradients, two operator
+// applications and three reductions per iteration.  Vectors are in T
+// (FP64 or FP32); every scalar is FP64 and stays on the device, so a chunk of
+// BI_CHUNK iterations is one CUDA-graph launch with no host round trip.  A
+// breakdown (rho or (r^, v) vanishing, omega = 0) or a recursive residual that
+// disagrees with the true one restarts from the current iterate with a fresh
+// shadow residual r^ = r.
+
+constexpr int BI_CHUNK = 8;
+
+struct BiState {
+  double rho, alpha, omega, beta, rr, bb, tol2;
+  int done;     // 0 running, 1 converged (recursive residual), 2 breakdown/divergence, 3 maxit
+  int iters;
+  int maxit;
+};
+
+// r = b - q (q = A x; q == nullptr for x = 0); r^ = r; p = r; partials r.r, b.b
+template <typename T>
+__global__ void k_bi_init(const T* __restrict__ b, const T* __restrict__ q, T* __restrict__ r,
+                          T* __restrict__ rh, T* __restrict__ p, int64_t n,
+                          double* __restrict__ part) {
+  __shared__ double sh[RED_THREADS];
+  double srr = 0.0, sbb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T ri = q ? (T)(b[i] - q[i]) : b[i];
+    r[i] = ri;
+    rh[i] = ri;
+    p[i] = ri;
+    srr = fma((double)ri, (double)ri, srr);
+    sbb = fma((double)b[i], (double)b[i], sbb);
+  }
+  srr = block_sum(srr, sh);
+  sbb = block_sum(sbb, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = srr;
+    part[RED_BLOCKS + blockIdx.x] = sbb;
+  }
+}
+
+__global__ void k_bi_init_fin(const double* __restrict__ part, BiState* st) {
+  __shared__ double sh[RED_THREADS];
+  double v[2];
+  for (int j = 0; j < 2; ++j) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) s += part[j * RED_BLOCKS + i];
+    v[j] = block_sum(s, sh);
+  }
+  if (threadIdx.x == 0) {
+    st->rr = v[0];
+    st->bb = v[1];
+    st->rho = v[0];              // (r^, r) with r^ = r
+    st->alpha = st->omega = 1.0;
+    st->beta = 0.0;
+    st->done = (v[0] <= st->tol2 * v[1]) ? 1 : 0;
+    if (!isfinite(v[0])) st->done = 2;
+    if (st->maxit <= 0 && !st->done) st->done = 3;
+  }
+}
+
+// alpha = rho / (r^, v)
+__global__ void k_bi_alpha(const double* __restrict__ part, BiState* st) {
+  __shared__ double sh[RED_THREADS];
+  if (st->done) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) s += part[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    if (!(s != 0.0) || !isfinite(s)) st->done = 2;
+    else st->alpha = st->rho / s;
+  }
+}
+
+// s = r - alpha v
+template <typename T>
+__global__ void k_bi_s(const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ s,
+                       int64_t n, const BiState* st) {
+  if (st->done) return;
+  const double al = st->alpha;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s[i] = (T)fma(-al, (double)v[i], (double)r[i]);
+}
+
+// partials of (t, s) and (t, t)
+template <typename T>
+__global__ void k_bi_dot2(const T* __restrict__ t, const T* __restrict__ s, int64_t n,
+                          const BiState* st, double* __restrict__ part) {
+  __shared__ double sh[RED_THREADS];
+  if (st->done) return;
+  double sts = 0.0, stt = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ti = (double)t[i];
+    sts = fma(ti, (double)s[i], sts);
+    stt = fma(ti, ti, stt);
+  }
+  sts = block_sum(sts, sh);
+  stt = block_sum(stt, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sts;
+    part[RED_BLOCKS + blockIdx.x] = stt;
+  }
+}
+
+// omega = (t, s) / (t, t)  (0 when t = 0: the update then keeps r = s)
+__global__ void k_bi_omega(const double* __restrict__ part, BiState* st) {
+  __shared__ double sh[RED_THREADS];
+  if (st->done) return;
+  double v[2];
+  for (int j = 0; j < 2; ++j) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) s += part[j * RED_BLOCKS + i];
+    v[j] = block_sum(s, sh);
+  }
+  if (threadIdx.x == 0) {
+    st->omega = (v[1] > 0.0) ? v[0] / v[1] : 0.0;
+    if (!isfinite(st->omega)) st->done = 2;
+  }
+}
+
+// x += alpha p + omega s; r = s - omega t; partials of (r^, r), (r, r)
+template <typename T>
+__global__ void k_bi_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                            const T* __restrict__ s, const T* __restrict__ t,
+                            const T* __restrict__ rh, int64_t n, const BiState* st,
+                            double* __restrict__ part) {
+  __shared__ double sh[RED_THREADS];
+  if (st->done) return;
+  const double al = st->alpha, om = st->omega;
+  double srh = 0.0, srr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = (double)s[i];
+    x[i] = (T)fma(om, si, fma(al, (double)p[i], (double)x[i]));
+    const T ri = (T)fma(-om, (double)t[i], si);
+    r[i] = ri;
+    srh = fma((double)rh[i], (double)ri, srh);
+    srr = fma((double)ri, (double)ri, srr);
+  }
+  srh = block_sum(srh, sh);
+  srr = block_sum(srr, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = srh;
+    part[RED_BLOCKS + blockIdx.x] = srr;
+  }
+}
+
+// rho' = (r^, r); convergence / breakdown tests; beta = (rho'/rho)(alpha/omega)
+__global__ void k_bi_beta(const double* __restrict__ part, BiState* st) {
+  __shared__ double sh[RED_THREADS];
+  if (st->done) return;
+  double v[2];
+  for (int j = 0; j < 2; ++j) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) s += part[j * RED_BLOCKS + i];
+    v[j] = block_sum(s, sh);
+  }
+  if (threadIdx.x == 0) {
+    st->iters += 1;
+    st->rr = v[1];
+    if (v[1] <= st->tol2 * st->bb) st->done = 1;
+    else if (!isfinite(v[1]) || v[1] > 1e24 * st->bb) st->done = 2;
+    else if (!(v[0] != 0.0) || !(st->omega != 0.0)) st->done = 2;
+    else if (st->iters >= st->maxit) st->done = 3;
+    if (!st->done) {
+      st->beta = (v[0] / st->rho) * (st->alpha / st->omega);
+      st->rho = v[0];
+    }
+  }
+}
+
+// p = r + beta (p - omega v)
+template <typename T>
+__global__ void k_bi_p(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ v,
+                       int64_t n, const BiState* st) {
+  if (st->done) return;
+  const double be = st->beta, om = st->omega;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (T)fma(be, fma(-om, (double)v[i], (double)p[i]), (double)r[i]);
+}
+
+template <typename T>
+cudaError_t Bicgstab<T>::setup(const ApplyFn<T>& apply_, int64_t n_, const T* b_, T* x_,
+                               Workspace& ws) {
+  apply = apply_;
+  n = n_;
+  b = b_;
+  x = x_;
+  cudaError_t e;
+  T** vecs[7] = {&r, &rh, &p, &v, &s, &t, &xb};
+  for (T** pv : vecs)
+    if ((e = ws.alloc((void**)pv, (size_t)n * sizeof(T))) != cudaSuccess) return e;
+  if ((e = ws.alloc((void**)&part, 2 * RED_BLOCKS * 8)) != cudaSuccess) return e;
+  if ((e = ws.alloc(&dstate, sizeof(BiState))) != cudaSuccess) return e;
+  if ((e = cudaMallocHost(&hstate, sizeof(BiState))) != cudaSuccess) return e;
+  if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  BiState* dst = (BiState*)dstate;
+  cudaGraph_t graph;
+  if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+    return e;
+  cudaError_t ae = cudaSuccess;
+  for (int it = 0; it < BI_CHUNK && ae == cudaSuccess; ++it) {
+    ae = apply(p, v, cap);
+    if (ae != cudaSuccess) break;
+    k_multi_dot<T><<<dim3(RED_BLOCKS, 1), RED_THREADS, 0, cap>>>(rh, 0, v, n, part);
+    k_bi_alpha<<<1, RED_THREADS, 0, cap>>>(part, dst);
+    k_bi_s<T><<<vec_grid(n), 256, 0, cap>>>(r, v, s, n, dst);
+    ae = apply(s, t, cap);
+    if (ae != cudaSuccess) break;
+    k_bi_dot2<T><<<RED_BLOCKS, RED_THREADS, 0, cap>>>(t, s, n, dst, part);
+    k_bi_omega<<<1, RED_THREADS, 0, cap>>>(part, dst);
+    k_bi_update<T><<<RED_BLOCKS, RED_THREADS, 0, cap>>>(x, r, p, s, t, rh, n, dst, part);
+    k_bi_beta<<<1, RED_THREADS, 0, cap>>>(part, dst);
+    k_bi_p<T><<<vec_grid(n), 256, 0, cap>>>(p, r, v, n, dst);
+  }
+  e = cudaStreamEndCapture(cap, &graph);
+  if (ae != cudaSuccess) {
+    if (e == cudaSuccess) cudaGraphDestroy(graph);
+    return ae;
+  }
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
+}
+
+template <typename T>
+void Bicgstab<T>::destroy() {
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  if (hstate) cudaFreeHost(hstate);
+  hstate = nullptr;
+  if (cap) cudaStreamDestroy(cap);
+  cap = nullptr;
+}
+
+template <typename T>
+SolveStatus Bicgstab<T>::solve(bool x_zero, double rtol, int maxit, cudaStream_t st,
+                               SolveInfo* info) {
+  BiState* dst = (BiState*)dstate;
+  BiState* hs = (BiState*)hstate;
+  int total = 0, restarts = 0, status = SBM_NOT_DONE;
+  double relres = INFINITY, best = INFINITY;
+  bool zero = x_zero;
+  while (true) {
+    BiState init{};
+    init.tol2 = rtol * rtol;
+    init.maxit = maxit - total;
+    CK(cudaMemcpyAsync(dst, &init, sizeof(BiState), cudaMemcpyHostToDevice, st));
+    if (!zero) CK(apply(x, v, st));
+    k_bi_init<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, zero ? nullptr : v, r, rh, p, n, part);
+    k_bi_init_fin<<<1, RED_THREADS, 0, st>>>(part, dst);
+    CK(cudaGetLastError());
+    zero = false;
+    int done = 0;
+    while (true) {
+      CK(cudaMemcpyAsync(hs, dst, sizeof(BiState), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      done = hs->done;
+      // keep the iterate of least (recursive) residual seen at a chunk end
+      if (std::isfinite(hs->rr) && hs->rr < best) {
+        best = hs->rr;
+        CK(cudaMemcpyAsync(xb, x, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      }
+      if (done) break;
+      CK(cudaGraphLaunch(exec, st));
+    }
+    total += hs->iters;
+    // after a breakdown, divergence or the iteration cap, continue from the
+    // best iterate rather than the last one
+    if (done != 1 && !(hs->rr <= best))
+      CK(cudaMemcpyAsync(x, xb, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    if (hs->bb == 0.0) {
+      relres = 0.0;
+      status = SBM_OK;
+      break;
+    }
+    // true residual of the current iterate
+    CK(apply(x, v, st));
+    k_residual<T><<<vec_grid(n), 256, 0, st>>>(b, v, n);
+    CK(multi_dot<T>(v, 0, v, n, 1, part, part + RED_BLOCKS, st));
+    double rr;
+    CK(cudaMemcpyAsync(&rr, part + RED_BLOCKS, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    relres = std::sqrt(rr / hs->bb);
+    if (relres <= rtol) { status = SBM_OK; break; }
+    if (done == 3 || total >= maxit || ++restarts > 50 || !std::isfinite(relres)) {
+      status = SBM_ERR_NOT_CONVERGED;
+      break;
+    }
+  }
+  info->iters = total;
+  info->relres = relres;
+  info->restarts = restarts;
+  return {status, cudaSuccess};
+}
+
+template struct Bicgstab<double>;
+template struct Bicgstab<float>;
+
+// ---- FP64 iterative refinement around an FP32 inner solve --------------------
 
 SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply32, int64_t n,
                      const double* b, double* x, double rtol, int maxit, int restart,
-                     double inner_rtol, int inner_maxit, cudaStream_t st, Workspace& ws,
-                     SolveInfo* info) {
+                     double inner_rtol, int inner_maxit, int inner, cudaStream_t st,
+                     Workspace& ws, SolveInfo* info) {
   double *r, *part, *dsc;
   float *r32, *c32;
   CK(ws.alloc((void**)&r, n * 8));
@@ -547,6 +852,14 @@ SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply
   double relres = INFINITY;
   int status = SBM_ERR_NOT_CONVERGED;
   Workspace inner_ws;
+  Bicgstab<float> bi;
+  if (inner == SBM_INNER_BICGSTAB) {
+    cudaError_t e = bi.setup(apply32, n, r32, c32, ws);
+    if (e != cudaSuccess) {
+      bi.destroy();
+      return {SBM_ERR_CUDA, e};
+    }
+  }
   while (outer <= maxit) {
     CK(apply64(x, r, st));
     k_residual<double><<<vec_grid(n), 256, 0, st>>>(b, r, n);
@@ -562,19 +875,28 @@ SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply
     k_convert_scaled<float, double><<<vec_grid(n), 256, 0, st>>>(r32, r, 1.0 / rn, n);
     CK(cudaMemsetAsync(c32, 0, n * 4, st));
     SolveInfo ii{};
-    SolveStatus s = solve_gmres<float, float>(apply32, n, r32, c32, inner_rtol, inner_maxit,
-                                              restart, st, inner_ws, &ii, &apply32);
-    inner_ws.release();
+    SolveStatus s;
+    if (inner == SBM_INNER_BICGSTAB) {
+      s = bi.solve(true, inner_rtol, inner_maxit, st, &ii);
+    } else {
+      s = solve_gmres<float, float>(apply32, n, r32, c32, inner_rtol, inner_maxit, restart, st,
+                                    inner_ws, &ii, &apply32);
+      inner_ws.release();
+    }
     if (s.status == SBM_ERR_CUDA) {
+      bi.destroy();
       info->iters = inner_total;
       return s;
     }
     inner_total += ii.iters;
+    // an inner solve that made no progress would only spoil x
+    if (s.status != SBM_OK && !(ii.relres < 1.0)) break;
     // x += |r| c
     k_add_scaled<<<vec_grid(n), 256, 0, st>>>(x, c32, rn, n);
     CK(cudaGetLastError());
     ++outer;
   }
+  bi.destroy();
   info->iters = inner_total;
   info->relres = relres;
   info->restarts = outer;

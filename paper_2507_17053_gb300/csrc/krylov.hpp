@@ -48,11 +48,36 @@ SolveStatus solve_gmres(const ApplyFn<T>& apply, int64_t n, const TX* b, TX* x, 
                         int maxit, int restart, cudaStream_t st, Workspace& ws, SolveInfo* info,
                         const ApplyFn<TX>* apply_x);
 
-// FP64 iterative refinement: r = b - A64 x in FP64, inner FP32 GMRES on
-// A32 c = r/|r| to inner_rtol, x += |r| c; maxit outer steps.
+// BiCGStab in precision T (FP64 scalars), bound to one right-hand side b and
+// iterate x; setup allocates from ws and captures BI_CHUNK iterations as one
+// CUDA graph, solve may run several times (e.g. as an inner solver), and
+// destroy frees the graph, the capture stream and the pinned state.
+template <typename T>
+struct Bicgstab {
+  ApplyFn<T> apply;
+  int64_t n = 0;
+  const T* b = nullptr;
+  T* x = nullptr;
+  T *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
+  T* xb = nullptr;   // iterate of least recursive residual so far
+  double* part = nullptr;
+  void* dstate = nullptr;
+  void* hstate = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t setup(const ApplyFn<T>& apply, int64_t n, const T* b, T* x, Workspace& ws);
+  // x_zero: x holds zeros on entry (skips the first residual's apply).
+  // info->iters counts iterations (two operator applications each).
+  SolveStatus solve(bool x_zero, double rtol, int maxit, cudaStream_t st, SolveInfo* info);
+  void destroy();
+};
+
+// FP64 iterative refinement: r = b - A64 x in FP64, inner FP32 solve
+// (GMRES(restart) or BiCGStab, SBM_INNER_*) of A32 c = r/|r| to inner_rtol,
+// x += |r| c; maxit outer steps.
 SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply32, int64_t n,
                      const double* b, double* x, double rtol, int maxit, int restart,
-                     double inner_rtol, int inner_maxit, cudaStream_t st, Workspace& ws,
-                     SolveInfo* info);
+                     double inner_rtol, int inner_maxit, int inner, cudaStream_t st,
+                     Workspace& ws, SolveInfo* info);
 
 }  // namespace sbm

@@ -78,3 +78,83 @@ def test_mixed_precision_ir(w):
                                        inner_rtol=1e-4, inner_maxit=3000)
     assert ok and rr <= 1e-10, (it, rr, outer)
     assert np.linalg.norm(x.cpu().numpy() - xref) <= 1e-7 * np.linalg.norm(xref)
+
+
+@pytest.mark.parametrize("w", [S.DISK_2D_Q2, S.SPHERE_3D_Q4.resized(8, degree=2),
+                               S.ELLIPSOID_3D_Q6.resized(6, degree=3)],
+                         ids=lambda w: w.name)
+def test_bicgstab_fp64(w):
+    """BiCGStab on the nonsymmetric SBM system reaches 1e-10 (true residual)
+    and the direct solution; a second solve is bitwise identical."""
+    O, P, b, xref = _system(w)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    it, rr, ok = G.sbm_bicgstab(P.handle, bd, x, rtol=1e-10, maxit=20000)
+    assert ok and rr <= 1e-10, (it, rr)
+    assert np.linalg.norm(x.cpu().numpy() - xref) <= 1e-7 * np.linalg.norm(xref)
+    x2 = torch.zeros_like(bd)
+    it2, _, _ = G.sbm_bicgstab(P.handle, bd, x2, rtol=1e-10, maxit=20000)
+    assert it2 == it and torch.equal(x, x2)
+
+
+def test_bicgstab_initial_guess_and_zero_rhs():
+    O, P, b, xref = _system(S.DISK_2D_Q2.resized(12))
+    bd = torch.from_numpy(b).cuda()
+    # the exact solution as initial guess: converged before the first iteration
+    x = torch.from_numpy(xref).cuda()
+    it, rr, ok = G.sbm_bicgstab(P.handle, bd, x, rtol=1e-8, maxit=100)
+    assert ok and it == 0 and rr <= 1e-8
+    # b = 0 from x = 0: nothing to do, x stays 0
+    z = torch.zeros_like(bd)
+    x = torch.zeros_like(bd)
+    it, rr, ok = G.sbm_bicgstab(P.handle, z, x, rtol=1e-10, maxit=100)
+    assert ok and it == 0 and rr == 0.0 and not x.any()
+    # an iteration cap too small reports NOT_CONVERGED with the true residual
+    x = torch.zeros_like(bd)
+    it, rr, ok = G.sbm_bicgstab(P.handle, bd, x, rtol=1e-12, maxit=3)
+    assert not ok and it == 3 and rr > 1e-12
+    with pytest.raises(G.SbmError):
+        G.sbm_bicgstab(P.handle, bd, torch.zeros_like(bd), rtol=1e-12, maxit=3,
+                       raise_not_converged=True)
+
+
+@pytest.mark.parametrize("mode,rtol", [("fp32", 1e-5), ("tf32", 1e-3)])
+def test_bicgstab_fp32(mode, rtol):
+    """FP32 vectors and apply, FP64 scalars: reaches rtol (true residual of
+    the same FP32 apply; with TF32 faces the apply's own rounding, about
+    1e-4 of |A x|, bounds what any residual can reach), and the FP64
+    operator's residual of the FP32 solution is within 10 rtol."""
+    w = S.SPHERE_3D_Q4.resized(8, degree=2)
+    O, P, b, xref = _system(w)
+    bd = torch.from_numpy(b).cuda().float()
+    x = torch.zeros_like(bd)
+    it, rr, ok = G.sbm_bicgstab_f32(P.handle, bd, x, rtol=rtol, maxit=20000,
+                                    face_mode=G.FACE_MODE[mode])
+    assert ok and rr <= rtol, (it, rr)
+    bd64 = torch.from_numpy(b).cuda()
+    r64 = bd64 - P.apply_f64(x.double())
+    assert float(r64.norm() / bd64.norm()) <= 10 * rtol
+
+
+def test_bicgstab_fp32_rejects_tensor_faces_in_2d():
+    P = G.Problem.from_workload(S.DISK_2D_Q2.resized(8))
+    b = torch.ones(P.n_dofs, device="cuda")
+    with pytest.raises(G.SbmError) as e:
+        G.sbm_bicgstab_f32(P.handle, b, torch.zeros_like(b), face_mode=G.FACE_MODE["tf32"])
+    assert G.STATUS[e.value.status] == "SBM_ERR_UNSUPPORTED"
+
+
+@pytest.mark.parametrize("mode", ["fp32", "tf32", "bf16"])
+def test_mixed_precision_ir_bicgstab_inner(mode):
+    """FP64 refinement around an FP32 BiCGStab inner solve reaches the FP64
+    tolerance, also when the faces run on the tensor cores."""
+    w = S.SPHERE_3D_Q4.resized(8, degree=2)
+    O, P, b, xref = _system(w)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    it, rr, ok, outer = G.sbm_solve_ir(P.handle, bd, x, rtol=1e-10, max_outer=60,
+                                       inner_rtol=1e-3, inner_maxit=5000,
+                                       face_mode=G.FACE_MODE[mode],
+                                       inner_solver=G.INNER["bicgstab"])
+    assert ok and rr <= 1e-10, (it, rr, outer)
+    assert np.linalg.norm(x.cpu().numpy() - xref) <= 1e-7 * np.linalg.norm(xref)
