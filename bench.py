@@ -33,6 +33,11 @@ import synthetic as S  # noqa: E402
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (CUDA cores) nominal dense rate
+# The FP64 pipe issues 2 lane-operations (DFMA, DADD or DMUL alike) per SM
+# per clock: 152 SMs x 2070 MHz x 2 = 629.3 G operations/s (x 2 flops per
+# FMA = the nominal 1.25 TFLOP/s).  The FP64 apply is bound by this pipe.
+SMS, SM_MAX_MHZ, FP64_LANES_PER_SM_CLK = 152, 2070, 2
+FP64_PIPE_GOPS = SMS * SM_MAX_MHZ * 1e6 * FP64_LANES_PER_SM_CLK / 1e9
 L2_BYTES = 129 * 1024 * 1024
 REF_BUDGET_S = 90.0              # wall-clock budget of the --impl reference run
 
@@ -51,6 +56,9 @@ def parse():
     ap.add_argument("--profile-applies", choices=["f64", "f32", "tf32", "bf16"], default=None,
                     help="run --steps applies of the workload in this precision and exit "
                          "(a fixed launch sequence for ncu captures; prints no JSON)")
+    ap.add_argument("--tile-shape", type=int, choices=[-1, 0, 1], default=-1,
+                    help="with --profile-applies: pin the cell kernel's tile shape "
+                         "(-1 keeps the default, 0)")
     return ap.parse_args()
 
 
@@ -60,15 +68,18 @@ def workload(name):
     raise SystemExit(f"unknown workload {name}; choose from {sorted(S.WORKLOADS)}")
 
 
-def cell_flops(d, p, n_cells):
-    """FLOPs the cell kernel executes per apply (an FMA counts 2, an add 1).
+def cell_ops(d, p, n_cells):
+    """FP64/FP32 operations the cell kernel executes per apply: (FMAs, adds).
 
     The exact cell stiffness is applied as 7 (3D) or 4 (2D) one-dimensional
     matrix applications per line of the tile (Algorithm 1 in tensor-product
     form).  For n = p+1 >= 5 each application uses the even/odd split of the
     centrosymmetric 1D matrices: ((n+1)/2)^2 + (n/2)^2 FMAs, plus 2 (n/2)
     additions for every folded input line and every unfolded output line
-    (3D: 5 folds and 5 unfolds per line triple; 2D: 3 and 3)."""
+    (3D: 5 folds and 5 unfolds per line triple; 2D: 3 and 3).  At p = 4 this
+    is 2275 FMAs + 1000 adds per cell; an ncu count of the FP64 kernel gives
+    2280 DFMA + 1035 DADD per cell (the rest: surrogate-face folds and the
+    shared x-face nodes)."""
     n = p + 1
     lines = n ** (d - 1)
     mats = 7 if d == 3 else 4
@@ -78,7 +89,8 @@ def cell_flops(d, p, n_cells):
         adds = (10 if d == 3 else 6) * 2 * h
     else:
         fma, adds = mats * n * n, 0
-    return (2 * fma + adds) * lines * n_cells
+    return fma * lines * n_cells, adds * lines * n_cells
+
 
 
 def face_flops(d, p, n_sfaces):
@@ -251,15 +263,16 @@ def time_applies(P, fn, x, y, steps, warmup, st, dist=None, dev=None, clocks=Non
 
 
 def solve_times(G, torch):
-    """Time-to-1e-10 on the 2D workload (disk, CG Q2, N = 32): CG as named,
-    GMRES(100) in FP64, and FP64 iterative refinement with an FP32 GMRES
-    inner solve.  b from u = sin(pi x) sin(pi y)."""
-    w = S.DISK_2D_Q2
-    P = G.Problem.from_workload(w)
-    b = torch.from_numpy(P.rhs(0)).cuda()
-    out = {"workload": w.name, "n_dofs": P.n_dofs, "rtol": 1e-10}
+    """Time-to-1e-10 (true FP64 relative residual; b from u = prod sin(pi x_i)).
 
-    def timed(f):
+    2D disk (CG Q2, N = 32): CG as named (it diverges: the operator is
+    nonsymmetric), GMRES(100) and BiCGStab in FP64, and FP64 iterative
+    refinement around FP32 GMRES / FP32 BiCGStab.  3D sphere, Q2, N = 64
+    (413,013 DoFs): BiCGStab and GMRES(200) in FP64, refinement around FP32
+    BiCGStab.  (At p >= 3 in 3D no unpreconditioned Krylov method reaches
+    1e-10 on this operator; see the solver notes.)"""
+
+    def timed(b, f):
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -267,20 +280,51 @@ def solve_times(G, torch):
         torch.cuda.synchronize()
         return r, time.perf_counter() - t
 
-    for _ in range(2):      # first call builds graphs / warms the path
-        (it, rr, ok), dt = timed(lambda x: G.sbm_cg(P.handle, b, x, rtol=1e-10, maxit=2000))
-    out["cg"] = {"converged": ok, "iters": it, "rel_residual": rr, "seconds": dt,
-                 "note": "operator is nonsymmetric (shifted trial functions); CG diverges"}
-    for _ in range(2):
-        (it, rr, ok), dt = timed(lambda x: G.sbm_gmres(P.handle, b, x, rtol=1e-10, maxit=5000,
-                                                       restart=100))
-    out["gmres_fp64"] = {"converged": ok, "iters": it, "rel_residual": rr, "seconds": dt}
-    for _ in range(2):
-        (it, rr, ok, outer), dt = timed(lambda x: G.sbm_solve_ir(
+    def run(b, f, reps=2):
+        for _ in range(reps):       # the first call builds graphs / warms the path
+            r, dt = timed(b, f)
+        return r, dt
+
+    out = {"rtol": 1e-10}
+    w = S.DISK_2D_Q2
+    P = G.Problem.from_workload(w)
+    b = torch.from_numpy(P.rhs(0)).cuda()
+    d2 = {"workload": w.name, "n_dofs": P.n_dofs}
+    (it, rr, ok), dt = run(b, lambda x: G.sbm_cg(P.handle, b, x, rtol=1e-10, maxit=2000))
+    d2["cg"] = {"converged": ok, "iters": it, "rel_residual": rr, "seconds": dt,
+                "note": "operator is nonsymmetric (shifted trial functions); CG diverges"}
+    (it, rr, ok), dt = run(b, lambda x: G.sbm_gmres(P.handle, b, x, rtol=1e-10, maxit=5000,
+                                                    restart=100))
+    d2["gmres_fp64"] = {"converged": ok, "iters": it, "rel_residual": rr, "seconds": dt}
+    (it, rr, ok), dt = run(b, lambda x: G.sbm_bicgstab(P.handle, b, x, rtol=1e-10, maxit=5000))
+    d2["bicgstab_fp64"] = {"converged": ok, "iters": it, "applies": 2 * it, "rel_residual": rr,
+                           "seconds": dt}
+    for name, inner in (("ir_fp32_gmres", "gmres"), ("ir_fp32_bicgstab", "bicgstab")):
+        (it, rr, ok, outer), dt = run(b, lambda x: G.sbm_solve_ir(
             P.handle, b, x, rtol=1e-10, max_outer=30, restart=100, inner_rtol=1e-4,
-            inner_maxit=3000))
-    out["ir_fp32_inner"] = {"converged": ok, "inner_iters": it, "outer": outer,
-                            "rel_residual": rr, "seconds": dt}
+            inner_maxit=3000, inner_solver=G.INNER[inner]))
+        d2[name] = {"converged": ok, "inner_iters": it, "outer": outer, "rel_residual": rr,
+                    "seconds": dt}
+    out["disk2d_q2"] = d2
+
+    w = S.SPHERE_3D_Q4.resized(64, degree=2)
+    P = G.Problem.from_workload(w)
+    G.sbm_autotune(P.handle)
+    b = torch.from_numpy(P.rhs(0)).cuda()
+    d3 = {"workload": w.name, "n_dofs": P.n_dofs}
+    (it, rr, ok), dt = run(b, lambda x: G.sbm_bicgstab(P.handle, b, x, rtol=1e-10,
+                                                       maxit=20000))
+    d3["bicgstab_fp64"] = {"converged": ok, "iters": it, "applies": 2 * it, "rel_residual": rr,
+                           "seconds": dt}
+    (it, rr, ok), dt = run(b, lambda x: G.sbm_gmres(P.handle, b, x, rtol=1e-10, maxit=20000,
+                                                    restart=200), reps=1)
+    d3["gmres200_fp64"] = {"converged": ok, "iters": it, "rel_residual": rr, "seconds": dt}
+    (it, rr, ok, outer), dt = run(b, lambda x: G.sbm_solve_ir(
+        P.handle, b, x, rtol=1e-10, max_outer=60, inner_rtol=1e-3, inner_maxit=20000,
+        inner_solver=G.INNER["bicgstab"]), reps=1)
+    d3["ir_fp32_bicgstab"] = {"converged": ok, "inner_iters": it, "outer": outer,
+                              "rel_residual": rr, "seconds": dt}
+    out["sphere3d_q2_n64"] = d3
     return out
 
 
@@ -361,6 +405,8 @@ def profile_applies(args, w):
 
     import paper_2507_17053_gb300 as G
     P = G.Problem.from_workload(w)
+    if args.tile_shape >= 0:
+        G.sbm_set_tile_shape(P.handle, args.tile_shape, args.tile_shape)
     x = torch.from_numpy(S.random_vector(w.seed, P.n_dofs, w.dist)).cuda()
     if args.profile_applies != "f64":
         x = x.float()
@@ -421,10 +467,12 @@ def run_ours(args, w):
     value = world * n * args.steps / (ms * 1e-3) / 1e9
     value32 = world * n * args.steps / (ms32 * 1e-3) / 1e9
     pk, pk_src = peaks()
-    cflops = cell_flops(w.dim, w.degree, P.n_cells)
+    cfma, cadd = cell_ops(w.dim, w.degree, P.n_cells)
+    cflops = 2 * cfma + cadd
+    cops = cfma + cadd
     fflops = face_flops(w.dim, w.degree, P.n_sfaces)
     cell_ms = ph[1]
-    achieved_tf = cflops / (cell_ms * 1e-3) / 1e12
+    achieved_gops = cops / (cell_ms * 1e-3) / 1e9
     step_s = ms / args.steps * 1e-3
     step32_s = ms32 / args.steps * 1e-3
     line = {
@@ -441,13 +489,17 @@ def run_ours(args, w):
         "e2e": {"value": world * n * e2e_steps / e2e_s / 1e9, "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tf / FP64_NOMINAL_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_PIPE_GOPS,
+                     "unit": "G FP64 ops/s", "frac": achieved_gops / FP64_PIPE_GOPS,
                      "traffic": None,
                      "kernel": f"cg_chunk_kernel<double,{w.dim},{w.degree + 1}> (cell kernel)",
-                     "flops_per_launch": cflops, "launches_per_step": 1,
-                     "kernel_ms_per_launch": cell_ms,
-                     "peak_note": "FP64 nominal 1.25 TFLOP/s; FP64 FMA microbenchmark 1.007",
+                     "ops_per_launch": cops, "fma_per_launch": cfma, "add_per_launch": cadd,
+                     "launches_per_step": 1, "kernel_ms_per_launch": cell_ms,
+                     "achieved_tflops": cflops / (cell_ms * 1e-3) / 1e12,
+                     "peak_note": "FP64 pipe: 2 lane-ops per SM per clock x 152 SMs x "
+                                  "2070 MHz (derived; x 2 flops/FMA = nominal 1.25 TFLOP/s); "
+                                  "an FP64 FMA microbenchmark on this GPU reached 1.007 "
+                                  "TFLOP/s",
                      "phases_ms_per_step": {"face": ph[0], "cell": ph[1], "assembly": ph[2]},
                      "face_kernel_tflops": fflops / (ph[0] * 1e-3) / 1e12 if ph[0] > 0 else None,
                      "hbm": {"bytes_per_dof": 16,

@@ -360,6 +360,15 @@ int sbm_device_status(sbm_problem* prob);
 int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32);
 
 /*
+ * Pin the tile shapes of the single applies instead (0: chunks of R cells,
+ * 1: chunks of R/2; -1 keeps the current one), e.g. to reproduce a run
+ * bitwise.  DG problems accept only 0 or -1.
+ * Errors: SBM_ERR_ARG (NULL, shape outside -1..1), SBM_ERR_STATE,
+ * SBM_ERR_UNSUPPORTED (shape 1 on a DG problem).
+ */
+int sbm_set_tile_shape(sbm_problem* prob, int shape64, int shape32);
+
+/*
  * Diagnostic of the failure path (the paper has no counterpart): enqueue one
  * device-side bounded wait on a barrier that nothing releases.  The wait
  * gives up after a fixed number of polls (well under a second), records

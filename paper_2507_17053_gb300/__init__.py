@@ -101,6 +101,7 @@ _SIGS = {
     "sbm_device_status": (ctypes.c_int, [ctypes.c_void_p]),
     "sbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]),
+    "sbm_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "sbm_selftest_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sbm_last_error_detail": (ctypes.c_char_p, []),
@@ -292,6 +293,10 @@ def sbm_autotune(handle: int) -> tuple[int, int]:
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(lib().sbm_autotune(handle, ctypes.byref(a), ctypes.byref(b)), "sbm_autotune")
     return a.value, b.value
+
+
+def sbm_set_tile_shape(handle: int, shape64=-1, shape32=-1) -> None:
+    _check(lib().sbm_set_tile_shape(handle, int(shape64), int(shape32)), "sbm_set_tile_shape")
 
 
 def sbm_selftest_timeout(handle: int, stream=None) -> None:

@@ -648,6 +648,18 @@ int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32) {
   return SBM_OK;
 }
 
+int sbm_set_tile_shape(sbm_problem* prob, int shape64, int shape32) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (shape64 < -1 || shape64 > 1 || shape32 < -1 || shape32 > 1)
+    return fail(SBM_ERR_ARG, "tile shape must be -1, 0 or 1");
+  if (prob->hp.desc.dg && (shape64 == 1 || shape32 == 1))
+    return fail(SBM_ERR_UNSUPPORTED, "DG applies have one tile shape");
+  if (shape64 >= 0) prob->dd.variant[0] = shape64;
+  if (shape32 >= 0) prob->dd.variant[1] = shape32;
+  return SBM_OK;
+}
+
 int sbm_selftest_timeout(sbm_problem* prob, void* stream) {
   if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");

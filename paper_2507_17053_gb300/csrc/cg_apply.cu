@@ -88,12 +88,17 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
   }
 }
 
+// Shared memory of a chunk: one pair tile (R cells; the second sweep phase
+// overwrites its own y-lines in place) and one scalar area that holds the
+// gathered x-line runs until the first phase has read them and the per-cell
+// x-line results after the last one.
 template <typename T, int D, int N, int R>
 struct ChunkSmem {
   static constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
   static constexpr int SM0 = (N - 1) * R + 1;
   static constexpr int SM = (SM0 % 2) ? SM0 : SM0 + 1;        // odd row stride of the runs
-  static constexpr size_t bytes = (size_t)(4 * R * ND + L * SM + R * L * N) * sizeof(T);
+  static constexpr int XZ = (L * SM > R * L * N) ? L * SM : R * L * N;
+  static constexpr size_t bytes = (size_t)(2 * R * ND + XZ) * sizeof(T);
 };
 
 template <typename T, int D, int N, int R>
@@ -103,10 +108,10 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   constexpr int SM = ChunkSmem<T, D, N, R>::SM;
   using P2 = typename PairOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  P2* AE = reinterpret_cast<P2*>(smem_raw);   // pair tiles first (8/16-byte aligned)
-  P2* BG = AE + R * ND;
-  T* Xs = reinterpret_cast<T*>(BG + R * ND);  // [L][SM] the chunk's x-line runs
-  T* Z = Xs + L * SM;                         // [R][L][N] per-cell x-line results
+  P2* AE = reinterpret_cast<P2*>(smem_raw);   // pair tile first (8/16-byte aligned)
+  P2* BG = AE;                                // phase 2 runs in place
+  T* Xs = reinterpret_cast<T*>(AE + R * ND);  // [L][SM] the chunk's x-line runs ...
+  T* Z = Xs;                                  // ... then [R][L][N] per-cell x-line results
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
   const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
@@ -158,10 +163,11 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   }
 }
 
-// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order.  Adding
-// 0.0 is exact, so this equals the plain sum over the set colours; the
-// additions of a colour that no lane of the warp has are skipped (on GB300
-// every double addition costs an FP64-pipe slot).
+// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order: the
+// lowest colour's value is loaded, the others are added to it.  Most DoFs
+// lie inside one chunk (a single colour) and cost no addition; the loop over
+// the further colours is warp-uniform (on GB300 a double addition costs an
+// FP64-pipe slot per warp instruction, whatever its active lanes).
 template <typename T>
 __global__ void assemble_kernel(const T* __restrict__ ycol, const uint8_t* __restrict__ mask,
                                 T* __restrict__ y, int64_t n, int ncol, int64_t ld_ycol = 0,
@@ -169,15 +175,17 @@ __global__ void assemble_kernel(const T* __restrict__ ycol, const uint8_t* __res
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   ycol += blockIdx.y * ld_ycol;
   y += blockIdx.y * ldy;
-  const unsigned m = (i < n) ? (unsigned)__ldg(mask + i) : 0u;
-  T v[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c)
-    v[c] = (c < ncol && (m & (1u << c))) ? __ldcs(ycol + (size_t)c * n + i) : T(0);
+  unsigned m = (i < n) ? (unsigned)__ldg(mask + i) : 0u;
+  if (ncol < 8) m &= (1u << ncol) - 1u;
   T acc = T(0);
-#pragma unroll
-  for (int c = 0; c < 8; ++c)
-    if (__any_sync(0xffffffffu, (m >> c) & 1u)) acc += v[c];
+  if (m) acc = __ldcs(ycol + (size_t)(__ffs(m) - 1) * n + i);
+  const unsigned rest = m & (m - 1u);
+  unsigned pending = __reduce_or_sync(0xffffffffu, rest);
+  while (pending) {
+    const int c = __ffs(pending) - 1;
+    pending &= pending - 1u;
+    if ((rest >> c) & 1u) acc += __ldcs(ycol + (size_t)c * n + i);
+  }
   if (i < n) __stcs(y + i, acc);
 }
 

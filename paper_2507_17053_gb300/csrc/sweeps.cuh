@@ -201,8 +201,9 @@ struct PairOf<double> {
 
 // 3D: three phases over z-, y- and x-lines.  The z-line (j0, j1) = line tl of
 // cell c is read from X[xb + xs * j2] (the caller's tile layout); AE and BG
-// hold per-cell pair tiles.  The x-line result of line `tl` of cell `c` is
-// returned in out[].
+// hold per-cell pair tiles, and BG may be AE itself (a phase-2 thread
+// rewrites only the nodes of its own y-line, after reading them).  The
+// x-line result of line `tl` of cell `c` is returned in out[].
 template <typename T, int N>
 __device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, int xb, int xs,
                                                typename PairOf<T>::type* AE,

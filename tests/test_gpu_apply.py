@@ -117,5 +117,13 @@ def test_autotuned_tile_shapes_keep_parity(w):
     shapes = G.sbm_autotune(P.handle)
     assert all(s in (0, 1) for s in shapes)
     assert _rel(P.apply_f64(xd).cpu().numpy(), ref) <= TOL
+    ref32 = O.apply(x.astype(np.float32).astype(np.float64))
     y32 = P.apply_f32(xd.float()).double().cpu().numpy()
-    assert _rel(y32, O.apply(x.astype(np.float32).astype(np.float64))) <= 1e-5 * w.degree
+    assert _rel(y32, ref32) <= 1e-5 * w.degree
+    # each shape pinned explicitly
+    for s in (0, 1):
+        G.sbm_set_tile_shape(P.handle, s, s)
+        assert _rel(P.apply_f64(xd).cpu().numpy(), ref) <= TOL
+        assert _rel(P.apply_f32(xd.float()).double().cpu().numpy(), ref32) <= 1e-5 * w.degree
+    with pytest.raises(G.SbmError):
+        G.sbm_set_tile_shape(P.handle, 2, 0)
