@@ -106,6 +106,8 @@ static void free_device(DeviceData* dd) {
     cudaFree(ct.first);
     cudaFree(ct.colour);
     cudaFree(ct.dof_mask);
+    cudaFree(ct.multi);
+    cudaFree(ct.multi_mask);
   }
   cudaFree(dd->diag_pos);
   cudaFree(dd->err_flag);
@@ -246,6 +248,19 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
       if ((e = upload(&dd->chunks[v].colour, ch_col[v].data(), ch_col[v].size())) != cudaSuccess)
         goto err;
       if ((e = upload(&dd->chunks[v].dof_mask, mask.data(), mask.size())) != cudaSuccess)
+        goto err;
+      std::vector<int32_t> multi;
+      std::vector<uint8_t> multi_mask;
+      for (int64_t g = 0; g < hp.n_dofs; ++g)
+        if (mask[g] & (mask[g] - 1)) {
+          multi.push_back((int32_t)g);
+          multi_mask.push_back(mask[g]);
+        }
+      dd->chunks[v].nmulti = (int64_t)multi.size();
+      if (!multi.empty() &&
+          ((e = upload(&dd->chunks[v].multi, multi.data(), multi.size())) != cudaSuccess ||
+           (e = upload(&dd->chunks[v].multi_mask, multi_mask.data(), multi_mask.size())) !=
+               cudaSuccess))
         goto err;
     }
     // ordered positions grouped by the parity colour of the cell (diagonal kernel)

@@ -10,12 +10,14 @@
 //     the block gathers those runs coalesced, runs the cell sweeps
 //     (Algorithm 1) for each cell, folds in the cells' surrogate faces, sums
 //     the values of the x-face nodes its consecutive cells share in shared
-//     memory, and writes each run once, coalesced, into the accumulation
-//     buffer of the chunk's colour.  A chunk's colour is (its parity within
-//     its row run, cy mod 2[, cz mod 2]); chunks of one colour share no DoF,
-//     so every buffer element has a single writer;
-//  3. the assembly kernel: y_i = sum over the colours that touch DoF i (a
-//     per-DoF bit mask) of buffer_c[i], in fixed colour order.
+//     memory, and writes each run once, coalesced: a DoF that no other chunk
+//     touches goes straight to y, any other into the accumulation buffer of
+//     the chunk's colour.  A chunk's colour is (its parity within its row
+//     run, cy mod 2[, cz mod 2]); chunks of one colour share no DoF, so every
+//     element of y and of the buffers has a single writer;
+//  3. the assembly kernel, over the DoFs that two colours or more touch:
+//     y_i = sum over those colours (a per-DoF bit mask) of buffer_c[i], in
+//     fixed colour order.
 // No atomics, no read-modify-write, no y = 0 fill; repeated applies are
 // bitwise equal.
 #include <algorithm>
@@ -43,7 +45,9 @@ CellLaunch cell_launch_shape(int d, int n) {
 template <typename T>
 struct ChunkArgs {
   const T* __restrict__ x;
+  T* __restrict__ y;                       // result (DoFs of a single colour)
   T* __restrict__ ycol;                    // [ncolours][n_dofs] accumulation buffers
+  const uint8_t* __restrict__ dof_mask;    // [n_dofs] colours touching each DoF
   const int32_t* __restrict__ lines;       // ordered cells x L
   const int32_t* __restrict__ face_start;  // ordered cells + 1
   const int32_t* __restrict__ face_kind;
@@ -52,8 +56,8 @@ struct ChunkArgs {
   const uint8_t* __restrict__ chunk_col;   // [nchunk] colour of each chunk
   int64_t n_dofs;
   int nchunk;
-  // right-hand side blockIdx.y of a multi-RHS launch: offsets of its x, its
-  // colour buffers and its face results (0 for a single right-hand side)
+  // right-hand side blockIdx.y of a multi-RHS launch: offsets of its x and y,
+  // its colour buffers and its face results (0 for a single right-hand side)
   int64_t ldx, ld_ycol, ld_face;
 };
 
@@ -98,7 +102,8 @@ struct ChunkSmem {
   static constexpr int SM0 = (N - 1) * R + 1;
   static constexpr int SM = (SM0 % 2) ? SM0 : SM0 + 1;        // odd row stride of the runs
   static constexpr int XZ = (L * SM > R * L * N) ? L * SM : R * L * N;
-  static constexpr size_t bytes = (size_t)(2 * R * ND + XZ) * sizeof(T);
+  // + the DoF colour masks of the runs ([L][SM] bytes)
+  static constexpr size_t bytes = (size_t)(2 * R * ND + XZ) * sizeof(T) + (size_t)L * SM;
 };
 
 template <typename T, int D, int N, int R>
@@ -112,21 +117,26 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   P2* BG = AE;                                // phase 2 runs in place
   T* Xs = reinterpret_cast<T*>(AE + R * ND);  // [L][SM] the chunk's x-line runs ...
   T* Z = Xs;                                  // ... then [R][L][N] per-cell x-line results
+  uint8_t* Ms = reinterpret_cast<uint8_t*>(Xs + ChunkSmem<T, D, N, R>::XZ);   // [L][SM] masks
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
   const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
   const T* fo = a.face_out + blockIdx.y * a.ld_face;
   T* ycb = a.ycol + blockIdx.y * a.ld_ycol;
+  T* yb = a.y + blockIdx.y * a.ldx;
 
   for (int ch = blockIdx.x; ch < a.nchunk; ch += gridDim.x) {
     const int first = __ldg(a.chunk_first + ch);
     const int nc = __ldg(a.chunk_first + ch + 1) - first;
     const int S = P * nc + 1;                 // values per x-line run
     const int* lines0 = a.lines + (size_t)first * L;
-    // coalesced gather of the L runs
+    // coalesced gather of the L runs (and of their DoFs' colour masks, which
+    // decide below where each result goes)
     for (int idx = tid; idx < L * S; idx += blockDim.x) {
       const int l = idx / S, kk = idx - l * S;
-      Xs[l * SM + kk] = __ldg(xr + __ldg(lines0 + l) + kk);
+      const int64_t g = (int64_t)__ldg(lines0 + l) + kk;
+      Xs[l * SM + kk] = __ldg(xr + g);
+      Ms[l * SM + kk] = __ldg(a.dof_mask + g);
     }
     __syncthreads();
     const bool act = c < nc;
@@ -148,7 +158,8 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
     }
     __syncthreads();
     // runs of the result: the node shared by cells c-1 and c is the sum of
-    // their two values (fixed order), then one coalesced store per run
+    // their two values (fixed order), then one coalesced store per run, into
+    // y where this chunk is the DoF's only writer
     T* yc = ycb + (size_t)__ldg(a.chunk_col + ch) * a.n_dofs;
     for (int idx = tid; idx < L * S; idx += blockDim.x) {
       const int l = idx / S, kk = idx - l * S;
@@ -157,36 +168,48 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
       if (cc == nc) v = Z[((nc - 1) * L + l) * N + P];
       else if (m == 0 && cc > 0) v = Z[((cc - 1) * L + l) * N + P] + Z[(cc * L + l) * N];
       else v = Z[(cc * L + l) * N + m];
-      yc[__ldg(lines0 + l) + kk] = v;
+      const int64_t g = (int64_t)__ldg(lines0 + l) + kk;
+      const unsigned mk = Ms[l * SM + kk];
+      if (mk & (mk - 1u)) yc[g] = v;
+      else yb[g] = v;
     }
     __syncthreads();                          // Xs / Z are reused by the next chunk
   }
 }
 
-// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order: the
-// lowest colour's value is loaded, the others are added to it.  Most DoFs
-// lie inside one chunk (a single colour) and cost no addition; the loop over
-// the further colours is warp-uniform (on GB300 a double addition costs an
+// For the DoFs i = multi[t] that several colours touch:
+// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order (the lowest
+// colour's value is loaded, the others are added to it).  The loop over the
+// further colours is warp-uniform (on GB300 a double addition costs an
 // FP64-pipe slot per warp instruction, whatever its active lanes).
 template <typename T>
-__global__ void assemble_kernel(const T* __restrict__ ycol, const uint8_t* __restrict__ mask,
-                                T* __restrict__ y, int64_t n, int ncol, int64_t ld_ycol = 0,
+__global__ void assemble_kernel(const T* __restrict__ ycol, const int32_t* __restrict__ multi,
+                                const uint8_t* __restrict__ multi_mask, T* __restrict__ y,
+                                int64_t n, int64_t nmulti, int ncol, int64_t ld_ycol = 0,
                                 int64_t ldy = 0) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   ycol += blockIdx.y * ld_ycol;
   y += blockIdx.y * ldy;
-  unsigned m = (i < n) ? (unsigned)__ldg(mask + i) : 0u;
-  if (ncol < 8) m &= (1u << ncol) - 1u;
-  T acc = T(0);
-  if (m) acc = __ldcs(ycol + (size_t)(__ffs(m) - 1) * n + i);
-  const unsigned rest = m & (m - 1u);
-  unsigned pending = __reduce_or_sync(0xffffffffu, rest);
-  while (pending) {
-    const int c = __ffs(pending) - 1;
-    pending &= pending - 1u;
-    if ((rest >> c) & 1u) acc += __ldcs(ycol + (size_t)c * n + i);
+  int64_t i = 0;
+  unsigned m = 0u;
+  if (t < nmulti) {
+    i = __ldg(multi + t);
+    m = (unsigned)__ldg(multi_mask + t);
   }
-  if (i < n) __stcs(y + i, acc);
+  if (ncol < 8) m &= (1u << ncol) - 1u;
+  // all loads first (independent), then the sum
+  T v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = ((m >> c) & 1u) ? __ldcs(ycol + (size_t)c * n + i) : T(0);
+  const unsigned c0 = m ? (unsigned)(__ffs(m) - 1) : 0u;
+  T acc = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (c == (int)c0) acc = ((m >> c) & 1u) ? v[c] : acc;
+    if (__any_sync(0xffffffffu, ((m >> c) & 1u) && c != (int)c0))
+      acc += (c != (int)c0) ? v[c] : T(0);
+  }
+  if (t < nmulti) __stcs(y + i, acc);
 }
 
 // Blocks of the chunk kernel: 4 x (resident blocks per SM) x SMs at most
@@ -237,7 +260,9 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   if ((err = chunk_prepare<T, D, N, R>(&cap)) != cudaSuccess) return err;
   ChunkArgs<T> a;
   a.x = x;
+  a.y = y;
   a.ycol = ycol;
+  a.dof_mask = ct.dof_mask;
   a.lines = dd.lines;
   a.face_start = dd.face_start;
   a.face_kind = dd.face_kind;
@@ -254,9 +279,12 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   nlaunch++;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   const int64_t n = hp.n_dofs;
-  assemble_kernel<T><<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(
-      ycol, ct.dof_mask, y, n, dd.ncolours, (int64_t)dd.ncolours * n, ld);
-  nlaunch++;
+  if (ct.nmulti > 0) {
+    assemble_kernel<T><<<dim3((unsigned)((ct.nmulti + 255) / 256), nrhs), 256, 0, st>>>(
+        ycol, ct.multi, ct.multi_mask, y, n, ct.nmulti, dd.ncolours, (int64_t)dd.ncolours * n,
+        ld);
+    nlaunch++;
+  }
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (pr) {
     prof->count(nlaunch);

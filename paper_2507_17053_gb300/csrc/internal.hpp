@@ -53,6 +53,9 @@ struct ChunkTable {
   int32_t* first = nullptr;      // [n + 1] first ordered cell of each chunk
   uint8_t* colour = nullptr;     // [n] colour of each chunk
   uint8_t* dof_mask = nullptr;   // [n_dofs] bit c set if a chunk of colour c touches the DoF
+  int32_t* multi = nullptr;      // [nmulti] DoFs touched by two colours or more, ascending
+  uint8_t* multi_mask = nullptr; // [nmulti] their colour masks
+  int64_t nmulti = 0;
 };
 
 // Device-resident set-up data of one problem.
