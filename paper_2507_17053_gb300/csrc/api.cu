@@ -249,6 +249,7 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
         goto err;
       if ((e = upload(&dd->chunks[v].dof_mask, mask.data(), mask.size())) != cudaSuccess)
         goto err;
+      // DoFs of two colours or more, ascending
       std::vector<int32_t> multi;
       std::vector<uint8_t> multi_mask;
       for (int64_t g = 0; g < hp.n_dofs; ++g)

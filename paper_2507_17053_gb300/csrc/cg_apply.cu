@@ -129,11 +129,15 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
     const int first = __ldg(a.chunk_first + ch);
     const int nc = __ldg(a.chunk_first + ch + 1) - first;
     const int S = P * nc + 1;                 // values per x-line run
+    // idx -> (run l, position kk) without an integer division: idx < L*S
+    // <= 1600, so (idx + 1/2)/S in FP32 is within 1e-5 of the exact
+    // quotient, far inside its distance 1/(2S) >= 0.0038 from an integer
+    const float invS = 1.0f / (float)S;
     const int* lines0 = a.lines + (size_t)first * L;
     // coalesced gather of the L runs (and of their DoFs' colour masks, which
     // decide below where each result goes)
     for (int idx = tid; idx < L * S; idx += blockDim.x) {
-      const int l = idx / S, kk = idx - l * S;
+      const int l = __float2int_rz(((float)idx + 0.5f) * invS), kk = idx - l * S;
       const int64_t g = (int64_t)__ldg(lines0 + l) + kk;
       Xs[l * SM + kk] = __ldg(xr + g);
       Ms[l * SM + kk] = __ldg(a.dof_mask + g);
@@ -162,7 +166,7 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
     // y where this chunk is the DoF's only writer
     T* yc = ycb + (size_t)__ldg(a.chunk_col + ch) * a.n_dofs;
     for (int idx = tid; idx < L * S; idx += blockDim.x) {
-      const int l = idx / S, kk = idx - l * S;
+      const int l = __float2int_rz(((float)idx + 0.5f) * invS), kk = idx - l * S;
       const int cc = kk / P, m = kk - cc * P;
       T v;
       if (cc == nc) v = Z[((nc - 1) * L + l) * N + P];
