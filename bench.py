@@ -69,28 +69,28 @@ def workload(name):
 
 
 def cell_ops(d, p, n_cells):
-    """FP64/FP32 operations the cell kernel executes per apply: (FMAs, adds).
+    """FP64/FP32 operations the cell kernel executes per apply: (FMAs, other).
 
-    The exact cell stiffness is applied as 7 (3D) or 4 (2D) one-dimensional
-    matrix applications per line of the tile (Algorithm 1 in tensor-product
-    form).  For n = p+1 >= 5 each application uses the even/odd split of the
-    centrosymmetric 1D matrices: ((n+1)/2)^2 + (n/2)^2 FMAs, plus 2 (n/2)
-    additions for every folded input line and every unfolded output line
-    (3D: 5 folds and 5 unfolds per line triple; 2D: 3 and 3).  At p = 4 this
-    is 2275 FMAs + 1000 adds per cell; an ncu count of the FP64 kernel gives
-    2280 DFMA + 1035 DADD per cell (the rest: surrogate-face folds and the
-    shared x-face nodes)."""
+    3D: the exact cell operator in the eigenbasis of the 1D pencil (K, M),
+    A_K = h (V x V x V) diag(lam_i + lam_j + lam_k) (V x V x V)^T: per line of
+    the tile 6 one-dimensional transforms in even/odd form, ((n+1)/2)^2 +
+    (n/2)^2 FMAs each, n products (the diagonal), and 3 folds + 3 unfolds of
+    2 (n/2) additions each (p = 4: 1950 FMAs + 725 other per cell).
+    2D: 4 one-dimensional matrix applications per line (Algorithm 1 in
+    tensor-product form), even/odd split for n >= 5 with 3 folds and 3
+    unfolds per line pair."""
     n = p + 1
     lines = n ** (d - 1)
-    mats = 7 if d == 3 else 4
-    if n >= 5:
-        h, he = n // 2, (n + 1) // 2
-        fma = mats * (he * he + h * h)
-        adds = (10 if d == 3 else 6) * 2 * h
+    h, he = n // 2, (n + 1) // 2
+    if d == 3:
+        fma = 6 * (he * he + h * h)
+        other = n + 12 * h
+    elif n >= 5:
+        fma = 4 * (he * he + h * h)
+        other = 6 * 2 * h
     else:
-        fma, adds = mats * n * n, 0
-    return fma * lines * n_cells, adds * lines * n_cells
-
+        fma, other = 4 * n * n, 0
+    return fma * lines * n_cells, other * lines * n_cells
 
 
 def face_flops(d, p, n_sfaces):
@@ -493,7 +493,8 @@ def run_ours(args, w):
                      "unit": "G FP64 ops/s", "frac": achieved_gops / FP64_PIPE_GOPS,
                      "traffic": None,
                      "kernel": f"cg_chunk_kernel<double,{w.dim},{w.degree + 1}> (cell kernel)",
-                     "ops_per_launch": cops, "fma_per_launch": cfma, "add_per_launch": cadd,
+                     "ops_per_launch": cops, "fma_per_launch": cfma,
+                     "other_per_launch": cadd,
                      "launches_per_step": 1, "kernel_ms_per_launch": cell_ms,
                      "achieved_tflops": cflops / (cell_ms * 1e-3) / 1e12,
                      "peak_note": "FP64 pipe: 2 lane-ops per SM per clock x 152 SMs x "

@@ -61,6 +61,23 @@ KTab<T> make_ktab(const HostProblem& hp) {
   fold(tb.K, 1.0, &t.fK);
   fold(tb.M, hd2, &t.fMh);
   fold(tb.K, hd2, &t.fKh);
+  // V^T on a folded line: even mode ke = sum_{j < HE} V[j][ke] e_j, odd mode
+  // ko = sum_{j < H} V[j][ko] o_j; V on the modes: s_j = sum V[j][ke] w_ke,
+  // d_j = sum V[j][ko] w_ko, then y_j = s_j + d_j, y_{n-1-j} = s_j - d_j
+  {
+    const int H = n / 2, HE = (n + 1) / 2;
+    for (int i = 0; i < HE; ++i)
+      for (int j = 0; j < HE; ++j) {
+        t.fVt.E[i][j] = (T)tb.V[j][i];
+        t.fV.E[j][i] = (T)tb.V[j][i];
+      }
+    for (int i = 0; i < H; ++i)
+      for (int j = 0; j < H; ++j) {
+        t.fVt.O[i][j] = (T)tb.V[j][HE + i];
+        t.fV.O[j][i] = (T)tb.V[j][HE + i];
+      }
+    for (int k = 0; k < n; ++k) t.hlam[k] = (T)(hd2 * tb.lam[k]);
+  }
   return t;
 }
 template KTab<double> make_ktab<double>(const HostProblem&);

@@ -61,6 +61,40 @@ struct ChunkArgs {
   int64_t ldx, ld_ycol, ld_face;
 };
 
+// Add the contributions of surrogate face (k, s) to the z-line result out[]
+// (nodes (a, b, m), m = 0..n-1) of a 3D cell: R[node with j_k = kend] +=
+// rv[jt], R[node] += phi_{j_k}'(s) rg[jt], jt = the node's tangential index
+// (the two other axes in increasing order, the first fastest).
+template <typename T, int N>
+__device__ __forceinline__ void fold_face_z(const KTab<T>& t, const T* __restrict__ fo, int k,
+                                            int s, int a, int b, T (&out)[N]) {
+  constexpr int L = N * N;
+  const T* rv = fo;
+  const T* rg = fo + L;
+  const int kend = s ? N - 1 : 0;
+  if (k == 2) {                       // normal along the line, tangential (a, b)
+    const int jt = a + N * b;
+    const T v = __ldg(rv + jt), g = __ldg(rg + jt);
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      out[m] = fma(s ? t.D1[m] : t.D0[m], g, out[m]);
+      if (m == kend) out[m] += v;       // compile-time index: out stays in registers
+    }
+  } else {
+    // k == 0: j_k = a, tangential (j1, j2) = (b, m);  k == 1: j_k = b, (j0, j2) = (a, m)
+    const int jk = (k == 0) ? a : b;
+    const int jo = (k == 0) ? b : a;
+    const T dk = s ? t.D1[jk] : t.D0[jk];
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      const int jt = jo + N * m;
+      T add = dk * __ldg(rg + jt);
+      if (jk == kend) add += __ldg(rv + jt);
+      out[m] += add;
+    }
+  }
+}
+
 // Add the contributions of surrogate face (k, s) to the x-line result out[]
 // of line tl: R[node (kend, jt)] += rv[jt], R[node (j, jt)] += phi_j'(s) rg[jt].
 template <typename T, int D, int N>
@@ -96,14 +130,21 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
 // overwrites its own y-lines in place) and one scalar area that holds the
 // gathered x-line runs until the first phase has read them and the per-cell
 // x-line results after the last one.
+// 3D: one scalar tile of R cells (the eigenbasis sweeps run in place and
+// leave the cells' results there) and the gathered runs.  2D: one pair tile
+// (the second sweep phase overwrites its own lines in place) and one area
+// that holds the gathered runs until the first phase has read them and the
+// per-cell x-line results after the last one.  Both: + the DoF colour masks
+// of the runs ([L][SM] bytes).
 template <typename T, int D, int N, int R>
 struct ChunkSmem {
   static constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
   static constexpr int SM0 = (N - 1) * R + 1;
   static constexpr int SM = (SM0 % 2) ? SM0 : SM0 + 1;        // odd row stride of the runs
   static constexpr int XZ = (L * SM > R * L * N) ? L * SM : R * L * N;
-  // + the DoF colour masks of the runs ([L][SM] bytes)
-  static constexpr size_t bytes = (size_t)(2 * R * ND + XZ) * sizeof(T) + (size_t)L * SM;
+  static constexpr int TILE = (D == 3) ? R * ND : 2 * R * ND;  // scalars before the runs
+  static constexpr int XS = (D == 3) ? L * SM : XZ;
+  static constexpr size_t bytes = (size_t)(TILE + XS) * sizeof(T) + (size_t)L * SM;
 };
 
 template <typename T, int D, int N, int R>
@@ -113,13 +154,22 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   constexpr int SM = ChunkSmem<T, D, N, R>::SM;
   using P2 = typename PairOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  P2* AE = reinterpret_cast<P2*>(smem_raw);   // pair tile first (8/16-byte aligned)
-  P2* BG = AE;                                // phase 2 runs in place
-  T* Xs = reinterpret_cast<T*>(AE + R * ND);  // [L][SM] the chunk's x-line runs ...
-  T* Z = Xs;                                  // ... then [R][L][N] per-cell x-line results
-  uint8_t* Ms = reinterpret_cast<uint8_t*>(Xs + ChunkSmem<T, D, N, R>::XZ);   // [L][SM] masks
+  using CS = ChunkSmem<T, D, N, R>;
+  T* tile = reinterpret_cast<T*>(smem_raw);   // 3D: [R][ND] scalar tile
+  P2* AE = reinterpret_cast<P2*>(smem_raw);   // 2D: pair tile (8/16-byte aligned); phase 2
+  P2* BG = AE;                                //     runs in place
+  T* Xs = tile + CS::TILE;                    // [L][SM] the chunk's x-line runs
+  // per-cell results, node (j0, j1, j2) of cell c at c ND + j0 + n j1 + n^2 j2
+  // (3D: the tile; 2D: the run area, free after the first phase)
+  T* Z = (D == 3) ? tile : Xs;
+  uint8_t* Ms = reinterpret_cast<uint8_t*>(Xs + CS::XS);   // [L][SM] masks
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
+  // 3D: h (lam_i + lam_a + lam_b) for this thread's x-line of modes (a, b)
+  T sc[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    sc[i] = (D == 3) ? (t.hlam[i] + t.hlam[tl % N]) + t.hlam[tl / N] : T(0);
   const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
   const T* fo = a.face_out + blockIdx.y * a.ld_face;
   T* ycb = a.ycol + blockIdx.y * a.ld_ycol;
@@ -145,9 +195,9 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
     __syncthreads();
     const bool act = c < nc;
     T out[N];
-    if (D == 3)
-      cell_sweeps_3d<T, N>(t, Xs, (tl / N) * SM + P * c + (tl % N), N * SM, AE, BG, c, tl, act,
-                           out);
+    if constexpr (D == 3)
+      cell_fd_3d<T, N>(t, Xs, (tl / N) * SM + P * c + (tl % N), N * SM, tile, c, tl, act, sc,
+                       out);
     else
       cell_sweeps_2d<T, N>(t, Xs, P * c + tl, SM, AE, c, tl, act, out);
     if (act) {
@@ -155,10 +205,17 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
       const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);
       for (int f = fs; f < fe; ++f) {
         const int kind = __ldg(a.face_kind + f);
-        fold_face<T, D, N>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, tl, out);
+        if constexpr (D == 3)
+          fold_face_z<T, N>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, tl % N, tl / N, out);
+        else
+          fold_face<T, D, N>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, tl, out);
       }
+      // 3D: z-line (j0, j1) = tl, back to the nodes it was read from
 #pragma unroll
-      for (int m = 0; m < N; ++m) Z[(c * L + tl) * N + m] = out[m];
+      for (int m = 0; m < N; ++m) {
+        if constexpr (D == 3) Z[c * ND + tl + L * m] = out[m];
+        else Z[(c * L + tl) * N + m] = out[m];
+      }
     }
     __syncthreads();
     // runs of the result: the node shared by cells c-1 and c is the sum of

@@ -42,6 +42,11 @@ struct KTab {
   T h_inv;
   T sigma;
   Folded<T> fM, fK, fMh, fKh;  // even/odd parts of M, K, Mh, Kh (GLL nodes are symmetric)
+  // eigenbasis of the pencil (K, M) (M = V V^T, K = V diag(lam) V^T; even
+  // modes first): fVt maps a folded nodal line to its modes, fV modes back
+  // to a line; hlam = h^(d-2) lam
+  Folded<T> fVt, fV;
+  T hlam[kMaxN];
 };
 
 template <typename T>

@@ -29,6 +29,129 @@ static void legendre(int m, double t, double* P, double* dP) {
   *dP = m * (p0 - t * p1) / (1.0 - t * t);
 }
 
+// Eigenbasis of the symmetric-definite pencil (K, M): Cholesky M = C C^T,
+// cyclic Jacobi rotations on the symmetric C^-1 K C^-T = Q diag(lam) Q^T,
+// V = C Q.  Then M = V V^T and K = V diag(lam) V^T.  Each column of V is
+// made exactly even or odd, and the columns are reordered (even modes, then
+// odd modes, each by increasing eigenvalue).
+static void pencil_eigenbasis(Tables1D* t) {
+  const int n = t->n;
+  double C[kMaxN][kMaxN] = {};
+  for (int j = 0; j < n; ++j) {
+    double d = t->M[j][j];
+    for (int k = 0; k < j; ++k) d -= C[j][k] * C[j][k];
+    C[j][j] = std::sqrt(d);
+    for (int i = j + 1; i < n; ++i) {
+      double s = t->M[i][j];
+      for (int k = 0; k < j; ++k) s -= C[i][k] * C[j][k];
+      C[i][j] = s / C[j][j];
+    }
+  }
+  // B = C^-1 K C^-T: forward substitution on the columns of K, then on the rows
+  double Y[kMaxN][kMaxN], B[kMaxN][kMaxN];
+  for (int c = 0; c < n; ++c)
+    for (int i = 0; i < n; ++i) {
+      double s = t->K[i][c];
+      for (int k = 0; k < i; ++k) s -= C[i][k] * Y[k][c];
+      Y[i][c] = s / C[i][i];
+    }
+  for (int r = 0; r < n; ++r)
+    for (int i = 0; i < n; ++i) {
+      double s = Y[r][i];
+      for (int k = 0; k < i; ++k) s -= C[i][k] * B[r][k];
+      B[r][i] = s / C[i][i];
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) B[i][j] = B[j][i] = 0.5 * (B[i][j] + B[j][i]);
+  double Q[kMaxN][kMaxN] = {};
+  for (int i = 0; i < n; ++i) Q[i][i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      diag += B[i][i] * B[i][i];
+      for (int j = i + 1; j < n; ++j) off += B[i][j] * B[i][j];
+    }
+    if (off <= 1e-34 * diag) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (B[p][q] == 0.0) continue;
+        // rotation zeroing B[p][q] (the symmetric Schur step)
+        const double theta = (B[q][q] - B[p][p]) / (2.0 * B[p][q]);
+        const double tt = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(tt * tt + 1.0), sn = tt * cs;
+        for (int k = 0; k < n; ++k) {
+          const double bp = B[k][p], bq = B[k][q];
+          B[k][p] = cs * bp - sn * bq;
+          B[k][q] = sn * bp + cs * bq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double bp = B[p][k], bq = B[q][k];
+          B[p][k] = cs * bp - sn * bq;
+          B[q][k] = sn * bp + cs * bq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double qp = Q[k][p], qq = Q[k][q];
+          Q[k][p] = cs * qp - sn * qq;
+          Q[k][q] = sn * qp + cs * qq;
+        }
+      }
+  }
+  double V0[kMaxN][kMaxN];
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      double s = 0.0;
+      for (int m = 0; m <= i; ++m) s += C[i][m] * Q[m][k];
+      V0[i][k] = s;
+    }
+  // parity of each column, exact symmetry, order
+  int order[kMaxN], parity[kMaxN];
+  for (int k = 0; k < n; ++k) {
+    double de = 0.0, dodd = 0.0;
+    for (int j = 0; j < n; ++j) {
+      de += std::fabs(V0[j][k] - V0[n - 1 - j][k]);
+      dodd += std::fabs(V0[j][k] + V0[n - 1 - j][k]);
+    }
+    parity[k] = (de <= dodd) ? 0 : 1;
+    for (int j = 0; j < n / 2; ++j) {
+      const double a = V0[j][k], b = V0[n - 1 - j][k];
+      const double m = parity[k] ? 0.5 * (a - b) : 0.5 * (a + b);
+      V0[j][k] = m;
+      V0[n - 1 - j][k] = parity[k] ? -m : m;
+    }
+    if ((n & 1) && parity[k]) V0[n / 2][k] = 0.0;
+    order[k] = k;
+  }
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b) {
+      const int ka = order[a], kb = order[b];
+      const bool swap = parity[kb] < parity[ka] ||
+                        (parity[kb] == parity[ka] && B[kb][kb] < B[ka][ka]);
+      if (swap) std::swap(order[a], order[b]);
+    }
+  double lmax = 0.0;
+  for (int k = 0; k < n; ++k) lmax = std::max(lmax, std::fabs(B[k][k]));
+  for (int k = 0; k < n; ++k) {
+    t->lam[k] = B[order[k]][order[k]];
+    // the constant mode: K annihilates constants, its eigenvalue is 0
+    if (std::fabs(t->lam[k]) <= 1e-12 * lmax) t->lam[k] = 0.0;
+    for (int j = 0; j < n; ++j) t->V[j][k] = V0[j][order[k]];
+  }
+  double em = 0.0, ek = 0.0, sm = 0.0, sk = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double m = 0.0, kk = 0.0;
+      for (int k = 0; k < n; ++k) {
+        m += t->V[i][k] * t->V[j][k];
+        kk += t->V[i][k] * t->lam[k] * t->V[j][k];
+      }
+      em = std::max(em, std::fabs(m - t->M[i][j]));
+      ek = std::max(ek, std::fabs(kk - t->K[i][j]));
+      sm = std::max(sm, std::fabs(t->M[i][j]));
+      sk = std::max(sk, std::fabs(t->K[i][j]));
+    }
+  t->fd_residual = em / sm + ek / sk;
+}
+
 void build_tables(int p, Tables1D* t) {
   const int n = p + 1;
   *t = Tables1D();
@@ -95,6 +218,7 @@ void build_tables(int p, Tables1D* t) {
     }
   lagrange_derivs(*t, 0.0, t->D0);
   lagrange_derivs(*t, 1.0, t->D1);
+  pencil_eigenbasis(t);
 }
 
 // Barycentric weights lambda_j = 1 / prod_{m != j} (x_j - x_m).
@@ -360,6 +484,10 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
     P.sigma_f = 0.0;
   }
   build_tables(p, &P.tab);
+  if (!(P.tab.fd_residual <= 1e-12)) {
+    *err = "1D eigenbasis of the cell operator is inaccurate";
+    return SBM_ERR_UNSUPPORTED;
+  }
   const double h = P.h;
 
   // active cells: phi(centre) < 0, centre = -1 + h (i + 1/2)

@@ -26,6 +26,13 @@ struct Tables1D {
   double K[kMaxN][kMaxN] = {};     // 1D stiffness sum_q w_q phi_i'(g_q) phi_j'(g_q)
   double D0[kMaxN] = {};           // phi_j'(0)
   double D1[kMaxN] = {};           // phi_j'(1)
+  // Eigenbasis of the pencil (K, M): M = V V^T, K = V diag(lam) V^T.  The
+  // columns of V are even or odd about the interval's midpoint (M and K are
+  // centrosymmetric on symmetric nodes): the ceil(n/2) even modes first, then
+  // the floor(n/2) odd ones, each group by increasing eigenvalue.
+  double V[kMaxN][kMaxN] = {};
+  double lam[kMaxN] = {};
+  double fd_residual = 0.0;        // max |V V^T - M| + max |V lam V^T - K|, relative
 };
 
 // GLL nodes by Newton on (1-t^2) P_p'(t) with the Legendre recurrence, Gauss

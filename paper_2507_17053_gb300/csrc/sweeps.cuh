@@ -35,6 +35,7 @@ struct LineFold {
   static constexpr int H = N / 2, HE = (N + 1) / 2;
   T e[HE];
   T o[H > 0 ? H : 1];
+  __device__ __forceinline__ LineFold() {}
   __device__ __forceinline__ explicit LineFold(const T (&v)[N]) {
 #pragma unroll
     for (int j = 0; j < H; ++j) {
@@ -42,6 +43,15 @@ struct LineFold {
       o[j] = v[j] - v[N - 1 - j];
     }
     if (N & 1) e[H] = v[H];
+  }
+  // modal coefficients (even modes first) are already split: no additions
+  __device__ __forceinline__ static LineFold of_modes(const T (&w)[N]) {
+    LineFold f;
+#pragma unroll
+    for (int i = 0; i < HE; ++i) f.e[i] = w[i];
+#pragma unroll
+    for (int i = 0; i < H; ++i) f.o[i] = w[HE + i];
+    return f;
   }
 };
 
@@ -179,6 +189,98 @@ __device__ __forceinline__ void line_phase2(const KTab<T>& t, const T (&va)[N], 
       b[m] = bb;
       g[m] = gg;
     }
+  }
+}
+
+// w = V^T v: the modes of a nodal line (even modes first); the folded input
+// feeds the even and the odd modes, and the output needs no unfolding.
+template <typename T, int N>
+__device__ __forceinline__ void line_to_modes(const Folded<T>& Vt, const T (&v)[N], T (&w)[N]) {
+  LineFold<T, N> f(v);
+  LineAcc<T, N> acc;
+  acc.mac(Vt, f);
+#pragma unroll
+  for (int i = 0; i < LineAcc<T, N>::HE; ++i) w[i] = acc.s[i];
+#pragma unroll
+  for (int i = 0; i < LineAcc<T, N>::H; ++i) w[LineAcc<T, N>::HE + i] = acc.d[i];
+}
+
+// y = V w: a nodal line from its modes (no folding of the input).
+template <typename T, int N>
+__device__ __forceinline__ void modes_to_line(const Folded<T>& V, const T (&w)[N], T (&y)[N]) {
+  const LineFold<T, N> f = LineFold<T, N>::of_modes(w);
+  LineAcc<T, N> acc;
+  acc.mac(V, f);
+  acc.unfold(y);
+}
+
+// ---- 3D cell term in the eigenbasis of the 1D pencil ---------------------------
+//
+// With M = V V^T and K = V diag(lam) V^T (the generalised eigenvectors of
+// (K, M), scaled), the exact cell operator factors as
+//   A_K = h (V x V x V) diag(lam_i + lam_j + lam_k) (V x V x V)^T,
+// five line phases over one scalar tile per cell, in place (a thread reads
+// its line, then writes the same nodes): z-lines to z-modes, y-lines to
+// y-modes, x-lines to x-modes / scale / back, y-modes back, z-modes back.
+// Every 1D transform is an even/odd split product (V's columns are even or
+// odd), so a line costs 6 (ceil(n/2)^2 + floor(n/2)^2) FMAs, n products and
+// 3 folds + 3 unfolds of 2 floor(n/2) additions each -- 107 operations per
+// line at p = 4, against 131 for the 7-sweep form.  Tile layout: node (j0, j1, j2) at
+// j0 + n j1 + n^2 j2.  The z-line (j0, j1) = line tl of cell c is read from
+// X[xb + xs * j2]; sc[i] = h (lam_i + lam_a + lam_b) for the thread's
+// x-line of modes (a, b) = (tl % n, tl / n).  The z-line result of line tl is
+// returned in out[] (nodal, j2 = 0..n-1); the tile then holds nothing useful.
+template <typename T, int N>
+__device__ __forceinline__ void cell_fd_3d(const KTab<T>& t, const T* X, int xb, int xs, T* tile,
+                                           int c, int tl, bool act, const T (&sc)[N],
+                                           T (&out)[N]) {
+  constexpr int L = N * N, ND = L * N;
+  const int a = tl % N, b = tl / N;
+  T* cell = tile + c * ND;
+  if (act) {                       // z-lines (j0, j1) = (a, b) -> z-modes
+    T v[N], w[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = X[xb + xs * j];
+    line_to_modes<T, N>(t.fVt, v, w);
+#pragma unroll
+    for (int k = 0; k < N; ++k) cell[tl + L * k] = w[k];
+  }
+  __syncthreads();
+  if (act) {                       // y-lines (j0 = a, z-mode b) -> y-modes
+    T v[N], w[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = cell[a + N * j + L * b];
+    line_to_modes<T, N>(t.fVt, v, w);
+#pragma unroll
+    for (int k = 0; k < N; ++k) cell[a + N * k + L * b] = w[k];
+  }
+  __syncthreads();
+  if (act) {                       // x-lines (y-mode a, z-mode b): modes, scale, back
+    T v[N], w[N], y[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[j] = cell[N * tl + j];
+    line_to_modes<T, N>(t.fVt, v, w);
+#pragma unroll
+    for (int i = 0; i < N; ++i) w[i] *= sc[i];
+    modes_to_line<T, N>(t.fV, w, y);
+#pragma unroll
+    for (int j = 0; j < N; ++j) cell[N * tl + j] = y[j];
+  }
+  __syncthreads();
+  if (act) {                       // y-modes back (j0 = a, z-mode b)
+    T w[N], y[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = cell[a + N * k + L * b];
+    modes_to_line<T, N>(t.fV, w, y);
+#pragma unroll
+    for (int j = 0; j < N; ++j) cell[a + N * j + L * b] = y[j];
+  }
+  __syncthreads();
+  if (act) {                       // z-modes back (j0, j1) = (a, b)
+    T w[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = cell[tl + L * k];
+    modes_to_line<T, N>(t.fV, w, out);
   }
 }
 
