@@ -122,7 +122,7 @@ static void free_device(DeviceData* dd) {
   for (auto& ct : dd->chunks) {
     cudaFree(ct.first);
     cudaFree(ct.colour);
-    cudaFree(ct.dof_mask);
+    cudaFree(ct.run_bits);
     cudaFree(ct.multi);
     cudaFree(ct.multi_mask);
   }
@@ -264,8 +264,29 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
         goto err;
       if ((e = upload(&dd->chunks[v].colour, ch_col[v].data(), ch_col[v].size())) != cudaSuccess)
         goto err;
-      if ((e = upload(&dd->chunks[v].dof_mask, mask.data(), mask.size())) != cudaSuccess)
-        goto err;
+      // per chunk: which elements of its L runs (p*nc + 1 each) several colours share
+      {
+        const int R = v == 0 ? chunk_cells(d, n) : std::max(chunk_cells(d, n) / 2, 1);
+        const int words = (L * ((n - 1) * R + 1) + 31) / 32;
+        std::vector<uint32_t> bits((size_t)nch * words, 0u);
+        for (int k = 0; k < nch; ++k) {
+          const int nc = ch_first[v][k + 1] - ch_first[v][k];
+          const int S = (n - 1) * nc + 1;
+          for (int l = 0; l < L; ++l) {
+            const int64_t g0 = lines_o[(int64_t)ch_first[v][k] * L + l];
+            for (int kk = 0; kk < S; ++kk) {
+              const uint8_t mk = mask[g0 + kk];
+              if (mk & (mk - 1)) {
+                const int b = l * S + kk;
+                bits[(size_t)k * words + b / 32] |= 1u << (b % 32);
+              }
+            }
+          }
+        }
+        dd->chunks[v].bit_words = words;
+        if ((e = upload(&dd->chunks[v].run_bits, bits.data(), bits.size())) != cudaSuccess)
+          goto err;
+      }
       // DoFs of two colours or more, ascending
       std::vector<int32_t> multi;
       std::vector<uint8_t> multi_mask;

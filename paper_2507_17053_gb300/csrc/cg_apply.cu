@@ -47,7 +47,8 @@ struct ChunkArgs {
   const T* __restrict__ x;
   T* __restrict__ y;                       // result (DoFs of a single colour)
   T* __restrict__ ycol;                    // [ncolours][n_dofs] accumulation buffers
-  const uint8_t* __restrict__ dof_mask;    // [n_dofs] colours touching each DoF
+  const uint32_t* __restrict__ run_bits;   // per chunk: bit l*S + kk set if that run
+  int bit_words;                           //   element is a DoF of several colours
   const int32_t* __restrict__ lines;       // ordered cells x L
   const int32_t* __restrict__ face_start;  // ordered cells + 1
   const int32_t* __restrict__ face_kind;
@@ -134,8 +135,8 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
 // leave the cells' results there) and the gathered runs.  2D: one pair tile
 // (the second sweep phase overwrites its own lines in place) and one area
 // that holds the gathered runs until the first phase has read them and the
-// per-cell x-line results after the last one.  Both: + the DoF colour masks
-// of the runs ([L][SM] bytes).
+// per-cell x-line results after the last one.  Both: + the L run starts and
+// the chunk's run-element bits (several colours or not).
 template <typename T, int D, int N, int R>
 struct ChunkSmem {
   static constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND;
@@ -144,7 +145,8 @@ struct ChunkSmem {
   static constexpr int XZ = (L * SM > R * L * N) ? L * SM : R * L * N;
   static constexpr int TILE = (D == 3) ? R * ND : 2 * R * ND;  // scalars before the runs
   static constexpr int XS = (D == 3) ? L * SM : XZ;
-  static constexpr size_t bytes = (size_t)(TILE + XS) * sizeof(T) + (size_t)L * SM;
+  static constexpr int WORDS = (L * SM + 31) / 32;              // run-element bits
+  static constexpr size_t bytes = (size_t)(TILE + XS) * sizeof(T) + (size_t)(L + WORDS) * 4;
 };
 
 template <typename T, int D, int N, int R>
@@ -162,7 +164,8 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   // per-cell results, node (j0, j1, j2) of cell c at c ND + j0 + n j1 + n^2 j2
   // (3D: the tile; 2D: the run area, free after the first phase)
   T* Z = (D == 3) ? tile : Xs;
-  uint8_t* Ms = reinterpret_cast<uint8_t*>(Xs + CS::XS);   // [L][SM] masks
+  int* Ls = reinterpret_cast<int*>(Xs + CS::XS);            // [L] run starts
+  uint32_t* Bs = reinterpret_cast<uint32_t*>(Ls + L);        // run-element bits
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
   // 3D: h (lam_i + lam_a + lam_b) for this thread's x-line of modes (a, b)
@@ -183,14 +186,18 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
     // <= 1600, so (idx + 1/2)/S in FP32 is within 1e-5 of the exact
     // quotient, far inside its distance 1/(2S) >= 0.0038 from an integer
     const float invS = 1.0f / (float)S;
-    const int* lines0 = a.lines + (size_t)first * L;
-    // coalesced gather of the L runs (and of their DoFs' colour masks, which
-    // decide below where each result goes)
+    // the chunk's run starts and run-element bits, then a coalesced gather
+    // of the L runs
+    {
+      const int* lines0 = a.lines + (size_t)first * L;
+      const uint32_t* bits = a.run_bits + (size_t)ch * a.bit_words;
+      for (int i = tid; i < L; i += blockDim.x) Ls[i] = __ldg(lines0 + i);
+      for (int i = tid; i < (L * S + 31) / 32; i += blockDim.x) Bs[i] = __ldg(bits + i);
+    }
+    __syncthreads();
     for (int idx = tid; idx < L * S; idx += blockDim.x) {
       const int l = __float2int_rz(((float)idx + 0.5f) * invS), kk = idx - l * S;
-      const int64_t g = (int64_t)__ldg(lines0 + l) + kk;
-      Xs[l * SM + kk] = __ldg(xr + g);
-      Ms[l * SM + kk] = __ldg(a.dof_mask + g);
+      Xs[l * SM + kk] = __ldg(xr + (int64_t)Ls[l] + kk);
     }
     __syncthreads();
     const bool act = c < nc;
@@ -229,12 +236,11 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
       if (cc == nc) v = Z[((nc - 1) * L + l) * N + P];
       else if (m == 0 && cc > 0) v = Z[((cc - 1) * L + l) * N + P] + Z[(cc * L + l) * N];
       else v = Z[(cc * L + l) * N + m];
-      const int64_t g = (int64_t)__ldg(lines0 + l) + kk;
-      const unsigned mk = Ms[l * SM + kk];
-      if (mk & (mk - 1u)) yc[g] = v;
+      const int64_t g = (int64_t)Ls[l] + kk;
+      if ((Bs[idx >> 5] >> (idx & 31)) & 1u) yc[g] = v;
       else yb[g] = v;
     }
-    __syncthreads();                          // Xs / Z are reused by the next chunk
+    __syncthreads();                          // Xs / Z / Ls / Bs are reused by the next chunk
   }
 }
 
@@ -323,7 +329,8 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   a.x = x;
   a.y = y;
   a.ycol = ycol;
-  a.dof_mask = ct.dof_mask;
+  a.run_bits = ct.run_bits;
+  a.bit_words = ct.bit_words;
   a.lines = dd.lines;
   a.face_start = dd.face_start;
   a.face_kind = dd.face_kind;

@@ -57,7 +57,8 @@ struct ChunkTable {
   int n = 0;
   int32_t* first = nullptr;      // [n + 1] first ordered cell of each chunk
   uint8_t* colour = nullptr;     // [n] colour of each chunk
-  uint8_t* dof_mask = nullptr;   // [n_dofs] bit c set if a chunk of colour c touches the DoF
+  uint32_t* run_bits = nullptr;  // [n][bit_words]: bit l*S + kk of chunk ch set if element kk
+  int bit_words = 0;             //   of its run l is a DoF that several colours touch
   int32_t* multi = nullptr;      // [nmulti] DoFs touched by two colours or more, ascending
   uint8_t* multi_mask = nullptr; // [nmulti] their colour masks
   int64_t nmulti = 0;
