@@ -2,8 +2,9 @@
 //
 // Cell-centric: every block owns CPB cells and writes their DoFs once (a DG
 // cell's DoFs belong to it alone), so there is a single launch, no colouring
-// and no atomics.  Per cell: the cell term (same sweeps as the CG kernel,
-// Algorithm 1), then its 2d faces in the order (k, s):
+// and no atomics.  Per cell: the cell term (Algorithm 1; 3D in the eigenbasis
+// of the 1D pencil, 2D by sweeps, as in the CG kernel), then its 2d faces in
+// the order (k, s):
 //  * interior face (neighbour active), Algorithm 2 from this cell's side:
 //      [u] = u_K1 - u_K2, {dn u} = (dn u_K1 + dn u_K2)/2 with n = +e_k, K1 the
 //      lower cell; the value test gets +T_v (K1) or -T_v (K2),
@@ -43,10 +44,11 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
   constexpr int L = DgShape<D, N>::L, ND = DgShape<D, N>::ND, CPB = DgShape<D, N>::CPB;
   using Pair2 = typename PairOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Pair2* AE = reinterpret_cast<Pair2*>(smem_raw);  // sweep pairs; their storage then holds the result
-  Pair2* BG = AE + CPB * ND;
-  T* X = reinterpret_cast<T*>(BG + CPB * ND);   // CPB tiles
-  T* A = reinterpret_cast<T*>(AE);             // result tile (after the sweeps)
+  // 3D: a scalar sweep tile (the eigenbasis phases run in place and leave the
+  // cell results there); 2D: a pair tile for the sweeps, then the results
+  T* A = reinterpret_cast<T*>(smem_raw);       // sweep tile, then the result tile
+  Pair2* AE = reinterpret_cast<Pair2*>(smem_raw);
+  T* X = A + (D == 3 ? 1 : 2) * CPB * ND;      // CPB input tiles
   T* T1 = X + CPB * ND;        // face scratch, CPB * L each
   T* T2 = T1 + CPB * L;
   T* U1 = T2 + CPB * L;
@@ -68,17 +70,26 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
   T* Xc = X + c * ND;
   T* R = A + c * ND;
   {
-    // cell term (Algorithm 1), then park the x-line result in R (A is free
-    // once every thread is past the sweeps)
+    // cell term (Algorithm 1), then the line result into R (node (j0, j1, j2)
+    // at j0 + n j1 + n^2 j2): 3D the z-line tl, back to the nodes its last
+    // phase read; 2D the x-line tl, once every thread is past the sweeps
     T out[N];
-    if (D == 3)
-      cell_sweeps_3d<T, N>(t, X, c * ND + (tl % N) + N * (tl / N), N * N, AE, BG, c, tl, act, out);
-    else
-      cell_sweeps_2d<T, N>(t, X, c * ND + tl, N, AE, c, tl, act, out);
-    __syncthreads();
-    if (act) {
+    if constexpr (D == 3) {
+      T sc[N];
 #pragma unroll
-      for (int m = 0; m < N; ++m) R[N * tl + m] = out[m];
+      for (int i = 0; i < N; ++i) sc[i] = (t.hlam[i] + t.hlam[tl % N]) + t.hlam[tl / N];
+      cell_fd_3d<T, N>(t, X, c * ND + tl, N * N, A, c, tl, act, sc, out);
+      if (act) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) R[tl + N * N * m] = out[m];
+      }
+    } else {
+      cell_sweeps_2d<T, N>(t, X, c * ND + tl, N, AE, c, tl, act, out);
+      __syncthreads();
+      if (act) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) R[N * tl + m] = out[m];
+      }
     }
   }
   __syncthreads();
@@ -240,7 +251,7 @@ static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x,
                         cudaStream_t st, Profiler* prof, int face_mode) {
   constexpr int L = DgShape<D, N>::L, ND = DgShape<D, N>::ND, CPB = DgShape<D, N>::CPB;
   const KTab<T> t = make_ktab<T>(hp);
-  const size_t smem = (size_t)(5 * CPB * ND + 6 * CPB * L) * sizeof(T);
+  const size_t smem = (size_t)(((D == 3) ? 2 : 3) * CPB * ND + 6 * CPB * L) * sizeof(T);
   cudaError_t err;
   if (smem > 48 * 1024) {
     err = cudaFuncSetAttribute(dg_apply_kernel<T, D, N>,

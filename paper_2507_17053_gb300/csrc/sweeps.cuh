@@ -4,12 +4,12 @@
 // Cell term.  With Gauss quadrature of n = p+1 points per axis the cell
 // integral of grad u . grad v is exact, so on a Cartesian cell
 //   A_K = h^(d-2) sum_k (M x ... x K_k x ... x M)
-// with the exact 1D mass M and stiffness K on [0,1].  It is evaluated with 7
-// one-dimensional sweeps in 3D (4 in 2D) instead of the 4d sweeps of
-// interpolate / differentiate / integrate:
-//   a = M_z u, e = K_z u;  b = M_y a, g = K_y a + M_y e;  y = h (K_x b + M_x g).
-// Each thread owns one line of the (p+1)^d tile per sweep (registers); the
-// tile is staged in shared memory between sweeps.
+// with the exact 1D mass M and stiffness K on [0,1], instead of the 4d
+// sweeps of interpolate / differentiate / integrate.  2D: 4 one-dimensional
+// sweeps, a = M_y u, e = K_y u;  y = K_x a + M_x e.  3D: the eigenbasis form
+// below (5 phases, 6 transforms per line).  Each thread owns one line of the
+// (p+1)^d tile per phase (registers); the tile is staged in shared memory
+// between phases.
 #pragma once
 
 #include "internal.hpp"
@@ -164,34 +164,6 @@ __device__ __forceinline__ void line_apply_sum(const T (&A1)[kMaxN][kMaxN], cons
   }
 }
 
-// b = M a, g = K a + M e (phase 2: the input a is folded once)
-template <typename T, int N>
-__device__ __forceinline__ void line_phase2(const KTab<T>& t, const T (&va)[N], const T (&ve)[N],
-                                            T (&b)[N], T (&g)[N]) {
-  if constexpr (UseFold<N>::value) {
-    LineFold<T, N> fa(va), fe(ve);
-    LineAcc<T, N> ab, ag;
-    ab.mac(t.fM, fa);
-    ag.mac(t.fK, fa);
-    ag.mac(t.fM, fe);
-    ab.unfold(b);
-    ag.unfold(g);
-  } else {
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-      T bb = T(0), gg = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        bb = fma(t.M[m][j], va[j], bb);
-        gg = fma(t.K[m][j], va[j], gg);
-        gg = fma(t.M[m][j], ve[j], gg);
-      }
-      b[m] = bb;
-      g[m] = gg;
-    }
-  }
-}
-
 // w = V^T v: the modes of a nodal line (even modes first); the folded input
 // feeds the even and the odd modes, and the output needs no unfolding.
 template <typename T, int N>
@@ -300,55 +272,6 @@ template <>
 struct PairOf<double> {
   using type = double2;
 };
-
-// 3D: three phases over z-, y- and x-lines.  The z-line (j0, j1) = line tl of
-// cell c is read from X[xb + xs * j2] (the caller's tile layout); AE and BG
-// hold per-cell pair tiles, and BG may be AE itself (a phase-2 thread
-// rewrites only the nodes of its own y-line, after reading them).  The
-// x-line result of line `tl` of cell `c` is returned in out[].
-template <typename T, int N>
-__device__ __forceinline__ void cell_sweeps_3d(const KTab<T>& t, const T* X, int xb, int xs,
-                                               typename PairOf<T>::type* AE,
-                                               typename PairOf<T>::type* BG, int c, int tl,
-                                               bool act, T (&out)[N]) {
-  using P2 = typename PairOf<T>::type;
-  constexpr int ND = N * N * N;
-  if (act) {
-    const int base = c * ND + (tl % N) + N * (tl / N);      // z-line (j0, j1)
-    T v[N], a[N], e[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = X[xb + xs * j];
-    line_apply2<T, N>(t.M, t.fM, t.K, t.fK, v, a, e);
-#pragma unroll
-    for (int m = 0; m < N; ++m) AE[base + N * N * m] = P2{a[m], e[m]};
-  }
-  __syncthreads();
-  if (act) {
-    const int base = c * ND + (tl % N) + N * N * (tl / N);  // y-line (j0, j2)
-    T va[N], ve[N], b[N], g[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const P2 p = AE[base + N * j];
-      va[j] = p.x;
-      ve[j] = p.y;
-    }
-    line_phase2<T, N>(t, va, ve, b, g);
-#pragma unroll
-    for (int m = 0; m < N; ++m) BG[base + N * m] = P2{b[m], g[m]};
-  }
-  __syncthreads();
-  if (act) {
-    const int base = c * ND + N * tl;                       // x-line (j1, j2) = line tl
-    T vb[N], vg[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      const P2 p = BG[base + j];
-      vb[j] = p.x;
-      vg[j] = p.y;
-    }
-    line_apply_sum<T, N>(t.Kh, t.fKh, vb, t.Mh, t.fMh, vg, out);
-  }
-}
 
 // 2D: y-lines then x-lines; the y-line j0 = tl of cell c is read from
 // X[xb + xs * j1].
