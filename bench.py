@@ -38,6 +38,10 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (CUDA cores) nominal dense rate
 # FMA = the nominal 1.25 TFLOP/s).  The FP64 apply is bound by this pipe.
 SMS, SM_MAX_MHZ, FP64_LANES_PER_SM_CLK = 152, 2070, 2
 FP64_PIPE_GOPS = SMS * SM_MAX_MHZ * 1e6 * FP64_LANES_PER_SM_CLK / 1e9
+# DRAM bytes (read + write) of one launch of the FP64 cell kernel, from one
+# ncu capture per (workload, tile shape) of the kernel as it stands
+# (profiles/apply_f64_sphere3d_q4_n96_kernels.md); other shapes: not captured
+CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 1): 158.541568e6 + 135.054592e6}
 L2_BYTES = 129 * 1024 * 1024
 REF_BUDGET_S = 90.0              # wall-clock budget of the --impl reference run
 
@@ -491,8 +495,9 @@ def run_ours(args, w):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_PIPE_GOPS,
                      "unit": "G FP64 ops/s", "frac": achieved_gops / FP64_PIPE_GOPS,
-                     "traffic": None,
-                     "kernel": f"cg_chunk_kernel<double,{w.dim},{w.degree + 1}> (cell kernel)",
+                     "traffic": CELL_TRAFFIC.get((w.name, shapes[0])),
+                     "kernel": f"cg_chunk_kernel<double,{w.dim},{w.degree + 1}> (cell kernel, "
+                               f"tile shape {shapes[0]})",
                      "ops_per_launch": cops, "fma_per_launch": cfma,
                      "other_per_launch": cadd,
                      "launches_per_step": 1, "kernel_ms_per_launch": cell_ms,
