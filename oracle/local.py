@@ -18,7 +18,10 @@ point on Gamma, in K's frame):
 i.e. I_value = -grad u.n~ + sigma E u tested against v, and I_grad = -E u
 tested against grad v . n~, with E u(x~_q) = u_K(x_q) evaluated from cell K's
 polynomial at the shifted point (exact point evaluation: the reading of the
-Taylor extension applied to the discrete polynomial).
+Taylor extension applied to the discrete polynomial).  The first-order
+variant truncates that series after the gradient term:
+    E1 psi_j(x~_q) = psi_j(xi~_q) + (1/h) d_q . grad_xi psi_j(xi~_q),
+d_q = x_q - x~_q (physical), in place of psi_j(xi_q).
 
 DG interior face between K1 (lower side along axis k) and K2, n = +e_k
 (Algorithm 2, Section 3.2, SIPG form):
@@ -75,16 +78,23 @@ def cell_matrix(nodes, gq, gw, d: int, h: float) -> np.ndarray:
     return h ** (d - 2) * A
 
 
-def face_matrices(nodes, xi_t, xi_s, w, k, s, h, sigma):
+def face_matrices(nodes, xi_t, xi_s, w, k, s, h, sigma, shift=None):
     """A_F for a batch of surrogate faces.
 
     xi_t [F, Q, d] face points, xi_s [F, Q, d] shifted points (cell frame),
     w [Q] tangential weights, k [F] normal axis, s [F] side (0 or 1).
+    The trial side is the extension E psi_j at x~_q (Section 2.1): with
+    shift = None the exact one, psi_j(x_q) (the whole Taylor series of the
+    polynomial); with shift = d [F, Q, d] (physical, d = x - x~) the
+    first-order truncation psi_j(x~_q) + d_q . grad psi_j(x~_q).
     Returns [F, nd, nd] (row = test i, column = trial j).
     """
     d = xi_t.shape[-1]
     Vt, Gt = tensor_values(nodes, xi_t)                  # [F, Q, nd], [F, Q, nd, d]
-    Vs, _ = tensor_values(nodes, xi_s)                   # [F, Q, nd]
+    if shift is None:
+        Vs, _ = tensor_values(nodes, xi_s)               # [F, Q, nd]
+    else:
+        Vs = Vt + np.einsum("fql,fqjl->fqj", shift, Gt) / h
     sign = (2.0 * s - 1.0)                               # outward normal +/- e_k
     Nt = np.take_along_axis(Gt, k[:, None, None, None], axis=3)[..., 0]
     Nt = Nt * (sign / h)[:, None, None]                  # dn psi at x~_q (physical)

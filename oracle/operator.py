@@ -13,6 +13,9 @@ Readings:
   local lexicographic order inside.
 * Penalties (the paper leaves the constants open): CG sigma = C p^2/h,
   DG surrogate sigma = C (p+1)^2/h, DG interior sigma_F = C_F (p+1)^2/h.
+* Extension operator E (Section 2.1): "exact" evaluates the cell polynomial
+  at the true-boundary point x_q (the whole Taylor series); "taylor1" keeps
+  the first-order term, u(x~_q) + d_q . grad u(x~_q).
 """
 from __future__ import annotations
 
@@ -28,7 +31,10 @@ _FACE_CACHE_BYTES = 1 << 30
 
 class Problem:
     def __init__(self, dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
-                 pen_interior=1.0):
+                 pen_interior=1.0, extension="exact"):
+        if extension not in ("exact", "taylor1"):
+            raise ValueError(f"unknown extension {extension!r}")
+        self.extension = extension
         self.d, self.p, self.N = dim, degree, cells
         self.n = degree + 1
         self.nd = self.n ** dim
@@ -51,7 +57,8 @@ class Problem:
     @classmethod
     def from_workload(cls, w):
         return cls(w.dim, w.degree, w.cells, w.kind, w.geom, dg=w.dg,
-                   pen_shift=w.pen_shift, pen_interior=w.pen_interior)
+                   pen_shift=w.pen_shift, pen_interior=w.pen_interior,
+                   extension=getattr(w, "extension", "exact"))
 
     # -- numbering -----------------------------------------------------------
     def _number_dofs(self):
@@ -85,9 +92,10 @@ class Problem:
     def face_matrices(self, sel=slice(None)):
         m = self.mesh
         f = m.sfaces[sel]
+        shift = m.face_shift[sel] if self.extension == "taylor1" else None
         return local.face_matrices(m.nodes, m.face_xi_t[sel], m.face_xi[sel],
                                    m.face_weights, f[:, 1], f[:, 2].astype(np.float64),
-                                   self.h, self.sigma)
+                                   self.h, self.sigma, shift=shift)
 
     def _face_chunks(self, chunk=1024):
         F = len(self.mesh.sfaces)

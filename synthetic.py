@@ -96,6 +96,7 @@ class Workload:
     pen_shift: float = 10.0         # sigma = C p^2/h (CG) or C (p+1)^2/h (DG)
     pen_interior: float = 1.0       # DG interior faces: C (p+1)^2/h
     nrhs: int = 1
+    extension: str = "exact"        # E u at x~: "exact" point evaluation, "taylor1"
 
     def resized(self, cells: int, degree: int | None = None) -> "Workload":
         return replace(self, cells=cells,
