@@ -78,7 +78,19 @@ typedef struct {
   double geom[16];      /* geometry parameters, see above */
   double pen_shift;     /* C in sigma = C p^2/h (CG) or C (p+1)^2/h (DG); paper leaves it open */
   double pen_interior;  /* C_F in sigma_F = C_F (p+1)^2/h (DG interior faces) */
+  int extension;        /* SBM_EXT_*: the extension operator E of the shifted terms */
 } sbm_desc;
+
+/*
+ * Extension operator E u_h(x~) on the surrogate boundary (Section 2.1, the
+ * Taylor expansion of u about x~ evaluated at the true-boundary point x):
+ *   SBM_EXT_EXACT   the whole series for the discrete polynomial: cell K's
+ *                   polynomial evaluated at x_q (O((p+1)^(2d-1)) per face);
+ *   SBM_EXT_TAYLOR1 truncated after the gradient term:
+ *                   u_h(x~_q) + d_q . grad u_h(x~_q), d_q = x_q - x~_q
+ *                   (sum-factorised, O(d (p+1)^d) per face; exact for affine u).
+ */
+enum { SBM_EXT_EXACT = 0, SBM_EXT_TAYLOR1 = 1 };
 
 typedef struct sbm_problem sbm_problem;
 

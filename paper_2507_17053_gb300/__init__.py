@@ -26,6 +26,7 @@ STATUS = {
     7: "SBM_ERR_STATE", 8: "SBM_ERR_UNSUPPORTED", 9: "SBM_ERR_GEOMETRY",
 }
 GEOM_KIND = {"ball": 0, "ellipsoid": 1, "torus": 2, "box": 3}
+EXTENSION = {"exact": 0, "taylor1": 1}
 
 
 class SbmError(RuntimeError):
@@ -44,6 +45,7 @@ class sbm_desc(ctypes.Structure):
         ("geom", ctypes.c_double * 16),
         ("pen_shift", ctypes.c_double),
         ("pen_interior", ctypes.c_double),
+        ("extension", ctypes.c_int),
     ]
 
 
@@ -159,7 +161,7 @@ def _stream(stream) -> int | None:
 
 
 def make_desc(dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
-              pen_interior=1.0) -> sbm_desc:
+              pen_interior=1.0, extension="exact") -> sbm_desc:
     d = sbm_desc()
     d.dim, d.degree, d.cells_per_side, d.dg = dim, degree, cells, int(bool(dg))
     d.geom_kind = GEOM_KIND[kind] if isinstance(kind, str) else int(kind)
@@ -169,6 +171,7 @@ def make_desc(dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
     for i, v in enumerate(g):
         d.geom[i] = float(v)
     d.pen_shift, d.pen_interior = float(pen_shift), float(pen_interior)
+    d.extension = EXTENSION[extension] if isinstance(extension, str) else int(extension)
     return d
 
 
@@ -367,8 +370,9 @@ class Problem:
     """Owning wrapper around an sbm_problem handle."""
 
     def __init__(self, dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
-                 pen_interior=1.0, device=True):
-        self.desc = make_desc(dim, degree, cells, kind, geom, dg, pen_shift, pen_interior)
+                 pen_interior=1.0, device=True, extension="exact"):
+        self.desc = make_desc(dim, degree, cells, kind, geom, dg, pen_shift, pen_interior,
+                              extension)
         self.dim, self.degree, self.dg = dim, degree, bool(dg)
         self.handle = sbm_create(self.desc)
         if device:
@@ -380,7 +384,8 @@ class Problem:
     @classmethod
     def from_workload(cls, w, device=True):
         return cls(w.dim, w.degree, w.cells, w.kind, w.geom, dg=w.dg, pen_shift=w.pen_shift,
-                   pen_interior=w.pen_interior, device=device)
+                   pen_interior=w.pen_interior, device=device,
+                   extension=getattr(w, "extension", "exact"))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -35,6 +35,7 @@ KTab<T> make_ktab(const HostProblem& hp) {
       t.Mh[i][j] = (T)(hd2 * tb.M[i][j]);
       t.Kh[i][j] = (T)(hd2 * tb.K[i][j]);
       t.S[i][j] = (T)tb.S[i][j];
+      t.Dg[i][j] = (T)tb.Dg[i][j];
     }
   for (int j = 0; j < n; ++j) {
     t.D0[j] = (T)tb.D0[j];
@@ -214,6 +215,10 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
       fcell.push_back((int32_t)i);
       for (int q = 0; q < L; ++q)
         for (int l = 0; l < d; ++l) {
+          if (hp.desc.extension == SBM_EXT_TAYLOR1) {   // the shift vector d_q
+            fphi.push_back(hp.face_d[(f * L + q) * d + l]);
+            continue;
+          }
           double phi[kMaxN];
           lagrange_values(hp.tab, hp.face_xi[(f * L + q) * d + l], phi);
           for (int jj = 0; jj < n; ++jj) fphi.push_back(phi[jj]);
@@ -477,6 +482,9 @@ static int check_face_mode(const sbm_problem* prob, int face_mode) {
     return fail(SBM_ERR_ARG, "unknown face mode");
   if (face_mode != SBM_FACE_FP32 && prob->hp.d != 3)
     return fail(SBM_ERR_UNSUPPORTED, "tensor-core face modes are built for 3D problems");
+  if (face_mode != SBM_FACE_FP32 && prob->hp.desc.extension != SBM_EXT_EXACT)
+    return fail(SBM_ERR_UNSUPPORTED,
+                "tensor-core face modes evaluate the exact extension's point evaluation");
   return SBM_OK;
 }
 

@@ -4,8 +4,10 @@
 // F of K of A_F[i,i], with (tensor-product closed form of the cell term)
 //   A_K[j,j] = h^(d-2) sum_k prod_l (l == k ? K[j_l][j_l] : M[j_l][j_l])
 // and, per face point q (same integrand as the apply, Algorithm 3),
-//   A_F[j,j] = sum_q W_q [ -psi_j(x~_q) dn psi_j(x~_q) - dn psi_j(x~_q) psi_j(x_q)
-//                          + sigma psi_j(x~_q) psi_j(x_q) ].
+//   A_F[j,j] = sum_q W_q [ -psi_j(x~_q) dn psi_j(x~_q) - dn psi_j(x~_q) E psi_j
+//                          + sigma psi_j(x~_q) E psi_j ],
+// E psi_j = psi_j(x_q) (exact extension) or psi_j(x~_q) + d_q . grad psi_j(x~_q)
+// (first-order Taylor).
 // CG: one launch per cell colour, plain read-modify-write (no atomics).
 // DG: one launch over all cells, plus the interior-face blocks' diagonals.
 #include "internal.hpp"
@@ -18,10 +20,10 @@ struct DiagArgs {
   const int32_t* __restrict__ cell_rank;   // ordered cell -> active-cell rank
   const int32_t* __restrict__ face_start;
   const int32_t* __restrict__ face_kind;
-  const double* __restrict__ face_phi;
+  const double* __restrict__ face_phi;      // 1D values at x_q, or the shifts d_q (Taylor)
   const int32_t* __restrict__ nbr;         // DG neighbours (null for CG)
   const int32_t* __restrict__ pos;         // CG: ordered positions of this colour's cells
-  int cell0, ncell, dg;
+  int cell0, ncell, dg, taylor;
   double sigma_f;                          // DG interior penalty
 };
 
@@ -50,9 +52,22 @@ __global__ void diag_f64_kernel(const DiagArgs a, const __grid_constant__ KTab<d
         const int qa = q % N, qb = q / N;
         double tang = t.S[qa][jj[ta]];
         if (D == 3) tang *= t.S[qb][jj[tb]];
-        const double* ph = a.face_phi + ((size_t)f * L + q) * D * N;
-        double shifted = 1.0;
-        for (int l = 0; l < D; ++l) shifted *= ph[l * N + jj[l]];
+        double shifted;
+        if (a.taylor) {
+          // psi_j(x~_q) + (1/h) d_q . grad_xi psi_j(x~_q)
+          const double* dq = a.face_phi + ((size_t)f * L + q) * D;
+          const double dnr = s ? t.D1[jj[k]] : t.D0[jj[k]];
+          const double ta_v = t.S[qa][jj[ta]], ta_d = t.Dg[qa][jj[ta]];
+          const double tb_v = (D == 3) ? t.S[qb][jj[tb]] : 1.0;
+          const double tb_d = (D == 3) ? t.Dg[qb][jj[tb]] : 0.0;
+          double g = dq[k] * dnr * ta_v * tb_v + dq[ta] * vn * ta_d * tb_v;
+          if (D == 3) g += dq[tb] * vn * ta_v * tb_d;
+          shifted = vn * ta_v * tb_v + t.h_inv * g;
+        } else {
+          const double* ph = a.face_phi + ((size_t)f * L + q) * D * N;
+          shifted = 1.0;
+          for (int l = 0; l < D; ++l) shifted *= ph[l * N + jj[l]];
+        }
         const double vt = vn * tang, dt = dn * tang;
         v += t.W[q] * (-vt * dt - dt * shifted + t.sigma * vt * shifted);
       }
@@ -114,6 +129,7 @@ static cudaError_t diag_t(const HostProblem& hp, const DeviceData& dd, double* d
     a.pos = hp.desc.dg ? nullptr : dd.diag_pos;
     a.ncell = n;
     a.dg = hp.desc.dg;
+    a.taylor = hp.desc.extension == SBM_EXT_TAYLOR1;
     a.sigma_f = hp.sigma_f;
     const int threads = ND < 128 ? ((ND + 31) / 32) * 32 : 128;
     diag_f64_kernel<D, N><<<n, threads, 0, st>>>(a, t);

@@ -7,7 +7,10 @@
 //  2. interpolation to the tangential Gauss points x~_q (sum factorisation);
 //  3. E u(x~_q) = u_K(x_q): point evaluation of the cell polynomial at the
 //     shifted point from the stored 1D values phi_j(xi_{q,l}) -- the
-//     O((p+1)^(2d-1)) step -- and the pointwise integrands
+//     O((p+1)^(2d-1)) step -- or, for the first-order Taylor extension,
+//     E u = u(x~_q) + d_q . grad u(x~_q) from the value and gradient traces
+//     (interpolated to x~_q like the normal derivative) and the stored shift
+//     d_q; then the pointwise integrands
 //       val_q = W_q (sigma E_q - dn u(x~_q)),  grd_q = -W_q E_q dn-scale;
 //  4. transposed interpolation back to the tangential nodes.
 // The face's contribution to its cell is then fully described by two
@@ -27,22 +30,29 @@ struct FaceArgs {
   const int32_t* __restrict__ cell_rank;   // DG gather
   const int32_t* __restrict__ face_cell;   // face -> ordered cell position
   const int32_t* __restrict__ face_kind;   // k | (s << 2)
-  const T* __restrict__ face_phi;          // [F][L][D][N]
+  const T* __restrict__ face_phi;          // [F][L][D][N], or the shifts [F][L][D] (Taylor)
   T* __restrict__ out;                     // [F][2L]
   int nface;
   int dg;
   int64_t ldx, ld_out;                     // right-hand side blockIdx.y offsets
 };
 
-template <typename T, int D, int N>
+// scratch arrays of L values per face: 6, or 9 with the Taylor extension
+template <int EXT>
+struct FaceScratch {
+  static constexpr int n = EXT ? 9 : 6;
+};
+
+template <typename T, int D, int N, int EXT>
 __global__ void __launch_bounds__(Shape<D, N>::CPB * Shape<D, N>::L)
 sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, FPB = Shape<D, N>::CPB;
+  constexpr int NS = FaceScratch<EXT>::n;
   const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
   T* __restrict__ outr = a.out + blockIdx.y * a.ld_out;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);
-  T* SC = X + FPB * ND;            // 6 L per face
+  T* SC = X + FPB * ND;            // NS L per face
   const int tid = threadIdx.x;
   const int f0 = blockIdx.x * FPB;
   const int nf = min(FPB, a.nface - f0);
@@ -61,13 +71,16 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
   const int kind = act ? __ldg(a.face_kind + f) : 0;
   const int k = kind & 3, s = kind >> 2;
   const T* Xf = X + fl * ND;
-  T* sc = SC + fl * 6 * L;
+  T* sc = SC + fl * NS * L;
   T* Td = sc;
   T* Da = sc + L;
   T* val = sc + 2 * L;
   T* grd = sc + 3 * L;
   T* Va = sc + 4 * L;
   T* Ga = sc + 5 * L;
+  T* Tv = sc + 6 * L;              // Taylor: value trace, then its two
+  T* VA = sc + 7 * L;              // first-direction interpolants (value,
+  T* VD = sc + 8 * L;              // derivative)
   int sk, sa, sb;
   if (D == 2) {
     sk = (k == 0) ? 1 : N;
@@ -82,39 +95,79 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
   const T sg = s ? T(1) : T(-1);
   const int bt = (tl % N) * sa + (D == 3 ? (tl / N) * sb : 0);
 
-  // 1. normal-derivative trace at the tangential nodes (the value trace u(x~_q)
-  //    does not enter the operator: only E u at the shifted point does)
+  // 1. normal-derivative trace at the tangential nodes (with the exact
+  //    extension the value trace u(x~_q) does not enter the operator: only
+  //    E u at the shifted point does; the Taylor extension needs it)
   if (act) {
     T dsum = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) dsum = fma(s ? t.D1[j] : t.D0[j], Xf[j * sk + bt], dsum);
     Td[tl] = dsum;
+    if (EXT) Tv[tl] = Xf[kend * sk + bt];
   }
   __syncthreads();
-  // 2. to the tangential Gauss points
-  T dg = T(0);
+  // 2. to the tangential Gauss points (Taylor: also the value and its
+  //    derivatives along the tangential axes ta, tb -- axis ta is the one
+  //    of stride sa, interpolated first)
+  T dg = T(0), uv = T(0), da = T(0), db = T(0);
   if (D == 3) {
     if (act) {
       const int qa = tl % N, jb = tl / N;
-      T dv = T(0);
+      T dv = T(0), va = T(0), vd = T(0);
 #pragma unroll
-      for (int j = 0; j < N; ++j) dv = fma(t.S[qa][j], Td[j + N * jb], dv);
+      for (int j = 0; j < N; ++j) {
+        dv = fma(t.S[qa][j], Td[j + N * jb], dv);
+        if (EXT) {
+          va = fma(t.S[qa][j], Tv[j + N * jb], va);
+          vd = fma(t.Dg[qa][j], Tv[j + N * jb], vd);
+        }
+      }
       Da[tl] = dv;
+      if (EXT) {
+        VA[tl] = va;
+        VD[tl] = vd;
+      }
     }
     __syncthreads();
     if (act) {
       const int qa = tl % N, qb = tl / N;
 #pragma unroll
-      for (int j = 0; j < N; ++j) dg = fma(t.S[qb][j], Da[qa + N * j], dg);
+      for (int j = 0; j < N; ++j) {
+        dg = fma(t.S[qb][j], Da[qa + N * j], dg);
+        if (EXT) {
+          uv = fma(t.S[qb][j], VA[qa + N * j], uv);
+          da = fma(t.S[qb][j], VD[qa + N * j], da);
+          db = fma(t.Dg[qb][j], VA[qa + N * j], db);
+        }
+      }
     }
   } else {
     if (act) {
 #pragma unroll
-      for (int j = 0; j < N; ++j) dg = fma(t.S[tl][j], Td[j], dg);
+      for (int j = 0; j < N; ++j) {
+        dg = fma(t.S[tl][j], Td[j], dg);
+        if (EXT) {
+          uv = fma(t.S[tl][j], Tv[j], uv);
+          da = fma(t.Dg[tl][j], Tv[j], da);
+        }
+      }
     }
   }
-  // 3. point evaluation at the shifted point, pointwise integrands
-  if (act) {
+  // 3. the extension at x~_q, pointwise integrands
+  if (act && EXT) {
+    // E u = u + d . grad u, grad = (1/h) reference gradient; reference
+    // derivatives: along k dg, along ta da, along tb db
+    const T* dq = a.face_phi + ((size_t)f * L + tl) * D;
+    const int ta = (D == 2) ? 1 - k : (k == 0 ? 1 : 0);
+    const int tb = (k == 2) ? 1 : 2;
+    T g = fma(__ldg(dq + k), dg, __ldg(dq + ta) * da);
+    if (D == 3) g = fma(__ldg(dq + tb), db, g);
+    const T e = fma(t.h_inv, g, uv);
+    const T W = t.W[tl];
+    val[tl] = W * (t.sigma * e - sg * t.h_inv * dg);
+    grd[tl] = -W * e * sg * t.h_inv;
+  }
+  if (act && !EXT) {
     const T* pq = a.face_phi + ((size_t)f * L + tl) * D * N;
     T p0[N], p1[N];
 #pragma unroll
@@ -191,7 +244,7 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
   }
 }
 
-template <typename T, int D, int N>
+template <typename T, int D, int N, int EXT>
 static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
                           cudaStream_t st, int64_t ldx = 0, int nrhs = 1) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, FPB = Shape<D, N>::CPB;
@@ -209,16 +262,24 @@ static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* 
   a.dg = hp.desc.dg;
   a.ldx = ldx;
   a.ld_out = (int64_t)dd.nface * 2 * L;
-  const size_t smem = (size_t)(FPB * ND + FPB * 6 * L) * sizeof(T);
-  sface_kernel<T, D, N><<<dim3((dd.nface + FPB - 1) / FPB, nrhs), FPB * L, smem, st>>>(a, t);
+  const size_t smem = (size_t)(FPB * ND + FPB * FaceScratch<EXT>::n * L) * sizeof(T);
+  sface_kernel<T, D, N, EXT><<<dim3((dd.nface + FPB - 1) / FPB, nrhs), FPB * L, smem, st>>>(a, t);
   return cudaGetLastError();
+}
+
+template <typename T, int D, int N>
+static cudaError_t face_x(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
+                          cudaStream_t st, int64_t ldx = 0, int nrhs = 1) {
+  return hp.desc.extension == SBM_EXT_TAYLOR1
+             ? face_t<T, D, N, 1>(hp, dd, x, out, st, ldx, nrhs)
+             : face_t<T, D, N, 0>(hp, dd, x, out, st, ldx, nrhs);
 }
 
 template <typename T>
 cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
                                cudaStream_t st) {
 #define SBM_CASE(DD, NN) \
-  if (hp.d == DD && hp.n == NN) return face_t<T, DD, NN>(hp, dd, x, out, st);
+  if (hp.d == DD && hp.n == NN) return face_x<T, DD, NN>(hp, dd, x, out, st);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE
@@ -231,7 +292,7 @@ template <typename T>
 cudaError_t launch_face_kernel_multi(const HostProblem& hp, const DeviceData& dd, const T* x,
                                      int64_t ldx, int nrhs, T* out, cudaStream_t st) {
 #define SBM_CASE(DD, NN) \
-  if (hp.d == DD && hp.n == NN) return face_t<T, DD, NN>(hp, dd, x, out, st, ldx, nrhs);
+  if (hp.d == DD && hp.n == NN) return face_x<T, DD, NN>(hp, dd, x, out, st, ldx, nrhs);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE

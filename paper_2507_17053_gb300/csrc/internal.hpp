@@ -36,6 +36,7 @@ struct KTab {
   T Mh[kMaxN][kMaxN];    // h^(d-2) * M   (last sweep of the cell operator)
   T Kh[kMaxN][kMaxN];    // h^(d-2) * K
   T S[kMaxN][kMaxN];     // S[q][j] = phi_j(g_q)
+  T Dg[kMaxN][kMaxN];    // Dg[q][j] = phi_j'(g_q)
   T D0[kMaxN];           // phi_j'(0)
   T D1[kMaxN];           // phi_j'(1)
   T W[kMaxN * kMaxN];    // face weights h^(d-1) w_qa w_qb (tangential Gauss index q)
@@ -87,7 +88,9 @@ struct DeviceData {
   std::vector<int> diag_col_start;
   double* ycol = nullptr;        // CG [ncolours * n_dofs] colour accumulation buffers (scratch)
   float* ycol32 = nullptr;
-  double* face_phi = nullptr;    // [F * Q * d * n] phi_j(xi_{q,l}) at the shifted points
+  // per surrogate-face point: exact extension: [F * Q * d * n] phi_j(xi_{q,l})
+  // at the shifted point; first-order Taylor: [F * Q * d] the shift d_q
+  double* face_phi = nullptr;
   float* face_phi32 = nullptr;   // the same table rounded to FP32
   int32_t* nbr = nullptr;        // DG [Nc * 2d] neighbour rank per (k, s), -1 = surrogate
   double* stage_x = nullptr;     // host-apply staging buffers (allocated on first use)

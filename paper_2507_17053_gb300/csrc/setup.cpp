@@ -469,6 +469,10 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
   if (N < 1 || N > 4096) { *err = "cells_per_side must be in 1..4096"; return SBM_ERR_ARG; }
   if (!(desc.pen_shift > 0)) { *err = "pen_shift must be > 0"; return SBM_ERR_ARG; }
   if (desc.dg && !(desc.pen_interior > 0)) { *err = "pen_interior must be > 0"; return SBM_ERR_ARG; }
+  if (desc.extension != SBM_EXT_EXACT && desc.extension != SBM_EXT_TAYLOR1) {
+    *err = "unknown extension operator";
+    return SBM_ERR_ARG;
+  }
   int st = P.ls.init(desc.geom_kind, d, desc.geom, err);
   if (st != SBM_OK) return st;
   P.d = d; P.p = p; P.n = p + 1; P.N = N;
@@ -537,6 +541,7 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
   const int Q = P.L, n = P.n;
   P.face_x.assign(F * Q * d, 0.0);
   P.face_xi.assign(F * Q * d, 0.0);
+  P.face_d.assign(F * Q * d, 0.0);
   for (int64_t f = 0; f < F; ++f) {
     const int c = P.sfaces[3 * f], k = P.sfaces[3 * f + 1], s = P.sfaces[3 * f + 2];
     int tang[2], nt = 0;
@@ -557,6 +562,7 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
       for (int l = 0; l < d; ++l) {
         P.face_x[(f * Q + q) * d + l] = xq[l];
         P.face_xi[(f * Q + q) * d + l] = (xq[l] - lo[l]) / h;
+        P.face_d[(f * Q + q) * d + l] = xq[l] - xt[l];
       }
     }
   }

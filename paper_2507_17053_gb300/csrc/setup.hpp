@@ -73,6 +73,7 @@ struct HostProblem {
   std::vector<int32_t> sfaces;      // [F * 3]
   std::vector<double> face_x;       // [F * L * d] closest points
   std::vector<double> face_xi;      // [F * L * d] reference coordinates in the cell's frame
+  std::vector<double> face_d;       // [F * L * d] shift d = x_q - x~_q (physical)
   // DG interior faces (K1 rank, k, K2 rank), K2 = K1 + e_k
   std::vector<int32_t> ifaces;
 

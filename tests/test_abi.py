@@ -37,6 +37,7 @@ def test_error_strings(lib):
     (dict(geom=(0.0, 0.0, -1.0)), "SBM_ERR_ARG"),
     (dict(geom=(5.0, 5.0, 0.1)), "SBM_ERR_EMPTY_DOMAIN"),
     (dict(pen_shift=0.0), "SBM_ERR_ARG"),
+    (dict(extension=2), "SBM_ERR_ARG"),
 ])
 def test_create_rejects_bad_descriptions(bad, code):
     args = dict(dim=2, degree=2, cells=8, kind="ball", geom=(0.0, 0.0, 0.7))
