@@ -372,6 +372,64 @@ def other_workloads(G, torch, steps=40):
     return out
 
 
+def extension_study(G, torch, steps=40):
+    """First-order Taylor extension against the exact one (the survey's
+    "next" row 1): throughput of the FP64 / FP32 applies and their face phase
+    on the 3D Q4 sphere (96^3), and accuracy on the 2D disk with
+    u = sin(pi x) sin(pi y): max nodal error |u_h - I u| / |I u| of the
+    solution (BiCGStab, else GMRES(300), to 1e-10) for p = 1, 2, 3 and
+    N = 16, 32, 64, with the observed rates (None: no solver converged)."""
+    import dataclasses
+    out = {"throughput": {}, "accuracy": {}}
+    for ext in ("exact", "taylor1"):
+        w = dataclasses.replace(S.SPHERE_3D_Q4, extension=ext)
+        P = G.Problem.from_workload(w)
+        G.sbm_autotune(P.handle)
+        x = torch.from_numpy(S.random_vector(w.seed, P.n_dofs, w.dist)).cuda()
+        res = {}
+        for name, xx in (("f64", x), ("f32", x.float())):
+            yy = torch.empty_like(xx)
+            fn = (lambda a, b: P.apply_f64(a, b)) if name == "f64" else \
+                 (lambda a, b: P.apply_f32(a, b))
+            for _ in range(3):
+                fn(xx, yy)
+            torch.cuda.synchronize()
+            G.sbm_profile_enable(P.handle, True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                fn(xx, yy)
+            e1.record()
+            torch.cuda.synchronize()
+            phases, _ = G.sbm_profile_read(P.handle)
+            G.sbm_profile_enable(P.handle, False)
+            ms = e0.elapsed_time(e1) / steps
+            res[name] = {"gdofs": P.n_dofs / ms / 1e6, "ms": ms,
+                         "face_ms": phases[0] / steps}
+        out["throughput"][ext] = res
+    for p in (1, 2, 3):
+        for ext in ("exact", "taylor1"):
+            errs = []
+            for N in (16, 32, 64):
+                w = dataclasses.replace(S.DISK_2D_Q2.resized(N, degree=p), extension=ext)
+                P = G.Problem.from_workload(w)
+                b = torch.from_numpy(P.rhs(0)).cuda()
+                u = torch.from_numpy(P.interpolate(0)).cuda()
+                xs = torch.zeros_like(b)
+                _, rr, ok = G.sbm_bicgstab(P.handle, b, xs, rtol=1e-10, maxit=20000)
+                if not ok:                      # BiCGStab stalls: GMRES(300)
+                    xs.zero_()
+                    _, rr, ok = G.sbm_gmres(P.handle, b, xs, rtol=1e-10, maxit=30000,
+                                            restart=300)
+                errs.append(float((xs - u).abs().max() / u.abs().max()) if ok else None)
+            rates = [None if (e0 is None or e1 is None) else float(np.log2(e0 / e1))
+                     for e0, e1 in zip(errs[:-1], errs[1:])]
+            out["accuracy"][f"p{p}_{ext}"] = {"N": [16, 32, 64], "max_nodal_rel_err": errs,
+                                             "rates": rates}
+    return out
+
+
 def batched(G, torch, steps=10):
     """64 rotated-ellipsoid CG problems (N ~ U{16..48}, p ~ U{2..6}), 8
     right-hand sides each, one CUDA-graph launch per batched apply."""
@@ -522,7 +580,7 @@ def run_ours(args, w):
     }
     if not args.skip_extras:
         for key, fn in (("solves", solve_times), ("other_workloads", other_workloads),
-                        ("batched_64x8", batched)):
+                        ("batched_64x8", batched), ("extension_taylor1", extension_study)):
             try:
                 line[key] = fn(G, torch)
             except Exception as e:  # noqa: BLE001 -- report, never hide the main number
