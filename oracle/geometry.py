@@ -15,7 +15,14 @@ Readings taken where the paper leaves a choice open:
 * ellipsoid closest point: root of the Lagrange-multiplier equation
   sum_i (a_i y_i / (a_i^2 + t))^2 = 1 found by plain bisection (the paper
   says only that a Newton solve is used; any convergent root finder reaches
-  the same point).
+  the same point);
+* union of balls (the multiple-ball benchmark of Section 4.3): phi =
+  min_i (|x - c_i| - r_i); the closest point on the union's boundary is the
+  nearest of the candidates that lie on it -- the projection onto each
+  sphere, the nearest point of each pairwise intersection circle (3D), and
+  the vertices where three spheres (3D) or two circles (2D) meet -- a
+  candidate lying strictly inside another ball being discarded; ties go to
+  the first candidate in that order.
 Formulas are written with an explicit, fixed summation order so that the
 integer decisions (active or not) are reproducible.
 """
@@ -45,6 +52,10 @@ class LevelSet:
             self.Rmaj, self.rmin = g[0], g[1]
         elif kind == "box":
             self.c, self.half = g[:d], g[d:2 * d]
+        elif kind == "balls":
+            B = g.reshape(-1, d + 1)
+            self.bc, self.br = B[:, :d].copy(), B[:, d].copy()
+            self._balls_setup()
         else:
             raise ValueError(kind)
 
@@ -83,6 +94,12 @@ class LevelSet:
             for i in range(1, d):
                 m = np.maximum(m, np.abs(x[..., i] - self.c[i]) - self.half[i])
             return m
+        if self.kind == "balls":
+            m = None
+            for b in range(len(self.br)):
+                v = _dist(x, self.bc[b]) - self.br[b]
+                m = v if m is None else np.minimum(m, v)
+            return m
         raise AssertionError
 
     # -- closest point on Gamma ------------------------------------------------
@@ -102,7 +119,77 @@ class LevelSet:
             return self._box_closest(x)
         if self.kind == "ellipsoid":
             return self._ellipsoid_closest(x)
+        if self.kind == "balls":
+            return self._balls_closest(x)
         raise AssertionError
+
+    # -- union of balls ----------------------------------------------------------
+    def _outside_others(self, p, skip):
+        """p lies on the union's boundary side of every ball not in skip:
+        |p - c_l| >= r_l."""
+        ok = np.ones(p.shape[:-1], dtype=bool)
+        for l in range(len(self.br)):
+            if l not in skip:
+                ok &= _dist(p, self.bc[l]) >= self.br[l]
+        return ok
+
+    def _balls_setup(self):
+        """Pairwise intersection circles (3D) and boundary vertices."""
+        d, C, R = self.dim, self.bc, self.br
+        nb = len(R)
+        self.circles = []                       # (i, j, m, u, rho)
+        verts = []                              # (point, defining balls)
+        for i in range(nb):
+            for j in range(i + 1, nb):
+                dv = C[j] - C[i]
+                D = _norm(dv)
+                if not (D < R[i] + R[j] and D > abs(R[i] - R[j])):
+                    continue
+                u = dv / D
+                a = (D * D + R[i] * R[i] - R[j] * R[j]) / (2.0 * D)
+                m = C[i] + a * u
+                rho = np.sqrt(R[i] * R[i] - a * a)
+                if d == 3:
+                    self.circles.append((i, j, m, u, rho))
+                else:
+                    perp = np.array([-u[1], u[0]])
+                    for sg in (1.0, -1.0):
+                        verts.append((m + sg * rho * perp, (i, j)))
+        if d == 3:
+            for i in range(nb):
+                for j in range(i + 1, nb):
+                    for k in range(j + 1, nb):
+                        for p in _three_spheres(C[i], R[i], C[j], R[j], C[k], R[k]):
+                            verts.append((p, (i, j, k)))
+        self.vertices = [p for p, s in verts if self._outside_others(p, s)]
+
+    def _balls_closest(self, x):
+        best = np.full(x.shape[:-1], np.inf)
+        out = np.full(x.shape, np.nan)
+
+        def take(p, ok):
+            d2 = _dist2(p, x)
+            upd = ok & (d2 < best)
+            best[upd] = d2[upd]
+            out[upd] = p[upd]
+
+        for i in range(len(self.br)):            # projections onto each sphere
+            v = x - self.bc[i]
+            s = _norm(v)
+            with np.errstate(invalid="ignore", divide="ignore"):
+                p = self.bc[i] + self.br[i] * v / s[..., None]
+            take(p, (s > 0) & self._outside_others(p, (i,)))
+        for i, j, m, u, rho in self.circles:     # nearest points of the circles
+            w = x - m
+            t = w[..., 0] * u[0] + w[..., 1] * u[1] + w[..., 2] * u[2]
+            wp = w - t[..., None] * u
+            s = _norm(wp)
+            with np.errstate(invalid="ignore", divide="ignore"):
+                p = m + rho * wp / s[..., None]
+            take(p, (s > 0) & self._outside_others(p, (i, j)))
+        for p in self.vertices:                  # vertices
+            take(np.broadcast_to(p, x.shape), np.ones(x.shape[:-1], dtype=bool))
+        return out
 
     def _box_closest(self, x):
         v = x - self.c
@@ -148,6 +235,50 @@ class LevelSet:
                 acc = acc + self.R[i, j] * z[..., j]
             out[..., i] = self.c[i] + acc
         return out
+
+
+def _norm(v):
+    s = np.zeros(np.shape(v)[:-1])
+    for l in range(np.shape(v)[-1]):
+        s = s + v[..., l] * v[..., l]
+    return np.sqrt(s)
+
+
+def _dist(x, c):
+    return _norm(x - c)
+
+
+def _dist2(p, x):
+    s = np.zeros(np.shape(x)[:-1])
+    for l in range(np.shape(x)[-1]):
+        s = s + (p[..., l] - x[..., l]) * (p[..., l] - x[..., l])
+    return s
+
+
+def _three_spheres(c1, r1, c2, r2, c3, r3):
+    """The 0 or 2 points common to three spheres (trilateration in the frame
+    e_x along c2 - c1, e_y in the plane of the centres)."""
+    dv = c2 - c1
+    D = _norm(dv)
+    ex = dv / D
+    w = c3 - c1
+    i = ex[0] * w[0] + ex[1] * w[1] + ex[2] * w[2]
+    ey = w - i * ex
+    ny = _norm(ey)
+    if not ny > 1e-12 * D:
+        return []                               # centres on one line
+    ey = ey / ny
+    ez = np.array([ex[1] * ey[2] - ex[2] * ey[1], ex[2] * ey[0] - ex[0] * ey[2],
+                   ex[0] * ey[1] - ex[1] * ey[0]])
+    j = ey[0] * w[0] + ey[1] * w[1] + ey[2] * w[2]
+    X = (r1 * r1 - r2 * r2 + D * D) / (2.0 * D)
+    Y = (r1 * r1 - r3 * r3 + i * i + j * j) / (2.0 * j) - (i / j) * X
+    z2 = r1 * r1 - X * X - Y * Y
+    if not z2 > 0:
+        return []
+    Z = np.sqrt(z2)
+    base = c1 + X * ex + Y * ey
+    return [base + Z * ez, base - Z * ez]
 
 
 class Mesh:

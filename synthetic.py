@@ -70,7 +70,7 @@ def random_vector(seed: int, n: int, dist: str) -> np.ndarray:
 # Workload descriptions
 # --------------------------------------------------------------------------
 
-BALL, ELLIPSOID, TORUS, BOX = "ball", "ellipsoid", "torus", "box"
+BALL, ELLIPSOID, TORUS, BOX, BALLS = "ball", "ellipsoid", "torus", "box", "balls"
 
 
 @dataclass(frozen=True)
@@ -83,6 +83,7 @@ class Workload:
                  with x = R y, y in the ellipsoid's own frame), centre (d values)
       torus:     major radius R, minor radius r (axis z, centred at 0; d = 3)
       box:       centre (d values), half-widths (d values)
+      balls:     union of balls: per ball its centre (d values) and radius
     """
     name: str
     dim: int
@@ -184,3 +185,32 @@ def batched_ellipsoids(nprob: int = 64, nrhs: int = 8, seed: int = BATCH_SEED,
 def rhs_seed(w: Workload, r: int) -> int:
     """Seed of right-hand side r of a workload (r = 0 is the workload's own seed)."""
     return w.seed + r
+
+
+MULTIBALL_SEED = 5
+
+
+def multiple_balls(nballs: int, dim: int = 3, cells: int = 64, degree: int = 3,
+                   seed: int = MULTIBALL_SEED) -> Workload:
+    """The multiple-ball geometric-complexity workload: the union of nballs
+    random balls in [-1, 1]^dim (the paper's placements are not published).
+
+    Geometry stream ``seed * 1000003 + nballs`` (uniforms, dim + 1 per ball):
+    radius r_i = r0 (0.7 + 0.3 u_0) with r0 = 0.55 (3 / nballs)^(2/3): from
+    three large balls to many small ones, whose boundary cells make up about
+    half of the cut-or-active cells at 25 balls (the paper's range); centre
+    coordinates uniform in [-1 + r_i + 2h, 1 - r_i - 2h] (h = 2 / cells), so
+    every ball stays inside the box.  CG, x ~ U(-1, 1) from stream
+    ``seed * 1000003 + nballs + 1000``.
+    """
+    per = dim + 1
+    u = uniform01(seed * 1000003 + nballs, nballs * per).reshape(nballs, per)
+    h = 2.0 / cells
+    r0 = 0.55 * (3.0 / nballs) ** (2.0 / 3.0)
+    geom = []
+    for i in range(nballs):
+        r = r0 * (0.7 + 0.3 * u[i, 0])
+        lim = 1.0 - r - 2.0 * h
+        geom += [-lim + 2.0 * lim * u[i, 1 + l] for l in range(dim)] + [r]
+    return _wl(f"balls{nballs}_{dim}d_cg_q{degree}_n{cells}", dim, degree, cells,
+               (BALLS, tuple(geom)), seed=seed * 1000003 + nballs + 1000)
