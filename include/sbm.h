@@ -53,7 +53,13 @@ enum {
 };
 
 /* ---- problem description ------------------------------------------------ */
-enum { SBM_GEOM_BALL = 0, SBM_GEOM_ELLIPSOID = 1, SBM_GEOM_TORUS = 2, SBM_GEOM_BOX = 3 };
+enum {
+  SBM_GEOM_BALL = 0,
+  SBM_GEOM_ELLIPSOID = 1,
+  SBM_GEOM_TORUS = 2,
+  SBM_GEOM_BOX = 3,
+  SBM_GEOM_BALLS = 4
+};
 
 /*
  * Geometry parameters (geom[]), d = dim:
@@ -64,6 +70,15 @@ enum { SBM_GEOM_BALL = 0, SBM_GEOM_ELLIPSOID = 1, SBM_GEOM_TORUS = 2, SBM_GEOM_B
  *   TORUS     : major radius R, minor radius r (d = 3, axis z, centred at 0)
  *                                                     phi = (sqrt(x^2+y^2)-R)^2 + z^2 - r^2
  *   BOX       : centre c[d], half-widths b[d]        phi = max_i |x_i - c_i| - b_i
+ *   BALLS     : the union of nballs balls given in balls[] (not geom[]), the
+ *               multiple-ball benchmark of Section 4.3
+ *                                                     phi = min_i |x - c_i| - r_i
+ *               closest point on the union's boundary: the nearest of the
+ *               projections onto each sphere, the nearest points of the
+ *               pairwise intersection circles (3D) and the vertices where
+ *               three spheres (3D) or two circles (2D) meet, keeping only
+ *               candidates not strictly inside another ball; ties go to the
+ *               first candidate in that order.
  * A background cell is active iff phi(cell centre) < 0 (strictly).
  * Penalties: CG sigma = pen_shift * p^2 / h; DG surrogate faces
  * sigma = pen_shift * (p+1)^2 / h and interior faces
@@ -79,6 +94,8 @@ typedef struct {
   double pen_shift;     /* C in sigma = C p^2/h (CG) or C (p+1)^2/h (DG); paper leaves it open */
   double pen_interior;  /* C_F in sigma_F = C_F (p+1)^2/h (DG interior faces) */
   int extension;        /* SBM_EXT_*: the extension operator E of the shifted terms */
+  int nballs;           /* SBM_GEOM_BALLS: number of balls (geom[] unused) */
+  const double* balls;  /* SBM_GEOM_BALLS: host [nballs][dim + 1] centre, radius; copied */
 } sbm_desc;
 
 /*

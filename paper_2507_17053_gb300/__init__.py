@@ -25,7 +25,7 @@ STATUS = {
     4: "SBM_ERR_EMPTY_DOMAIN", 5: "SBM_ERR_NOT_CONVERGED", 6: "SBM_ERR_TIMEOUT",
     7: "SBM_ERR_STATE", 8: "SBM_ERR_UNSUPPORTED", 9: "SBM_ERR_GEOMETRY",
 }
-GEOM_KIND = {"ball": 0, "ellipsoid": 1, "torus": 2, "box": 3}
+GEOM_KIND = {"ball": 0, "ellipsoid": 1, "torus": 2, "box": 3, "balls": 4}
 EXTENSION = {"exact": 0, "taylor1": 1}
 
 
@@ -46,6 +46,8 @@ class sbm_desc(ctypes.Structure):
         ("pen_shift", ctypes.c_double),
         ("pen_interior", ctypes.c_double),
         ("extension", ctypes.c_int),
+        ("nballs", ctypes.c_int),
+        ("balls", ctypes.c_void_p),
     ]
 
 
@@ -166,6 +168,13 @@ def make_desc(dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
     d.dim, d.degree, d.cells_per_side, d.dg = dim, degree, cells, int(bool(dg))
     d.geom_kind = GEOM_KIND[kind] if isinstance(kind, str) else int(kind)
     g = list(geom)
+    if d.geom_kind == GEOM_KIND["balls"]:
+        # the balls travel in a separate host array (kept alive with the desc)
+        arr = (ctypes.c_double * len(g))(*[float(v) for v in g])
+        d._balls_ref = arr
+        d.nballs = len(g) // (dim + 1)
+        d.balls = ctypes.cast(arr, ctypes.c_void_p)
+        g = []
     if len(g) > 16:
         raise ValueError("at most 16 geometry parameters")
     for i, v in enumerate(g):

@@ -317,8 +317,170 @@ int LevelSet::init(int k, int d, const double* g, std::string* err) {
   return SBM_ERR_ARG;
 }
 
+// ---- union of balls ----------------------------------------------------------
+// The same formulas, in the same operation order, as the oracle's, so that the
+// two geometries agree to the last bit.
+
+static double norm_d(const double* v, int d) {
+  double s = 0.0;
+  for (int l = 0; l < d; ++l) s = s + v[l] * v[l];
+  return std::sqrt(s);
+}
+
+static double dist_d(const double* x, const double* c, int d) {
+  double v[3];
+  for (int l = 0; l < d; ++l) v[l] = x[l] - c[l];
+  return norm_d(v, d);
+}
+
+// p is not strictly inside any ball other than those in skip[0..ns)
+static bool outside_others(const LevelSet& ls, const double* p, const int* skip, int ns) {
+  const int nb = (int)ls.br.size();
+  for (int l = 0; l < nb; ++l) {
+    bool sk = false;
+    for (int q = 0; q < ns; ++q) sk = sk || (skip[q] == l);
+    if (!sk && !(dist_d(p, &ls.bc[3 * l], ls.dim) >= ls.br[l])) return false;
+  }
+  return true;
+}
+
+// the 0 or 2 points common to three spheres (trilateration)
+static int three_spheres(const double* c1, double r1, const double* c2, double r2,
+                         const double* c3, double r3, double out[2][3]) {
+  double dv[3], ex[3], w[3], ey[3], ez[3];
+  for (int l = 0; l < 3; ++l) dv[l] = c2[l] - c1[l];
+  const double D = norm_d(dv, 3);
+  for (int l = 0; l < 3; ++l) ex[l] = dv[l] / D;
+  for (int l = 0; l < 3; ++l) w[l] = c3[l] - c1[l];
+  const double i = ex[0] * w[0] + ex[1] * w[1] + ex[2] * w[2];
+  for (int l = 0; l < 3; ++l) ey[l] = w[l] - i * ex[l];
+  const double ny = norm_d(ey, 3);
+  if (!(ny > 1e-12 * D)) return 0;
+  for (int l = 0; l < 3; ++l) ey[l] = ey[l] / ny;
+  ez[0] = ex[1] * ey[2] - ex[2] * ey[1];
+  ez[1] = ex[2] * ey[0] - ex[0] * ey[2];
+  ez[2] = ex[0] * ey[1] - ex[1] * ey[0];
+  const double j = ey[0] * w[0] + ey[1] * w[1] + ey[2] * w[2];
+  const double X = (r1 * r1 - r2 * r2 + D * D) / (2.0 * D);
+  const double Y = (r1 * r1 - r3 * r3 + i * i + j * j) / (2.0 * j) - (i / j) * X;
+  const double z2 = r1 * r1 - X * X - Y * Y;
+  if (!(z2 > 0)) return 0;
+  const double Z = std::sqrt(z2);
+  for (int l = 0; l < 3; ++l) {
+    const double base = c1[l] + X * ex[l] + Y * ey[l];
+    out[0][l] = base + Z * ez[l];
+    out[1][l] = base - Z * ez[l];
+  }
+  return 2;
+}
+
+int LevelSet::init_balls(int d, int nb, const double* b, std::string* err) {
+  kind = SBM_GEOM_BALLS;
+  dim = d;
+  if (nb < 1 || !b) { *err = "balls: nballs >= 1 and a balls array are needed"; return SBM_ERR_ARG; }
+  bc.assign(3 * (size_t)nb, 0.0);
+  br.assign(nb, 0.0);
+  for (int i = 0; i < nb; ++i) {
+    for (int l = 0; l < d; ++l) bc[3 * i + l] = b[(d + 1) * i + l];
+    br[i] = b[(d + 1) * i + d];
+    if (!(br[i] > 0)) { *err = "ball radius must be > 0"; return SBM_ERR_ARG; }
+  }
+  circles.clear();
+  verts.clear();
+  std::vector<double> cand;            // vertex candidates with their defining balls
+  std::vector<int> cdef;
+  for (int i = 0; i < nb; ++i)
+    for (int j = i + 1; j < nb; ++j) {
+      double dv[3] = {0, 0, 0};
+      for (int l = 0; l < d; ++l) dv[l] = bc[3 * j + l] - bc[3 * i + l];
+      const double D = norm_d(dv, d);
+      if (!(D < br[i] + br[j] && D > std::fabs(br[i] - br[j]))) continue;
+      Circle C{};
+      C.i = i;
+      C.j = j;
+      for (int l = 0; l < d; ++l) C.u[l] = dv[l] / D;
+      const double aa = (D * D + br[i] * br[i] - br[j] * br[j]) / (2.0 * D);
+      for (int l = 0; l < d; ++l) C.m[l] = bc[3 * i + l] + aa * C.u[l];
+      C.rho = std::sqrt(br[i] * br[i] - aa * aa);
+      if (d == 3) {
+        circles.push_back(C);
+      } else {
+        const double perp[2] = {-C.u[1], C.u[0]};
+        for (int sg = 0; sg < 2; ++sg) {
+          const double sgn = sg ? -1.0 : 1.0;
+          for (int l = 0; l < 2; ++l) cand.push_back(C.m[l] + sgn * C.rho * perp[l]);
+          cand.push_back(0.0);
+          cdef.push_back(i);
+          cdef.push_back(j);
+          cdef.push_back(-1);
+        }
+      }
+    }
+  if (d == 3)
+    for (int i = 0; i < nb; ++i)
+      for (int j = i + 1; j < nb; ++j)
+        for (int k = j + 1; k < nb; ++k) {
+          double pts[2][3];
+          const int np = three_spheres(&bc[3 * i], br[i], &bc[3 * j], br[j], &bc[3 * k], br[k], pts);
+          for (int q = 0; q < np; ++q) {
+            for (int l = 0; l < 3; ++l) cand.push_back(pts[q][l]);
+            cdef.push_back(i);
+            cdef.push_back(j);
+            cdef.push_back(k);
+          }
+        }
+  for (size_t q = 0; q * 3 < cand.size(); ++q) {
+    const int skip[3] = {cdef[3 * q], cdef[3 * q + 1], cdef[3 * q + 2]};
+    if (outside_others(*this, &cand[3 * q], skip, skip[2] < 0 ? 2 : 3))
+      for (int l = 0; l < 3; ++l) verts.push_back(cand[3 * q + l]);
+  }
+  return SBM_OK;
+}
+
+static bool balls_closest(const LevelSet& ls, const double* x, double* out) {
+  const int d = ls.dim, nb = (int)ls.br.size();
+  double best = INFINITY;
+  bool found = false;
+  auto take = [&](const double* p) {
+    double d2 = 0.0;
+    for (int l = 0; l < d; ++l) d2 = d2 + (p[l] - x[l]) * (p[l] - x[l]);
+    if (d2 < best) {
+      best = d2;
+      for (int l = 0; l < d; ++l) out[l] = p[l];
+      found = true;
+    }
+  };
+  for (int i = 0; i < nb; ++i) {                      // projections onto each sphere
+    double v[3], p[3];
+    for (int l = 0; l < d; ++l) v[l] = x[l] - ls.bc[3 * i + l];
+    const double s = norm_d(v, d);
+    if (!(s > 0)) continue;
+    for (int l = 0; l < d; ++l) p[l] = ls.bc[3 * i + l] + ls.br[i] * v[l] / s;
+    const int skip[1] = {i};
+    if (outside_others(ls, p, skip, 1)) take(p);
+  }
+  for (const LevelSet::Circle& C : ls.circles) {     // nearest points of the circles
+    double w[3], wp[3], p[3];
+    for (int l = 0; l < 3; ++l) w[l] = x[l] - C.m[l];
+    const double t = w[0] * C.u[0] + w[1] * C.u[1] + w[2] * C.u[2];
+    for (int l = 0; l < 3; ++l) wp[l] = w[l] - t * C.u[l];
+    const double s = norm_d(wp, 3);
+    if (!(s > 0)) continue;
+    for (int l = 0; l < 3; ++l) p[l] = C.m[l] + C.rho * wp[l] / s;
+    const int skip[2] = {C.i, C.j};
+    if (outside_others(ls, p, skip, 2)) take(p);
+  }
+  for (size_t q = 0; q * 3 < ls.verts.size(); ++q) take(&ls.verts[3 * q]);
+  return found;
+}
+
 double LevelSet::phi(const double* x) const {
   switch (kind) {
+    case SBM_GEOM_BALLS: {
+      double m = dist_d(x, &bc[0], dim) - br[0];
+      for (size_t b = 1; b < br.size(); ++b) m = std::min(m, dist_d(x, &bc[3 * b], dim) - br[b]);
+      return m;
+    }
     case SBM_GEOM_BALL: {
       double s = 0.0;
       for (int i = 0; i < dim; ++i) s = s + (x[i] - c[i]) * (x[i] - c[i]);
@@ -396,6 +558,8 @@ static bool ellipsoid_root(int d, const double* a, const double* y, double* tout
 
 bool LevelSet::closest(const double* x, double* out) const {
   switch (kind) {
+    case SBM_GEOM_BALLS:
+      return balls_closest(*this, x, out);
     case SBM_GEOM_BALL: {
       double v[3], s = 0.0;
       for (int i = 0; i < dim; ++i) { v[i] = x[i] - c[i]; s += v[i] * v[i]; }
@@ -473,7 +637,10 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
     *err = "unknown extension operator";
     return SBM_ERR_ARG;
   }
-  int st = P.ls.init(desc.geom_kind, d, desc.geom, err);
+  int st = (desc.geom_kind == SBM_GEOM_BALLS)
+               ? P.ls.init_balls(d, desc.nballs, desc.balls, err)
+               : P.ls.init(desc.geom_kind, d, desc.geom, err);
+  P.desc.balls = nullptr;              // copied into the level set; the caller owns it
   if (st != SBM_OK) return st;
   P.d = d; P.p = p; P.n = p + 1; P.N = N;
   P.nd = 1; P.L = 1;

@@ -49,8 +49,18 @@ struct LevelSet {
   double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double Rmaj = 0, rmin = 0;
   double half[3] = {0, 0, 0};
+  // union of balls: centres, radii, pairwise intersection circles (3D) and
+  // the boundary vertices
+  struct Circle {
+    int i, j;
+    double m[3], u[3], rho;
+  };
+  std::vector<double> bc, br;          // [nb * 3] (dim used), [nb]
+  std::vector<Circle> circles;
+  std::vector<double> verts;           // [nv * 3]
 
   int init(int kind, int dim, const double* g, std::string* err);
+  int init_balls(int dim, int nballs, const double* balls, std::string* err);
   double phi(const double* x) const;
   // closest point on Gamma; returns false if the projection is undefined
   bool closest(const double* x, double* out) const;

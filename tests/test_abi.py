@@ -85,7 +85,9 @@ SMALL = [
     S.SPHERE_3D_Q4.resized(20),
     S.ELLIPSOID_3D_Q6.resized(14),
     S.TORUS_3D_DG_Q3.resized(18),
-] + S.batched_ellipsoids(nprob=4, n_range=(8, 14))
+] + S.batched_ellipsoids(nprob=4, n_range=(8, 14)) + [
+    S.multiple_balls(3, cells=24), S.multiple_balls(12, cells=24, degree=2),
+    S.multiple_balls(25, cells=32), S.multiple_balls(6, dim=2, cells=48, degree=2)]
 
 
 @pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)
