@@ -430,6 +430,62 @@ def extension_study(G, torch, steps=40):
     return out
 
 
+def _cut_fraction(w):
+    """Fraction of background cells the true boundary cuts, among the cells
+    that are active or cut (the paper's measure of geometric complexity):
+    a cell is cut when the level set changes sign over its corners."""
+    N, d = w.cells, w.dim
+    h = 2.0 / N
+    g = np.asarray(w.geom).reshape(-1, d + 1)
+    xs = -1.0 + h * np.arange(N + 1)
+    X = np.stack(np.meshgrid(*([xs] * d), indexing="ij"), -1)
+    phi = np.min([np.sqrt(((X - b[:d]) ** 2).sum(-1)) - b[d] for b in g], axis=0)
+    corners = [phi[tuple(slice(o, N + o) for o in off)]
+               for off in np.ndindex(*([2] * d))]
+    lo, hi = np.min(corners, 0), np.max(corners, 0)
+    xc = -1.0 + h * (np.arange(N) + 0.5)
+    Xc = np.stack(np.meshgrid(*([xc] * d), indexing="ij"), -1)
+    active = np.min([np.sqrt(((Xc - b[:d]) ** 2).sum(-1)) - b[d] for b in g], axis=0) < 0
+    cut = (lo < 0) & (hi > 0)
+    return float(cut.sum() / (cut | active).sum())
+
+
+def multiball_study(G, torch, steps=20):
+    """Geometric complexity (Section 4.3): unions of 3 to 25 random balls on a
+    64^3 background mesh, CG p = 2 and 4: FP64 and FP32 GDoF/s and the share
+    of the apply spent on surrogate faces, against the fraction of cut cells."""
+    out = []
+    for p in (2, 4):
+        for nb in (3, 5, 10, 15, 25):
+            w = S.multiple_balls(nb, degree=p)
+            P = G.Problem.from_workload(w)
+            G.sbm_autotune(P.handle)
+            x = torch.from_numpy(S.random_vector(w.seed, P.n_dofs, w.dist)).cuda()
+            r = {"balls": nb, "degree": p, "n_dofs": P.n_dofs, "n_cells": P.n_cells,
+                 "n_sfaces": P.n_sfaces, "cut_fraction": _cut_fraction(w)}
+            for name, xx in (("f64", x), ("f32", x.float())):
+                yy = torch.empty_like(xx)
+                fn = P.apply_f64 if name == "f64" else P.apply_f32
+                for _ in range(3):
+                    fn(xx, yy)
+                torch.cuda.synchronize()
+                G.sbm_profile_enable(P.handle, True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(steps):
+                    fn(xx, yy)
+                e1.record()
+                torch.cuda.synchronize()
+                ph, _ = G.sbm_profile_read(P.handle)
+                G.sbm_profile_enable(P.handle, False)
+                ms = e0.elapsed_time(e1) / steps
+                r[name] = {"gdofs": P.n_dofs / ms / 1e6,
+                           "face_share": ph[0] / max(sum(ph), 1e-30)}
+            out.append(r)
+    return out
+
+
 def batched(G, torch, steps=10):
     """64 rotated-ellipsoid CG problems (N ~ U{16..48}, p ~ U{2..6}), 8
     right-hand sides each, one CUDA-graph launch per batched apply."""
@@ -580,7 +636,8 @@ def run_ours(args, w):
     }
     if not args.skip_extras:
         for key, fn in (("solves", solve_times), ("other_workloads", other_workloads),
-                        ("batched_64x8", batched), ("extension_taylor1", extension_study)):
+                        ("batched_64x8", batched), ("extension_taylor1", extension_study),
+                        ("multiple_balls", multiball_study)):
             try:
                 line[key] = fn(G, torch)
             except Exception as e:  # noqa: BLE001 -- report, never hide the main number
