@@ -430,6 +430,33 @@ def extension_study(G, torch, steps=40):
     return out
 
 
+def activity_study(G, torch):
+    """Active-cell criterion (Section 2): the cell centre inside Omega against
+    the volume fraction >= 0.25 / 0.75 (8^d sub-cell midpoints), on the 2D
+    disk, p = 2, u = sin(pi x) sin(pi y): active cells and the max nodal error
+    of the solution (BiCGStab, else GMRES(300), to 1e-10)."""
+    import dataclasses
+    out = {}
+    for crit, th in (("centre", 0.5), ("volume", 0.25), ("volume", 0.75)):
+        key = crit if crit == "centre" else f"volume{th}"
+        rows = []
+        for N in (16, 32, 64):
+            w = dataclasses.replace(S.DISK_2D_Q2.resized(N), activity=crit, vf_threshold=th)
+            P = G.Problem.from_workload(w)
+            b = torch.from_numpy(P.rhs(0)).cuda()
+            u = torch.from_numpy(P.interpolate(0)).cuda()
+            xs = torch.zeros_like(b)
+            _, rr, ok = G.sbm_bicgstab(P.handle, b, xs, rtol=1e-10, maxit=20000)
+            if not ok:
+                xs.zero_()
+                _, rr, ok = G.sbm_gmres(P.handle, b, xs, rtol=1e-10, maxit=30000, restart=300)
+            rows.append({"N": N, "n_cells": P.n_cells, "n_dofs": P.n_dofs,
+                         "max_nodal_rel_err": float((xs - u).abs().max() / u.abs().max())
+                         if ok else None})
+        out[key] = rows
+    return out
+
+
 def _cut_fraction(w):
     """Fraction of background cells the true boundary cuts, among the cells
     that are active or cut (the paper's measure of geometric complexity):
@@ -637,7 +664,8 @@ def run_ours(args, w):
     if not args.skip_extras:
         for key, fn in (("solves", solve_times), ("other_workloads", other_workloads),
                         ("batched_64x8", batched), ("extension_taylor1", extension_study),
-                        ("multiple_balls", multiball_study)):
+                        ("multiple_balls", multiball_study),
+                        ("activity_criterion", activity_study)):
             try:
                 line[key] = fn(G, torch)
             except Exception as e:  # noqa: BLE001 -- report, never hide the main number

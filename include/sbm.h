@@ -79,7 +79,8 @@ enum {
  *               three spheres (3D) or two circles (2D) meet, keeping only
  *               candidates not strictly inside another ball; ties go to the
  *               first candidate in that order.
- * A background cell is active iff phi(cell centre) < 0 (strictly).
+ * A background cell is active iff phi(cell centre) < 0 (strictly), unless
+ * the volume-fraction criterion is chosen (activity, below).
  * Penalties: CG sigma = pen_shift * p^2 / h; DG surrogate faces
  * sigma = pen_shift * (p+1)^2 / h and interior faces
  * sigma_F = pen_interior * (p+1)^2 / h; h = 2 / cells_per_side.
@@ -96,7 +97,19 @@ typedef struct {
   int extension;        /* SBM_EXT_*: the extension operator E of the shifted terms */
   int nballs;           /* SBM_GEOM_BALLS: number of balls (geom[] unused) */
   const double* balls;  /* SBM_GEOM_BALLS: host [nballs][dim + 1] centre, radius; copied */
+  int activity;         /* SBM_ACTIVE_*: which background cells form the surrogate domain */
+  double vf_threshold;  /* SBM_ACTIVE_VOLUME: minimum volume fraction, in (0, 1] */
 } sbm_desc;
+
+/*
+ * Active cells (Section 2: "lying entirely within Omega or intersecting it
+ * significantly, based on a chosen criterion, e.g. volume fraction"):
+ *   SBM_ACTIVE_CENTRE  phi(cell centre) < 0 (strictly);
+ *   SBM_ACTIVE_VOLUME  the volume fraction of Omega in the cell, estimated
+ *                      by the midpoint rule on 8^d sub-cells (the share of
+ *                      sub-cell midpoints with phi < 0), is >= vf_threshold.
+ */
+enum { SBM_ACTIVE_CENTRE = 0, SBM_ACTIVE_VOLUME = 1 };
 
 /*
  * Extension operator E u_h(x~) on the surrogate boundary (Section 2.1, the

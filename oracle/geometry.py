@@ -10,7 +10,10 @@ the reference coordinates of x in the frame of the owning cell K are kept
 
 Readings taken where the paper leaves a choice open:
 * mesh [-1,1]^d, N cells per side, h = 2/N, cell lower corner -1 + h*i;
-* a cell is active iff the level set at its centre is strictly negative;
+* a cell is active iff the level set at its centre is strictly negative
+  (default), or -- the volume-fraction criterion the paper cites (Section 2)
+  -- iff at least a fraction theta of the midpoints of its 8^d sub-cells
+  have a strictly negative level set;
 * a face between an active cell and the box boundary is a surrogate face;
 * ellipsoid closest point: root of the Lagrange-multiplier equation
   sum_i (a_i y_i / (a_i^2 + t))^2 = 1 found by plain bisection (the paper
@@ -281,10 +284,14 @@ def _three_spheres(c1, r1, c2, r2, c3, r3):
     return [base + Z * ez, base - Z * ez]
 
 
+VF_SAMPLES = 8          # sub-cells per axis of the volume-fraction estimate
+
+
 class Mesh:
     """Active cells, surrogate faces, interior faces and face quadrature data."""
 
-    def __init__(self, dim: int, degree: int, cells: int, levelset: LevelSet):
+    def __init__(self, dim: int, degree: int, cells: int, levelset: LevelSet,
+                 activity: str = "centre", vf_threshold: float = 0.5):
         self.d, self.p, self.N = dim, degree, cells
         self.n = degree + 1
         self.h = 2.0 / cells
@@ -292,8 +299,21 @@ class Mesh:
         d, N, h = dim, cells, self.h
         # all background cells in lexicographic order (axis 0 fastest)
         grid = np.indices((N,) * d)[::-1].reshape(d, -1).T     # [N^d, d], col 0 fastest
-        centres = -1.0 + h * (grid + 0.5)
-        active = levelset.phi(centres) < 0.0
+        if activity == "centre":
+            centres = -1.0 + h * (grid + 0.5)
+            active = levelset.phi(centres) < 0.0
+        elif activity == "volume":
+            # volume fraction of Omega in the cell by the midpoint rule on
+            # VF_SAMPLES^d sub-cells; active iff >= vf_threshold
+            m = VF_SAMPLES
+            sub = np.indices((m,) * d)[::-1].reshape(d, -1).T   # [m^d, d]
+            count = np.zeros(len(grid), dtype=np.int64)
+            for s in sub:
+                pts = -1.0 + h * (grid + (s + 0.5) / m)
+                count += levelset.phi(pts) < 0.0
+            active = count >= vf_threshold * m ** d
+        else:
+            raise ValueError(f"unknown activity criterion {activity!r}")
         self.active = active                                     # [N^d] background mask
         self.cells = grid[active]                                # [Nc, d] multi-indices
         self.cell_lin = np.nonzero(active)[0]                    # background index

@@ -31,7 +31,7 @@ _FACE_CACHE_BYTES = 1 << 30
 
 class Problem:
     def __init__(self, dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
-                 pen_interior=1.0, extension="exact"):
+                 pen_interior=1.0, extension="exact", activity="centre", vf_threshold=0.5):
         if extension not in ("exact", "taylor1"):
             raise ValueError(f"unknown extension {extension!r}")
         self.extension = extension
@@ -40,7 +40,7 @@ class Problem:
         self.nd = self.n ** dim
         self.dg = bool(dg)
         self.ls = geometry.LevelSet(kind, geom, dim)
-        self.mesh = geometry.Mesh(dim, degree, cells, self.ls)
+        self.mesh = geometry.Mesh(dim, degree, cells, self.ls, activity, vf_threshold)
         self.h = self.mesh.h
         p, h = degree, self.h
         if self.dg:
@@ -58,7 +58,9 @@ class Problem:
     def from_workload(cls, w):
         return cls(w.dim, w.degree, w.cells, w.kind, w.geom, dg=w.dg,
                    pen_shift=w.pen_shift, pen_interior=w.pen_interior,
-                   extension=getattr(w, "extension", "exact"))
+                   extension=getattr(w, "extension", "exact"),
+                   activity=getattr(w, "activity", "centre"),
+                   vf_threshold=getattr(w, "vf_threshold", 0.5))
 
     # -- numbering -----------------------------------------------------------
     def _number_dofs(self):

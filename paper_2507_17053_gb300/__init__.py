@@ -27,6 +27,7 @@ STATUS = {
 }
 GEOM_KIND = {"ball": 0, "ellipsoid": 1, "torus": 2, "box": 3, "balls": 4}
 EXTENSION = {"exact": 0, "taylor1": 1}
+ACTIVITY = {"centre": 0, "volume": 1}
 
 
 class SbmError(RuntimeError):
@@ -48,6 +49,8 @@ class sbm_desc(ctypes.Structure):
         ("extension", ctypes.c_int),
         ("nballs", ctypes.c_int),
         ("balls", ctypes.c_void_p),
+        ("activity", ctypes.c_int),
+        ("vf_threshold", ctypes.c_double),
     ]
 
 
@@ -163,7 +166,8 @@ def _stream(stream) -> int | None:
 
 
 def make_desc(dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
-              pen_interior=1.0, extension="exact") -> sbm_desc:
+              pen_interior=1.0, extension="exact", activity="centre",
+              vf_threshold=0.5) -> sbm_desc:
     d = sbm_desc()
     d.dim, d.degree, d.cells_per_side, d.dg = dim, degree, cells, int(bool(dg))
     d.geom_kind = GEOM_KIND[kind] if isinstance(kind, str) else int(kind)
@@ -181,6 +185,8 @@ def make_desc(dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
         d.geom[i] = float(v)
     d.pen_shift, d.pen_interior = float(pen_shift), float(pen_interior)
     d.extension = EXTENSION[extension] if isinstance(extension, str) else int(extension)
+    d.activity = ACTIVITY[activity] if isinstance(activity, str) else int(activity)
+    d.vf_threshold = float(vf_threshold)
     return d
 
 
@@ -379,9 +385,10 @@ class Problem:
     """Owning wrapper around an sbm_problem handle."""
 
     def __init__(self, dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
-                 pen_interior=1.0, device=True, extension="exact"):
+                 pen_interior=1.0, device=True, extension="exact", activity="centre",
+                 vf_threshold=0.5):
         self.desc = make_desc(dim, degree, cells, kind, geom, dg, pen_shift, pen_interior,
-                              extension)
+                              extension, activity, vf_threshold)
         self.dim, self.degree, self.dg = dim, degree, bool(dg)
         self.handle = sbm_create(self.desc)
         if device:
@@ -394,7 +401,9 @@ class Problem:
     def from_workload(cls, w, device=True):
         return cls(w.dim, w.degree, w.cells, w.kind, w.geom, dg=w.dg, pen_shift=w.pen_shift,
                    pen_interior=w.pen_interior, device=device,
-                   extension=getattr(w, "extension", "exact"))
+                   extension=getattr(w, "extension", "exact"),
+                   activity=getattr(w, "activity", "centre"),
+                   vf_threshold=getattr(w, "vf_threshold", 0.5))
 
     def close(self):
         if getattr(self, "handle", None):

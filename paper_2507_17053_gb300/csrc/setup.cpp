@@ -637,6 +637,14 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
     *err = "unknown extension operator";
     return SBM_ERR_ARG;
   }
+  if (desc.activity != SBM_ACTIVE_CENTRE && desc.activity != SBM_ACTIVE_VOLUME) {
+    *err = "unknown activity criterion";
+    return SBM_ERR_ARG;
+  }
+  if (desc.activity == SBM_ACTIVE_VOLUME && !(desc.vf_threshold > 0 && desc.vf_threshold <= 1)) {
+    *err = "vf_threshold must be in (0, 1]";
+    return SBM_ERR_ARG;
+  }
   int st = (desc.geom_kind == SBM_GEOM_BALLS)
                ? P.ls.init_balls(d, desc.nballs, desc.balls, err)
                : P.ls.init(desc.geom_kind, d, desc.geom, err);
@@ -661,7 +669,8 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
   }
   const double h = P.h;
 
-  // active cells: phi(centre) < 0, centre = -1 + h (i + 1/2)
+  // active cells: phi(centre) < 0, centre = -1 + h (i + 1/2); or the volume
+  // fraction (sub-cell midpoints with phi < 0) >= vf_threshold
   int64_t nbg = 1;
   for (int i = 0; i < d; ++i) nbg *= N;
   P.bg_to_cell.assign(nbg, -1);
@@ -676,7 +685,26 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
       r /= N;
       xc[i] = -1.0 + h * (idx[i] + 0.5);
     }
-    if (P.ls.phi(xc) < 0.0) {
+    bool active;
+    if (desc.activity == SBM_ACTIVE_VOLUME) {
+      // volume fraction by the midpoint rule on kVfSamples^d sub-cells
+      constexpr int m = kVfSamples;
+      int count = 0, tot = 1;
+      for (int i = 0; i < d; ++i) tot *= m;
+      for (int s = 0; s < tot; ++s) {
+        double xs[3];
+        int rs = s;
+        for (int i = 0; i < d; ++i) {
+          xs[i] = -1.0 + h * ((double)idx[i] + ((rs % m) + 0.5) / m);
+          rs /= m;
+        }
+        if (P.ls.phi(xs) < 0.0) ++count;
+      }
+      active = (double)count >= desc.vf_threshold * (double)tot;
+    } else {
+      active = P.ls.phi(xc) < 0.0;
+    }
+    if (active) {
       P.bg_to_cell[b] = (int32_t)P.cell_bg.size();
       P.cell_bg.push_back(b);
       for (int i = 0; i < d; ++i) P.cells.push_back(idx[i]);

@@ -41,6 +41,8 @@ void build_tables(int p, Tables1D* t);
 void lagrange_values(const Tables1D& t, double x, double* phi);     // phi[j], any real x
 void lagrange_derivs(const Tables1D& t, double x, double* dphi);
 
+constexpr int kVfSamples = 8;    // sub-cells per axis of the volume-fraction estimate
+
 struct LevelSet {
   int kind = 0, dim = 0;
   double c[3] = {0, 0, 0};

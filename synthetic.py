@@ -98,6 +98,8 @@ class Workload:
     pen_interior: float = 1.0       # DG interior faces: C (p+1)^2/h
     nrhs: int = 1
     extension: str = "exact"        # E u at x~: "exact" point evaluation, "taylor1"
+    activity: str = "centre"        # active cells: "centre" inside, or "volume" fraction
+    vf_threshold: float = 0.5       # volume fraction an active cell needs ("volume")
 
     def resized(self, cells: int, degree: int | None = None) -> "Workload":
         return replace(self, cells=cells,

@@ -2,6 +2,8 @@
 arguments on the host (no GPU needed)."""
 import ctypes
 
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -38,6 +40,8 @@ def test_error_strings(lib):
     (dict(geom=(5.0, 5.0, 0.1)), "SBM_ERR_EMPTY_DOMAIN"),
     (dict(pen_shift=0.0), "SBM_ERR_ARG"),
     (dict(extension=2), "SBM_ERR_ARG"),
+    (dict(activity=2), "SBM_ERR_ARG"),
+    (dict(activity=1, vf_threshold=0.0), "SBM_ERR_ARG"),
 ])
 def test_create_rejects_bad_descriptions(bad, code):
     args = dict(dim=2, degree=2, cells=8, kind="ball", geom=(0.0, 0.0, 0.7))
@@ -87,7 +91,13 @@ SMALL = [
     S.TORUS_3D_DG_Q3.resized(18),
 ] + S.batched_ellipsoids(nprob=4, n_range=(8, 14)) + [
     S.multiple_balls(3, cells=24), S.multiple_balls(12, cells=24, degree=2),
-    S.multiple_balls(25, cells=32), S.multiple_balls(6, dim=2, cells=48, degree=2)]
+    S.multiple_balls(25, cells=32), S.multiple_balls(6, dim=2, cells=48, degree=2)] + [
+    dataclasses.replace(S.DISK_2D_Q2, activity="volume", vf_threshold=t, name=f"disk_vf{t}")
+    for t in (0.2, 0.5, 0.9)] + [
+    dataclasses.replace(S.SPHERE_3D_Q4.resized(16), activity="volume", vf_threshold=0.3,
+                        name="sphere_vf0.3"),
+    dataclasses.replace(S.multiple_balls(10, cells=24), activity="volume", vf_threshold=0.6,
+                        name="balls_vf0.6")]
 
 
 @pytest.mark.parametrize("w", SMALL, ids=lambda w: w.name)

@@ -1,6 +1,7 @@
-"""The multiple-ball geometry (union of balls, Section 4.3) on the GPU: FP64
-apply parity with the oracle (CG and DG, 2D and 3D, exact and first-order
-Taylor extension) at 1e-12, and the FP32 apply within 1e-5 p."""
+"""Geometry variants on the GPU: the multiple-ball geometry (union of balls,
+Section 4.3) and the volume-fraction activity criterion.  FP64 apply parity
+with the oracle (CG and DG, 2D and 3D, exact and first-order Taylor
+extension) at 1e-12, and the FP32 apply within 1e-5 p."""
 import dataclasses
 
 import numpy as np
@@ -21,6 +22,12 @@ CASES = [
     dataclasses.replace(S.multiple_balls(10, cells=16, degree=3), dg=True, name="balls10_dg"),
     dataclasses.replace(S.multiple_balls(10, cells=16, degree=3), extension="taylor1",
                         name="balls10_taylor1"),
+    # the volume-fraction activity criterion (surrogate faces on both sides of Gamma)
+    dataclasses.replace(S.DISK_2D_Q2, activity="volume", vf_threshold=0.2, name="disk_vf0.2"),
+    dataclasses.replace(S.SPHERE_3D_Q4.resized(12), activity="volume", vf_threshold=0.3,
+                        name="sphere_vf0.3"),
+    dataclasses.replace(S.multiple_balls(10, cells=16, degree=2), activity="volume",
+                        vf_threshold=0.7, name="balls10_vf0.7"),
 ]
 
 
