@@ -582,11 +582,23 @@ def run_ours(args, w):
     G.sbm_setup_face_data(P.handle)                  # device tables, chunking, uploads
     torch.cuda.synchronize()
     t2 = time.perf_counter()
+    # the same with the geometry stage on the GPU (identical problem)
+    t3 = time.perf_counter()
+    Pg = G.Problem.from_workload(w, device=False, gpu_setup=True)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    G.sbm_setup_face_data(Pg.handle)
+    torch.cuda.synchronize()
+    t5 = time.perf_counter()
+    del Pg
     init = {"host_geometry_s": t1 - t0, "device_setup_s": t2 - t1,
             "dofs_per_s": P.n_dofs / (t2 - t0),
+            "gpu_geometry": {"create_s": t4 - t3, "device_setup_s": t5 - t4,
+                             "dofs_per_s": P.n_dofs / (t5 - t3)},
             "face_table_bytes_per_dof": (P.n_sfaces * (w.degree + 1) ** (w.dim - 1) * w.dim
                                          * (w.degree + 1) * 8) / P.n_dofs,
-            "note": "sbm_create + sbm_setup_face_data; face table = FP64 1D values at the "
+            "note": "sbm_create (host) or sbm_create_gpu (geometry stage on the GPU, numbering "
+                    "on the host) + sbm_setup_face_data; face table = FP64 1D values at the "
                     "shifted points (the FP32 copy adds half)"}
     shapes = G.sbm_autotune(P.handle)       # tile shapes of the FP64 / FP32 cell kernel
     x_host = S.random_vector(w.seed, P.n_dofs, w.dist)

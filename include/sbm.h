@@ -145,6 +145,20 @@ int sbm_create(const sbm_desc* desc, sbm_problem** out);
  */
 int sbm_setup_face_data(sbm_problem* prob);
 
+/*
+ * sbm_create with the geometry stage on GPU `device` (the operator
+ * initialisation of Section 4.4): active-cell marking, surrogate-face
+ * enumeration (deterministic scans), the closest-point projection of every
+ * surrogate quadrature point and the CG DoF numbering (lattice marks, scan)
+ * run as kernels.  The result is identical, bit for bit, to sbm_create's (the level-set
+ * and projection code is shared and compiled without fused multiply-adds).
+ * Synchronous; temporary device memory about 16 bytes per background cell,
+ * 72 bytes per surrogate quadrature point and (CG) 12 bytes per lattice node
+ * of the (pN+1)^d background lattice, freed before returning.
+ * Errors: as sbm_create, plus SBM_ERR_ARG (device < 0) and SBM_ERR_CUDA.
+ */
+int sbm_create_gpu(const sbm_desc* desc, int device, sbm_problem** out);
+
 /* Free every host and device resource of the problem (NULL is ignored).
  * The caller must make sure no work that uses the problem is still running. */
 void sbm_destroy(sbm_problem* prob);

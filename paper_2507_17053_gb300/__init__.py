@@ -57,6 +57,8 @@ class sbm_desc(ctypes.Structure):
 _c_i64p = ctypes.POINTER(ctypes.c_int64)
 _SIGS = {
     "sbm_create": (ctypes.c_int, [ctypes.POINTER(sbm_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "sbm_create_gpu": (ctypes.c_int, [ctypes.POINTER(sbm_desc), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
     "sbm_setup_face_data": (ctypes.c_int, [ctypes.c_void_p]),
     "sbm_destroy": (None, [ctypes.c_void_p]),
     "sbm_sizes": (ctypes.c_int, [ctypes.c_void_p, _c_i64p, _c_i64p, _c_i64p, _c_i64p]),
@@ -195,6 +197,13 @@ def make_desc(dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
 def sbm_create(desc: sbm_desc) -> int:
     h = ctypes.c_void_p()
     _check(lib().sbm_create(ctypes.byref(desc), ctypes.byref(h)), "sbm_create")
+    return h.value
+
+
+def sbm_create_gpu(desc: sbm_desc, device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sbm_create_gpu(ctypes.byref(desc), int(device), ctypes.byref(h)),
+           "sbm_create_gpu")
     return h.value
 
 
@@ -381,16 +390,23 @@ class Batch:
         _check(lib().sbm_batch_set_tile_shape(self.handle, k, variant), "sbm_batch_set_tile_shape")
 
 
+def _current_device() -> int:
+    import torch
+    return torch.cuda.current_device()
+
+
 class Problem:
     """Owning wrapper around an sbm_problem handle."""
 
     def __init__(self, dim, degree, cells, kind, geom, dg=False, pen_shift=10.0,
                  pen_interior=1.0, device=True, extension="exact", activity="centre",
-                 vf_threshold=0.5):
+                 vf_threshold=0.5, gpu_setup=False):
         self.desc = make_desc(dim, degree, cells, kind, geom, dg, pen_shift, pen_interior,
                               extension, activity, vf_threshold)
         self.dim, self.degree, self.dg = dim, degree, bool(dg)
-        self.handle = sbm_create(self.desc)
+        # gpu_setup: the geometry stage on the current CUDA device (same result)
+        self.handle = (sbm_create_gpu(self.desc, _current_device()) if gpu_setup
+                       else sbm_create(self.desc))
         if device:
             sbm_setup_face_data(self.handle)
         s = sbm_sizes(self.handle)
@@ -398,9 +414,9 @@ class Problem:
         self.n_sfaces, self.n_ifaces = s["n_sfaces"], s["n_ifaces"]
 
     @classmethod
-    def from_workload(cls, w, device=True):
+    def from_workload(cls, w, device=True, gpu_setup=False):
         return cls(w.dim, w.degree, w.cells, w.kind, w.geom, dg=w.dg, pen_shift=w.pen_shift,
-                   pen_interior=w.pen_interior, device=device,
+                   pen_interior=w.pen_interior, device=device, gpu_setup=gpu_setup,
                    extension=getattr(w, "extension", "exact"),
                    activity=getattr(w, "activity", "centre"),
                    vf_threshold=getattr(w, "vf_threshold", 0.5))

@@ -21,6 +21,9 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsbm.so")
 
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+# the device set-up shares its level-set arithmetic with the host set-up and
+# must round like it: no fused multiply-adds there
+PER_FILE = {"setup_gpu.cu": ["--fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -40,7 +43,8 @@ def _compile(src: str, extra: list[str]) -> str:
     inc = [f"-I{INCLUDE}", f"-I{CSRC}"]
     if src.endswith(".cu"):
         cmd = [_nvcc(), ARCH, "-lineinfo", "-O3", "-std=c++17", "-c", src, "-o", obj,
-               "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr", *inc, *extra]
+               "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr", *inc, *extra,
+               *PER_FILE.get(os.path.basename(src), [])]
     else:
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", "-c", src,
                "-o", obj, f"-I{os.path.join(os.path.dirname(_nvcc()), '..', 'include')}", *inc]

@@ -374,7 +374,9 @@ const char* sbm_error_string(int status) {
 
 const char* sbm_last_error_detail(void) { return g_detail.c_str(); }
 
-int sbm_create(const sbm_desc* desc, sbm_problem** out) {
+// device < 0: the whole set-up on the host; otherwise the geometry stage on
+// that GPU
+static int create_problem(const sbm_desc* desc, int device, sbm_problem** out) {
   if (!out) return fail(SBM_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!desc) return fail(SBM_ERR_ARG, "desc is NULL");
@@ -383,7 +385,13 @@ int sbm_create(const sbm_desc* desc, sbm_problem** out) {
   std::string err;
   int st;
   try {
-    st = build_host_problem(*desc, &P->hp, &err);
+    if (device < 0) {
+      st = build_host_problem(*desc, &P->hp, &err);
+    } else {
+      st = setup_prepare(*desc, &P->hp, &err);
+      if (st == SBM_OK) st = setup_geometry_device(&P->hp, device, &err);
+      if (st == SBM_OK) st = setup_numbering_device(&P->hp, device, &err);
+    }
   } catch (const std::bad_alloc&) {
     st = SBM_ERR_OOM;
     err = "host allocation failed";
@@ -394,6 +402,13 @@ int sbm_create(const sbm_desc* desc, sbm_problem** out) {
   }
   *out = P;
   return SBM_OK;
+}
+
+int sbm_create(const sbm_desc* desc, sbm_problem** out) { return create_problem(desc, -1, out); }
+
+int sbm_create_gpu(const sbm_desc* desc, int device, sbm_problem** out) {
+  if (device < 0) return fail(SBM_ERR_ARG, "device must be >= 0");
+  return create_problem(desc, device, out);
 }
 
 int sbm_setup_face_data(sbm_problem* prob) {

@@ -321,27 +321,27 @@ int LevelSet::init(int k, int d, const double* g, std::string* err) {
 // The same formulas, in the same operation order, as the oracle's, so that the
 // two geometries agree to the last bit.
 
-static double norm_d(const double* v, int d) {
-  double s = 0.0;
-  for (int l = 0; l < d; ++l) s = s + v[l] * v[l];
-  return std::sqrt(s);
-}
-
-static double dist_d(const double* x, const double* c, int d) {
-  double v[3];
-  for (int l = 0; l < d; ++l) v[l] = x[l] - c[l];
-  return norm_d(v, d);
-}
-
-// p is not strictly inside any ball other than those in skip[0..ns)
-static bool outside_others(const LevelSet& ls, const double* p, const int* skip, int ns) {
-  const int nb = (int)ls.br.size();
-  for (int l = 0; l < nb; ++l) {
-    bool sk = false;
-    for (int q = 0; q < ns; ++q) sk = sk || (skip[q] == l);
-    if (!sk && !(dist_d(p, &ls.bc[3 * l], ls.dim) >= ls.br[l])) return false;
+GeomView LevelSet::view() const {
+  GeomView g;
+  g.kind = kind;
+  g.dim = dim;
+  for (int i = 0; i < 3; ++i) {
+    g.c[i] = c[i];
+    g.a[i] = a[i];
+    g.half[i] = half[i];
   }
-  return true;
+  for (int i = 0; i < 9; ++i) g.R[i] = R[i];
+  g.r = r;
+  g.Rmaj = Rmaj;
+  g.rmin = rmin;
+  g.nb = (int)br.size();
+  g.ncirc = (int)circles.size();
+  g.nvert = (int)(verts.size() / 3);
+  g.bc = bc.data();
+  g.br = br.data();
+  g.circ = circles.data();
+  g.verts = verts.data();
+  return g;
 }
 
 // the 0 or 2 points common to three spheres (trilateration)
@@ -349,12 +349,12 @@ static int three_spheres(const double* c1, double r1, const double* c2, double r
                          const double* c3, double r3, double out[2][3]) {
   double dv[3], ex[3], w[3], ey[3], ez[3];
   for (int l = 0; l < 3; ++l) dv[l] = c2[l] - c1[l];
-  const double D = norm_d(dv, 3);
+  const double D = gv_norm(dv, 3);
   for (int l = 0; l < 3; ++l) ex[l] = dv[l] / D;
   for (int l = 0; l < 3; ++l) w[l] = c3[l] - c1[l];
   const double i = ex[0] * w[0] + ex[1] * w[1] + ex[2] * w[2];
   for (int l = 0; l < 3; ++l) ey[l] = w[l] - i * ex[l];
-  const double ny = norm_d(ey, 3);
+  const double ny = gv_norm(ey, 3);
   if (!(ny > 1e-12 * D)) return 0;
   for (int l = 0; l < 3; ++l) ey[l] = ey[l] / ny;
   ez[0] = ex[1] * ey[2] - ex[2] * ey[1];
@@ -393,9 +393,9 @@ int LevelSet::init_balls(int d, int nb, const double* b, std::string* err) {
     for (int j = i + 1; j < nb; ++j) {
       double dv[3] = {0, 0, 0};
       for (int l = 0; l < d; ++l) dv[l] = bc[3 * j + l] - bc[3 * i + l];
-      const double D = norm_d(dv, d);
+      const double D = gv_norm(dv, d);
       if (!(D < br[i] + br[j] && D > std::fabs(br[i] - br[j]))) continue;
-      Circle C{};
+      GeomCircle C{};
       C.i = i;
       C.j = j;
       for (int l = 0; l < d; ++l) C.u[l] = dv[l] / D;
@@ -429,202 +429,20 @@ int LevelSet::init_balls(int d, int nb, const double* b, std::string* err) {
             cdef.push_back(k);
           }
         }
-  for (size_t q = 0; q * 3 < cand.size(); ++q) {
-    const int skip[3] = {cdef[3 * q], cdef[3 * q + 1], cdef[3 * q + 2]};
-    if (outside_others(*this, &cand[3 * q], skip, skip[2] < 0 ? 2 : 3))
-      for (int l = 0; l < 3; ++l) verts.push_back(cand[3 * q + l]);
-  }
+  const GeomView g = view();            // nb, bc, br set; no circles or vertices needed
+  std::vector<double> kept;
+  for (size_t q = 0; q * 3 < cand.size(); ++q)
+    if (gv_outside_others(g, &cand[3 * q], cdef[3 * q], cdef[3 * q + 1], cdef[3 * q + 2]))
+      for (int l = 0; l < 3; ++l) kept.push_back(cand[3 * q + l]);
+  verts = kept;
   return SBM_OK;
-}
-
-static bool balls_closest(const LevelSet& ls, const double* x, double* out) {
-  const int d = ls.dim, nb = (int)ls.br.size();
-  double best = INFINITY;
-  bool found = false;
-  auto take = [&](const double* p) {
-    double d2 = 0.0;
-    for (int l = 0; l < d; ++l) d2 = d2 + (p[l] - x[l]) * (p[l] - x[l]);
-    if (d2 < best) {
-      best = d2;
-      for (int l = 0; l < d; ++l) out[l] = p[l];
-      found = true;
-    }
-  };
-  for (int i = 0; i < nb; ++i) {                      // projections onto each sphere
-    double v[3], p[3];
-    for (int l = 0; l < d; ++l) v[l] = x[l] - ls.bc[3 * i + l];
-    const double s = norm_d(v, d);
-    if (!(s > 0)) continue;
-    for (int l = 0; l < d; ++l) p[l] = ls.bc[3 * i + l] + ls.br[i] * v[l] / s;
-    const int skip[1] = {i};
-    if (outside_others(ls, p, skip, 1)) take(p);
-  }
-  for (const LevelSet::Circle& C : ls.circles) {     // nearest points of the circles
-    double w[3], wp[3], p[3];
-    for (int l = 0; l < 3; ++l) w[l] = x[l] - C.m[l];
-    const double t = w[0] * C.u[0] + w[1] * C.u[1] + w[2] * C.u[2];
-    for (int l = 0; l < 3; ++l) wp[l] = w[l] - t * C.u[l];
-    const double s = norm_d(wp, 3);
-    if (!(s > 0)) continue;
-    for (int l = 0; l < 3; ++l) p[l] = C.m[l] + C.rho * wp[l] / s;
-    const int skip[2] = {C.i, C.j};
-    if (outside_others(ls, p, skip, 2)) take(p);
-  }
-  for (size_t q = 0; q * 3 < ls.verts.size(); ++q) take(&ls.verts[3 * q]);
-  return found;
-}
-
-double LevelSet::phi(const double* x) const {
-  switch (kind) {
-    case SBM_GEOM_BALLS: {
-      double m = dist_d(x, &bc[0], dim) - br[0];
-      for (size_t b = 1; b < br.size(); ++b) m = std::min(m, dist_d(x, &bc[3 * b], dim) - br[b]);
-      return m;
-    }
-    case SBM_GEOM_BALL: {
-      double s = 0.0;
-      for (int i = 0; i < dim; ++i) s = s + (x[i] - c[i]) * (x[i] - c[i]);
-      return std::sqrt(s) - r;
-    }
-    case SBM_GEOM_ELLIPSOID: {
-      double s = 0.0;
-      for (int i = 0; i < dim; ++i) {
-        double y = 0.0;
-        for (int j = 0; j < dim; ++j) y = y + R[j * dim + i] * (x[j] - c[j]);
-        s = s + (y / a[i]) * (y / a[i]);
-      }
-      return s - 1.0;
-    }
-    case SBM_GEOM_TORUS: {
-      double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]);
-      return (rho - Rmaj) * (rho - Rmaj) + x[2] * x[2] - rmin * rmin;
-    }
-    case SBM_GEOM_BOX: {
-      double m = std::fabs(x[0] - c[0]) - half[0];
-      for (int i = 1; i < dim; ++i) m = std::max(m, std::fabs(x[i] - c[i]) - half[i]);
-      return m;
-    }
-  }
-  return 1.0;
-}
-
-// Ellipsoid: in the frame y = R^T (x - c) the closest point is
-// z_i = a_i^2 y_i / (a_i^2 + t) with t the root on (-a_min^2, inf) of
-// F(t) = sum_i (a_i y_i / (a_i^2 + t))^2 - 1 (D. Eberly, "Distance from a
-// point to an ellipse, an ellipsoid, or a hyperellipsoid").  F is convex and
-// decreasing there: safeguarded Newton (bisection whenever a Newton step
-// leaves the bracket).
-static bool ellipsoid_root(int d, const double* a, const double* y, double* tout) {
-  double a2[3], amin2 = 1e300, amax = 0, yn = 0, f0 = -1.0;
-  for (int i = 0; i < d; ++i) {
-    a2[i] = a[i] * a[i];
-    amin2 = std::min(amin2, a2[i]);
-    amax = std::max(amax, a[i]);
-    yn += y[i] * y[i];
-    f0 += (y[i] / a[i]) * (y[i] / a[i]);
-  }
-  yn = std::sqrt(yn);
-  if (f0 == 0.0) { *tout = 0.0; return true; }
-  double lo, hi;
-  if (f0 > 0) { lo = 0.0; hi = amax * yn; }
-  else {
-    lo = -amin2; hi = 0.0;
-    // the root exists in (-a_min^2, 0) only if some y_i on a shortest axis is non-zero
-    bool ok = false;
-    for (int i = 0; i < d; ++i) if (a2[i] == amin2 && y[i] != 0.0) ok = true;
-    if (!ok) return false;
-  }
-  double t = (f0 > 0) ? 0.0 : 0.5 * (lo + hi);
-  for (int it = 0; it < 300; ++it) {
-    double F = -1.0, dF = 0.0;
-    for (int i = 0; i < d; ++i) {
-      double q = a[i] * y[i] / (a2[i] + t);
-      F += q * q;
-      dF += -2.0 * q * q / (a2[i] + t);
-    }
-    if (F > 0) lo = t; else hi = t;
-    if (F == 0.0) break;
-    double tn = t - F / dF;
-    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-    if (std::fabs(tn - t) <= 1e-16 * std::max(1.0, std::fabs(t)) || tn == lo || tn == hi) {
-      t = tn;
-      break;
-    }
-    t = tn;
-  }
-  *tout = t;
-  return true;
-}
-
-bool LevelSet::closest(const double* x, double* out) const {
-  switch (kind) {
-    case SBM_GEOM_BALLS:
-      return balls_closest(*this, x, out);
-    case SBM_GEOM_BALL: {
-      double v[3], s = 0.0;
-      for (int i = 0; i < dim; ++i) { v[i] = x[i] - c[i]; s += v[i] * v[i]; }
-      s = std::sqrt(s);
-      if (!(s > 0)) return false;
-      for (int i = 0; i < dim; ++i) out[i] = c[i] + r * v[i] / s;
-      return true;
-    }
-    case SBM_GEOM_TORUS: {
-      double rho = std::sqrt(x[0] * x[0] + x[1] * x[1]);
-      if (!(rho > 0)) return false;
-      double q[3] = {Rmaj * x[0] / rho, Rmaj * x[1] / rho, 0.0};
-      double v[3], s = 0.0;
-      for (int i = 0; i < 3; ++i) { v[i] = x[i] - q[i]; s += v[i] * v[i]; }
-      s = std::sqrt(s);
-      if (!(s > 0)) return false;
-      for (int i = 0; i < 3; ++i) out[i] = q[i] + rmin * v[i] / s;
-      return true;
-    }
-    case SBM_GEOM_BOX: {
-      double v[3];
-      bool inside = true;
-      for (int i = 0; i < dim; ++i) {
-        v[i] = x[i] - c[i];
-        if (std::fabs(v[i]) > half[i]) inside = false;
-      }
-      if (!inside) {
-        for (int i = 0; i < dim; ++i) out[i] = c[i] + std::min(std::max(v[i], -half[i]), half[i]);
-        return true;
-      }
-      int kmin = 0;
-      double gmin = half[0] - std::fabs(v[0]);
-      for (int i = 1; i < dim; ++i) {
-        double gap = half[i] - std::fabs(v[i]);
-        if (gap < gmin) { gmin = gap; kmin = i; }
-      }
-      for (int i = 0; i < dim; ++i) out[i] = x[i];
-      out[kmin] = c[kmin] + (v[kmin] >= 0 ? half[kmin] : -half[kmin]);
-      return true;
-    }
-    case SBM_GEOM_ELLIPSOID: {
-      double y[3], z[3], t;
-      for (int i = 0; i < dim; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < dim; ++j) s += R[j * dim + i] * (x[j] - c[j]);
-        y[i] = s;
-      }
-      if (!ellipsoid_root(dim, a, y, &t)) return false;
-      for (int i = 0; i < dim; ++i) z[i] = a[i] * a[i] * y[i] / (a[i] * a[i] + t);
-      for (int i = 0; i < dim; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < dim; ++j) s += R[i * dim + j] * z[j];
-        out[i] = c[i] + s;
-      }
-      return true;
-    }
-  }
-  return false;
 }
 
 // ---------------------------------------------------------------------------
 // Mesh, faces, numbering
 // ---------------------------------------------------------------------------
 
-int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) {
+int setup_prepare(const sbm_desc& desc, HostProblem* hp, std::string* err) {
   HostProblem& P = *hp;
   P.desc = desc;
   const int d = desc.dim, p = desc.degree, N = desc.cells_per_side;
@@ -667,7 +485,15 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
     *err = "1D eigenbasis of the cell operator is inaccurate";
     return SBM_ERR_UNSUPPORTED;
   }
+  return SBM_OK;
+}
+
+int setup_geometry_host(HostProblem* hp, std::string* err) {
+  HostProblem& P = *hp;
+  const sbm_desc& desc = P.desc;
+  const int d = P.d, N = P.N;
   const double h = P.h;
+  const GeomView gv = P.ls.view();
 
   // active cells: phi(centre) < 0, centre = -1 + h (i + 1/2); or the volume
   // fraction (sub-cell midpoints with phi < 0) >= vf_threshold
@@ -698,11 +524,11 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
           xs[i] = -1.0 + h * ((double)idx[i] + ((rs % m) + 0.5) / m);
           rs /= m;
         }
-        if (P.ls.phi(xs) < 0.0) ++count;
+        if (geom_phi(gv, xs) < 0.0) ++count;
       }
       active = (double)count >= desc.vf_threshold * (double)tot;
     } else {
-      active = P.ls.phi(xc) < 0.0;
+      active = geom_phi(gv, xc) < 0.0;
     }
     if (active) {
       P.bg_to_cell[b] = (int32_t)P.cell_bg.size();
@@ -750,7 +576,7 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
       xi[tang[0]] = P.tab.gpts[qa];
       if (d == 3) xi[tang[1]] = P.tab.gpts[qb];
       for (int l = 0; l < d; ++l) xt[l] = lo[l] + h * xi[l];
-      if (!P.ls.closest(xt, xq)) {
+      if (!geom_closest(gv, xt, xq)) {
         *err = "closest-point projection undefined for a surrogate quadrature point";
         return SBM_ERR_GEOMETRY;
       }
@@ -762,7 +588,14 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
     }
   }
 
-  // numbering
+  return SBM_OK;
+}
+
+int setup_numbering(HostProblem* hp, std::string* err) {
+  HostProblem& P = *hp;
+  const sbm_desc& desc = P.desc;
+  const int d = P.d, p = P.p, n = P.n, N = P.N;
+  const int64_t Nc = (int64_t)P.cell_bg.size();
   if (desc.dg) {
     P.n_dofs = Nc * P.nd;
     if (P.n_dofs >= (int64_t(1) << 31)) { *err = "too many DoFs for int32 indices"; return SBM_ERR_ARG; }
@@ -803,6 +636,13 @@ int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) 
     }
   }
   return SBM_OK;
+}
+
+int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err) {
+  int st = setup_prepare(desc, hp, err);
+  if (st == SBM_OK) st = setup_geometry_host(hp, err);
+  if (st == SBM_OK) st = setup_numbering(hp, err);
+  return st;
 }
 
 // ---------------------------------------------------------------------------

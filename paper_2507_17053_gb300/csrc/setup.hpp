@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "geom.hpp"
 #include "sbm.h"
 
 namespace sbm {
@@ -53,19 +54,17 @@ struct LevelSet {
   double half[3] = {0, 0, 0};
   // union of balls: centres, radii, pairwise intersection circles (3D) and
   // the boundary vertices
-  struct Circle {
-    int i, j;
-    double m[3], u[3], rho;
-  };
   std::vector<double> bc, br;          // [nb * 3] (dim used), [nb]
-  std::vector<Circle> circles;
+  std::vector<GeomCircle> circles;
   std::vector<double> verts;           // [nv * 3]
 
   int init(int kind, int dim, const double* g, std::string* err);
   int init_balls(int dim, int nballs, const double* balls, std::string* err);
-  double phi(const double* x) const;
+  // a plain view (host pointers into this object) for geom_phi / geom_closest
+  GeomView view() const;
+  double phi(const double* x) const { return geom_phi(view(), x); }
   // closest point on Gamma; returns false if the projection is undefined
-  bool closest(const double* x, double* out) const;
+  bool closest(const double* x, double* out) const { return geom_closest(view(), x, out); }
 };
 
 struct HostProblem {
@@ -97,6 +96,15 @@ struct HostProblem {
 
 // Build everything on the host.  Returns SBM_OK or an error code with *err set.
 int build_host_problem(const sbm_desc& desc, HostProblem* hp, std::string* err);
+// The three stages of it: checks, 1D tables and level set; active cells,
+// surrogate faces and closest points; DoF numbering.  The middle stage has a
+// device counterpart (setup_geometry_device, setup_gpu.cu) with identical
+// results.
+int setup_prepare(const sbm_desc& desc, HostProblem* hp, std::string* err);
+int setup_geometry_host(HostProblem* hp, std::string* err);
+int setup_numbering(HostProblem* hp, std::string* err);
+int setup_geometry_device(HostProblem* hp, int device, std::string* err);
+int setup_numbering_device(HostProblem* hp, int device, std::string* err);
 
 // Manufactured solutions: 0 = prod_i sin(pi x_i) (f = d pi^2 u),
 // 1 = 2 cos(x_0) sin(x_1) in 2D (f = 2 u).
