@@ -200,10 +200,10 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   for (int col = 1; col < dd->ncolours; ++col) dd->col_start[col] = dd->col_start[dd->ncolours];
 
   std::vector<int32_t> lines_o, fstart(Nc + 1, 0), fkind, fcell;
-  std::vector<double> fphi;
+  std::vector<int64_t> fsrc;             // kernel face order -> face index
   if (!hp.desc.dg) lines_o.resize(Nc * L);
   fkind.reserve(F);
-  fphi.reserve(F * L * d * n);
+  fsrc.reserve(F);
   for (int64_t i = 0; i < Nc; ++i) {
     const int c = dd->order[i];
     if (!hp.desc.dg)
@@ -213,16 +213,7 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
       const int64_t f = first_face[c] + j;
       fkind.push_back(hp.sfaces[3 * f + 1] | (hp.sfaces[3 * f + 2] << 2));
       fcell.push_back((int32_t)i);
-      for (int q = 0; q < L; ++q)
-        for (int l = 0; l < d; ++l) {
-          if (hp.desc.extension == SBM_EXT_TAYLOR1) {   // the shift vector d_q
-            fphi.push_back(hp.face_d[(f * L + q) * d + l]);
-            continue;
-          }
-          double phi[kMaxN];
-          lagrange_values(hp.tab, hp.face_xi[(f * L + q) * d + l], phi);
-          for (int jj = 0; jj < n; ++jj) fphi.push_back(phi[jj]);
-        }
+      fsrc.push_back(f);
     }
   }
   fstart[Nc] = (int32_t)fkind.size();
@@ -251,60 +242,19 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   if ((e = cudaMalloc((void**)&dd->err_flag, sizeof(int))) != cudaSuccess) goto err;
   if ((e = cudaMemset(dd->err_flag, 0, sizeof(int))) != cudaSuccess) goto err;
   if (!hp.desc.dg) {
-    // per chunking: chunk tables and the per-DoF colour masks
+    // per chunking: chunk tables, then on the device the per-DoF colour sets,
+    // the list of DoFs several colours share and the per-chunk run bits
     for (int v = 0; v < 2; ++v) {
-      std::vector<uint8_t> mask(hp.n_dofs, 0);
       const int nch = (int)ch_col[v].size();
-      for (int k = 0; k < nch; ++k)
-        for (int i = ch_first[v][k]; i < ch_first[v][k + 1]; ++i) {
-          const int c = dd->order[i];
-          for (int line = 0; line < L; ++line) {
-            const int32_t g = hp.lines[(int64_t)c * L + line];
-            for (int m = 0; m < n; ++m) mask[g + m] |= (uint8_t)(1u << ch_col[v][k]);
-          }
-        }
       dd->chunks[v].n = nch;
       if ((e = upload(&dd->chunks[v].first, ch_first[v].data(), ch_first[v].size())) !=
           cudaSuccess)
         goto err;
       if ((e = upload(&dd->chunks[v].colour, ch_col[v].data(), ch_col[v].size())) != cudaSuccess)
         goto err;
-      // per chunk: which elements of its L runs (p*nc + 1 each) several colours share
-      {
-        const int R = v == 0 ? chunk_cells(d, n) : std::max(chunk_cells(d, n) / 2, 1);
-        const int words = (L * ((n - 1) * R + 1) + 31) / 32;
-        std::vector<uint32_t> bits((size_t)nch * words, 0u);
-        for (int k = 0; k < nch; ++k) {
-          const int nc = ch_first[v][k + 1] - ch_first[v][k];
-          const int S = (n - 1) * nc + 1;
-          for (int l = 0; l < L; ++l) {
-            const int64_t g0 = lines_o[(int64_t)ch_first[v][k] * L + l];
-            for (int kk = 0; kk < S; ++kk) {
-              const uint8_t mk = mask[g0 + kk];
-              if (mk & (mk - 1)) {
-                const int b = l * S + kk;
-                bits[(size_t)k * words + b / 32] |= 1u << (b % 32);
-              }
-            }
-          }
-        }
-        dd->chunks[v].bit_words = words;
-        if ((e = upload(&dd->chunks[v].run_bits, bits.data(), bits.size())) != cudaSuccess)
-          goto err;
-      }
-      // DoFs of two colours or more, ascending
-      std::vector<int32_t> multi;
-      std::vector<uint8_t> multi_mask;
-      for (int64_t g = 0; g < hp.n_dofs; ++g)
-        if (mask[g] & (mask[g] - 1)) {
-          multi.push_back((int32_t)g);
-          multi_mask.push_back(mask[g]);
-        }
-      dd->chunks[v].nmulti = (int64_t)multi.size();
-      if (!multi.empty() &&
-          ((e = upload(&dd->chunks[v].multi, multi.data(), multi.size())) != cudaSuccess ||
-           (e = upload(&dd->chunks[v].multi_mask, multi_mask.data(), multi_mask.size())) !=
-               cudaSuccess))
+      const int R = v == 0 ? chunk_cells(d, n) : std::max(chunk_cells(d, n) / 2, 1);
+      if ((e = device_chunk_tables(dd->lines, Nc, L, n, hp.n_dofs, ch_first[v], ch_col[v], R,
+                                   dd->chunks[v].first, &dd->chunks[v])) != cudaSuccess)
         goto err;
     }
     // ordered positions grouped by the parity colour of the cell (diagonal kernel)
@@ -335,11 +285,7 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
         cudaSuccess)
       goto err;
   }
-  if ((e = upload(&dd->face_phi, fphi.data(), fphi.size())) != cudaSuccess) goto err;
-  {
-    std::vector<float> f32(fphi.begin(), fphi.end());
-    if ((e = upload(&dd->face_phi32, f32.data(), f32.size())) != cudaSuccess) goto err;
-  }
+  if ((e = device_face_phi(hp, fsrc, &dd->face_phi, &dd->face_phi32)) != cudaSuccess) goto err;
   return SBM_OK;
 err:
   free_device(dd);

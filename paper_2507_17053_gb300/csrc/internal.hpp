@@ -65,6 +65,20 @@ struct ChunkTable {
   int64_t nmulti = 0;
 };
 
+// Device-built set-up tables (setup_gpu.cu).  For one chunking: the colour set
+// of every DoF (from the chunk-ordered line table `lines` on the device), the
+// list of DoFs several colours share and the per-chunk run bits, into ct.
+cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, int64_t n_dofs,
+                                const std::vector<int32_t>& ch_first,
+                                const std::vector<uint8_t>& ch_col, int R,
+                                const int32_t* first_dev, ChunkTable* ct);
+
+// The 1D Lagrange values at every shifted surrogate point (exact extension) or
+// the shift vectors (first-order Taylor), in kernel face order (fsrc[k] = the
+// face index of kernel face k), FP64 and FP32, allocated here.
+cudaError_t device_face_phi(const HostProblem& hp, const std::vector<int64_t>& fsrc,
+                            double** phi, float** phi32);
+
 // Device-resident set-up data of one problem.
 struct DeviceData {
   // cells in kernel order: for each colour (CG) -- interior cells, then cells

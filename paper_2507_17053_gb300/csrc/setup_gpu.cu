@@ -367,6 +367,185 @@ int setup_numbering_device(HostProblem* hp, int device, std::string* err) {
   return status;
 }
 
+// ---- device tables of sbm_setup_face_data -------------------------------------
+
+namespace {
+
+// per chunk-ordered cell: the DoFs of its n^d nodes get the bit of its colour
+__global__ void k_colour_masks(int64_t nc, int L, int n, const int32_t* __restrict__ lines,
+                               const uint8_t* __restrict__ col, uint32_t* __restrict__ mask) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nc * L * n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ((int64_t)L * n);
+    const int r = (int)(t - i * L * n);
+    const int64_t g = (int64_t)lines[i * L + r / n] + (r % n);
+    atomicOr(mask + g, 1u << col[i]);
+  }
+}
+
+__global__ void k_multi_flags(const uint32_t* __restrict__ mask, int64_t n, int32_t* __restrict__ flag) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n;
+       g += (int64_t)gridDim.x * blockDim.x)
+    flag[g] = (__popc(mask[g]) >= 2) ? 1 : 0;
+}
+
+__global__ void k_multi_write(const uint32_t* __restrict__ mask, const int32_t* __restrict__ flag,
+                              const int64_t* __restrict__ pos, int64_t n, int32_t* __restrict__ multi,
+                              uint8_t* __restrict__ multi_mask) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n;
+       g += (int64_t)gridDim.x * blockDim.x)
+    if (flag[g]) {
+      multi[pos[g]] = (int32_t)g;
+      multi_mask[pos[g]] = (uint8_t)mask[g];
+    }
+}
+
+// run element (l, kk) of chunk k shared by several colours -> bit l*S + kk
+__global__ void k_run_bits(int nch, int L, int P, int R, int words, const int32_t* __restrict__ first,
+                           const int32_t* __restrict__ lines, const uint32_t* __restrict__ mask,
+                           uint32_t* __restrict__ bits) {
+  const int Smax = P * R + 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nch * L * Smax;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / ((int64_t)L * Smax));
+    const int r = (int)(t - (int64_t)k * L * Smax);
+    const int l = r / Smax, kk = r - l * Smax;
+    const int S = P * (first[k + 1] - first[k]) + 1;
+    if (kk >= S) continue;
+    const int64_t g = (int64_t)lines[(int64_t)first[k] * L + l] + kk;
+    if (__popc(mask[g]) >= 2) {
+      const int b = l * S + kk;
+      atomicOr(bits + (size_t)k * words + b / 32, 1u << (b % 32));
+    }
+  }
+}
+
+struct LagArgs {
+  int n, d, L, taylor;
+  double nodes[kMaxN], lam[kMaxN];
+};
+
+// the 1D Lagrange values at each shifted point (first barycentric form, exact
+// Kronecker delta at the nodes), or (Taylor) the shift itself, in kernel face
+// order
+__global__ void k_face_phi(const LagArgs a, int64_t F, const int64_t* __restrict__ fsrc,
+                           const double* __restrict__ xi, double* __restrict__ out,
+                           float* __restrict__ out32) {
+  const int per = a.taylor ? 1 : a.n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < F * a.L * a.d;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = t / ((int64_t)a.L * a.d);
+    const int r = (int)(t - f * a.L * a.d);              // q * d + l
+    const double x = xi[(fsrc[f] * a.L) * a.d + r];
+    double* o = out + t * per;
+    float* o32 = out32 + t * per;
+    if (a.taylor) {
+      o[0] = x;
+      o32[0] = (float)x;
+      continue;
+    }
+    int hit = -1;
+    for (int j = 0; j < a.n; ++j)
+      if (x == a.nodes[j]) hit = j;
+    double l = 1.0;
+    for (int m = 0; m < a.n; ++m) l *= (x - a.nodes[m]);
+    for (int j = 0; j < a.n; ++j) {
+      const double v = (hit >= 0) ? ((j == hit) ? 1.0 : 0.0) : l * a.lam[j] / (x - a.nodes[j]);
+      o[j] = v;
+      o32[j] = (float)v;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, int64_t n_dofs,
+                                const std::vector<int32_t>& ch_first,
+                                const std::vector<uint8_t>& ch_col, int R,
+                                const int32_t* first_dev, ChunkTable* ct) {
+  DevBufs B;
+  const int nch = (int)ch_col.size();
+  std::vector<uint8_t> col(nc);
+  for (int k = 0; k < nch; ++k)
+    for (int i = ch_first[k]; i < ch_first[k + 1]; ++i) col[i] = ch_col[k];
+  uint8_t* col_d;
+  uint32_t* mask;
+  int32_t* flag;
+  int64_t *pos, *tot;
+  cudaError_t e;
+  if ((e = B.alloc(&col_d, (size_t)nc)) != cudaSuccess ||
+      (e = B.alloc(&mask, (size_t)n_dofs)) != cudaSuccess ||
+      (e = B.alloc(&flag, (size_t)n_dofs)) != cudaSuccess ||
+      (e = B.alloc(&pos, (size_t)n_dofs)) != cudaSuccess || (e = B.alloc(&tot, 1)) != cudaSuccess ||
+      (e = cudaMemcpy(col_d, col.data(), (size_t)nc, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(mask, 0, (size_t)n_dofs * 4)) != cudaSuccess)
+    return e;
+  k_colour_masks<<<grid_for(nc * L * n), 256>>>(nc, L, n, lines, col_d, mask);
+  k_multi_flags<<<grid_for(n_dofs), 256>>>(mask, n_dofs, flag);
+  if ((e = exclusive_scan(flag, n_dofs, pos, tot, B)) != cudaSuccess) return e;
+  int64_t nm = 0;
+  if ((e = cudaMemcpy(&nm, tot, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+  ct->nmulti = nm;
+  if (nm > 0) {
+    if ((e = cudaMalloc((void**)&ct->multi, (size_t)nm * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ct->multi_mask, (size_t)nm)) != cudaSuccess)
+      return e;
+    k_multi_write<<<grid_for(n_dofs), 256>>>(mask, flag, pos, n_dofs, ct->multi, ct->multi_mask);
+  }
+  const int P = n - 1;
+  const int words = (L * (P * R + 1) + 31) / 32;
+  ct->bit_words = words;
+  if ((e = cudaMalloc((void**)&ct->run_bits, (size_t)nch * words * 4)) != cudaSuccess ||
+      (e = cudaMemset(ct->run_bits, 0, (size_t)nch * words * 4)) != cudaSuccess)
+    return e;
+  k_run_bits<<<grid_for((int64_t)nch * L * (P * R + 1)), 256>>>(nch, L, P, R, words, first_dev,
+                                                                lines, mask, ct->run_bits);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaDeviceSynchronize();
+}
+
+cudaError_t device_face_phi(const HostProblem& hp, const std::vector<int64_t>& fsrc,
+                            double** phi, float** phi32) {
+  DevBufs B;
+  const int64_t F = (int64_t)fsrc.size();
+  const int d = hp.d, L = hp.L, n = hp.n;
+  const bool taylor = hp.desc.extension == SBM_EXT_TAYLOR1;
+  const size_t per = taylor ? 1 : n;
+  const size_t cnt = (size_t)F * L * d * per;
+  *phi = nullptr;
+  *phi32 = nullptr;
+  if (F == 0) return cudaSuccess;
+  const std::vector<double>& src = taylor ? hp.face_d : hp.face_xi;
+  int64_t* fsrc_d;
+  double* xi_d;
+  cudaError_t e;
+  if ((e = B.alloc(&fsrc_d, (size_t)F)) != cudaSuccess ||
+      (e = B.alloc(&xi_d, src.size())) != cudaSuccess ||
+      (e = cudaMemcpy(fsrc_d, fsrc.data(), (size_t)F * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(xi_d, src.data(), src.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMalloc((void**)phi, cnt * 8)) != cudaSuccess ||
+      (e = cudaMalloc((void**)phi32, cnt * 4)) != cudaSuccess)
+    return e;
+  LagArgs la;
+  la.n = n;
+  la.d = d;
+  la.L = L;
+  la.taylor = taylor;
+  for (int j = 0; j < kMaxN; ++j) {
+    la.nodes[j] = hp.tab.nodes[j];
+    la.lam[j] = 0.0;
+  }
+  for (int j = 0; j < n; ++j) {             // barycentric weights 1 / prod_{m != j} (x_j - x_m)
+    double prod = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != j) prod *= (hp.tab.nodes[j] - hp.tab.nodes[m]);
+    la.lam[j] = 1.0 / prod;
+  }
+  k_face_phi<<<grid_for(F * L * d), 256>>>(la, F, fsrc_d, xi_d, *phi, *phi32);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaDeviceSynchronize();
+}
+
 int setup_geometry_device(HostProblem* hp, int device, std::string* err) {
   HostProblem& P = *hp;
   const int d = P.d, N = P.N, n = P.n, Q = P.L;
