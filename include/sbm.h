@@ -351,8 +351,13 @@ int sbm_bicgstab(sbm_problem* prob, const double* b, double* x, double rtol, int
 int sbm_bicgstab_f32(sbm_problem* prob, const float* b, float* x, double rtol, int maxit,
                      int face_mode, int* iters, double* relres, void* stream);
 
-/* Inner solver of the mixed-precision refinement. */
-enum { SBM_INNER_GMRES = 0, SBM_INNER_BICGSTAB = 1 };
+/*
+ * Inner solver of the mixed-precision refinement: GMRES(restart) or BiCGStab
+ * on FP32 vectors, or BiCGStab on FP64 vectors and scalars whose operator
+ * applications alone run in FP32 (the vector converted to FP32 before and the
+ * result back to FP64 after each one).
+ */
+enum { SBM_INNER_GMRES = 0, SBM_INNER_BICGSTAB = 1, SBM_INNER_BICGSTAB_MIXED = 2 };
 
 /*
  * Mixed precision: FP64 iterative refinement (defect correction).  Each
@@ -361,9 +366,13 @@ enum { SBM_INNER_GMRES = 0, SBM_INNER_BICGSTAB = 1 };
  * face_mode, as in sbm_apply_f32) with the inner solver inner_solver:
  * GMRES(restart), or BiCGStab (restart unused) (relative tolerance
  * inner_rtol, at most inner_maxit iterations), and updates x += |r| c in
- * FP64.  Stops when |b - A x|/|b| <= rtol (FP64) or after max_outer steps.
- * *iters = FP32 inner iterations in total (a BiCGStab iteration applies the
- * operator twice), *outer = outer steps; same conventions otherwise.
+ * FP64.  Stops when |b - A x|/|b| <= rtol (FP64).  If the refinement stalls
+ * first (an inner solve without progress, or max_outer steps spent) -- the
+ * FP32 operator's rounding, about condition number x 6e-8 of |b|, limits what
+ * an inner solve can reach -- FP64 BiCGStab continues from x to rtol (at most
+ * 20000 iterations; counted as one more outer step).  *iters = inner
+ * iterations in total, including that finish (a BiCGStab iteration applies
+ * the operator twice), *outer = outer steps; same conventions otherwise.
  */
 int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int max_outer,
                  int restart, double inner_rtol, int inner_maxit, int face_mode,

@@ -246,7 +246,7 @@ def sbm_diagonal(handle: int, diag, stream=None) -> None:
 
 FACE_MODE = {"fp32": 0, "tf32": 1, "bf16": 2}
 PRECOND = {"none": 0, "jacobi": 1}
-INNER = {"gmres": 0, "bicgstab": 1}
+INNER = {"gmres": 0, "bicgstab": 1, "bicgstab_mixed": 2}
 
 
 def sbm_apply_f32(handle: int, x, y, face_mode=0, stream=None) -> None:

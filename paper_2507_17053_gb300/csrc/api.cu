@@ -573,7 +573,8 @@ int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int
   if (!prob || !b || !x || b == x) return fail(SBM_ERR_ARG, "bad vector argument");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
   if (!(rtol > 0) || max_outer < 0 || restart < 1 || restart > 1000 || !(inner_rtol > 0) ||
-      inner_maxit < 1 || (inner_solver != SBM_INNER_GMRES && inner_solver != SBM_INNER_BICGSTAB))
+      inner_maxit < 1 || (inner_solver != SBM_INNER_GMRES && inner_solver != SBM_INNER_BICGSTAB &&
+                          inner_solver != SBM_INNER_BICGSTAB_MIXED))
     return fail(SBM_ERR_ARG, "bad solver parameter");
   const int fm = check_face_mode(prob, face_mode);
   if (fm != SBM_OK) return fm;

@@ -253,6 +253,14 @@ __global__ void k_convert_scaled(TO* __restrict__ o, const TI* __restrict__ in, 
     o[i] = (TO)((double)in[i] * scale);
 }
 
+// x += s * c (FP64)
+__global__ void k_axpy_d(double* __restrict__ x, const double* __restrict__ c, double s,
+                         int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(s, c[i], x[i]);
+}
+
 // x += s * c (c in FP32, x in FP64)
 __global__ void k_add_scaled(double* __restrict__ x, const float* __restrict__ c, double s,
                              int64_t n) {
@@ -536,6 +544,7 @@ template SolveStatus solve_gmres<float, float>(const ApplyFn<float>&, int64_t, c
 // shadow residual r^ = r.
 
 constexpr int BI_CHUNK = 8;
+constexpr int kIrFinishMaxit = 20000;   // FP64 BiCGStab finish of the refinement
 
 struct BiState {
   double rho, alpha, omega, beta, rr, bb, tol2;
@@ -860,6 +869,29 @@ SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply
       return {SBM_ERR_CUDA, e};
     }
   }
+  // mixed inner solver: FP64 vectors and scalars, the FP32 apply (converted
+  // in and out around every application)
+  Bicgstab<double> bm;
+  double *r64 = nullptr, *c64 = nullptr;
+  float *xa = nullptr, *ya = nullptr;
+  ApplyFn<double> apply_mixed = [&](const double* xin, double* yout, cudaStream_t s) {
+    k_convert_scaled<float, double><<<vec_grid(n), 256, 0, s>>>(xa, xin, 1.0, n);
+    cudaError_t e = apply32(xa, ya, s);
+    if (e != cudaSuccess) return e;
+    k_convert_scaled<double, float><<<vec_grid(n), 256, 0, s>>>(yout, ya, 1.0, n);
+    return cudaGetLastError();
+  };
+  if (inner == SBM_INNER_BICGSTAB_MIXED) {
+    cudaError_t e;
+    if ((e = ws.alloc((void**)&r64, n * 8)) != cudaSuccess ||
+        (e = ws.alloc((void**)&c64, n * 8)) != cudaSuccess ||
+        (e = ws.alloc((void**)&xa, n * 4)) != cudaSuccess ||
+        (e = ws.alloc((void**)&ya, n * 4)) != cudaSuccess ||
+        (e = bm.setup(apply_mixed, n, r64, c64, ws)) != cudaSuccess) {
+      bm.destroy();
+      return {SBM_ERR_CUDA, e};
+    }
+  }
   while (outer <= maxit) {
     CK(apply64(x, r, st));
     k_residual<double><<<vec_grid(n), 256, 0, st>>>(b, r, n);
@@ -872,10 +904,27 @@ SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply
     if (!std::isfinite(relres) || outer == maxit) break;
     // inner: A32 c = r / |r| to inner_rtol, c starts at 0
     const double rn = std::sqrt(rr);
-    k_convert_scaled<float, double><<<vec_grid(n), 256, 0, st>>>(r32, r, 1.0 / rn, n);
-    CK(cudaMemsetAsync(c32, 0, n * 4, st));
     SolveInfo ii{};
     SolveStatus s;
+    if (inner == SBM_INNER_BICGSTAB_MIXED) {
+      k_convert_scaled<double, double><<<vec_grid(n), 256, 0, st>>>(r64, r, 1.0 / rn, n);
+      CK(cudaMemsetAsync(c64, 0, n * 8, st));
+      s = bm.solve(true, inner_rtol, inner_maxit, st, &ii);
+      if (s.status == SBM_ERR_CUDA) {
+        bm.destroy();
+        bi.destroy();
+        info->iters = inner_total;
+        return s;
+      }
+      inner_total += ii.iters;
+      if (s.status != SBM_OK && !(ii.relres < 1.0)) break;
+      k_axpy_d<<<vec_grid(n), 256, 0, st>>>(x, c64, rn, n);       // x += |r| c
+      CK(cudaGetLastError());
+      ++outer;
+      continue;
+    }
+    k_convert_scaled<float, double><<<vec_grid(n), 256, 0, st>>>(r32, r, 1.0 / rn, n);
+    CK(cudaMemsetAsync(c32, 0, n * 4, st));
     if (inner == SBM_INNER_BICGSTAB) {
       s = bi.solve(true, inner_rtol, inner_maxit, st, &ii);
     } else {
@@ -897,6 +946,26 @@ SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply
     ++outer;
   }
   bi.destroy();
+  bm.destroy();
+  // FP64 finish: when the reduced-precision corrections stall (an ill-conditioned
+  // operator whose FP32 rounding, about kappa * 6e-8 of |b|, floors what an
+  // inner solve can reach), BiCGStab on the FP64 operator continues from x
+  if (status != SBM_OK && std::isfinite(relres) && bnorm > 0) {
+    Bicgstab<double> bf;
+    cudaError_t e = bf.setup(apply64, n, b, x, ws);
+    SolveInfo fi{};
+    SolveStatus s{SBM_ERR_CUDA, e};
+    if (e == cudaSuccess) s = bf.solve(false, rtol, kIrFinishMaxit, st, &fi);
+    bf.destroy();
+    if (s.status == SBM_ERR_CUDA) {
+      info->iters = inner_total;
+      return s;
+    }
+    inner_total += fi.iters;
+    relres = fi.relres;
+    status = s.status;
+    ++outer;
+  }
   info->iters = inner_total;
   info->relres = relres;
   info->restarts = outer;

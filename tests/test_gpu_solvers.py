@@ -144,6 +144,25 @@ def test_bicgstab_fp32_rejects_tensor_faces_in_2d():
     assert G.STATUS[e.value.status] == "SBM_ERR_UNSUPPORTED"
 
 
+@pytest.mark.parametrize("inner,tol,maxit", [("bicgstab_mixed", 1e-2, 300),
+                                              ("bicgstab", 1e-2, 300),
+                                              ("bicgstab_mixed", 1e-6, 100)])
+def test_refinement_short_inner_solves_and_fp64_finish(inner, tol, maxit):
+    """Short inner solves (capped, loose tolerance) with FP64 vectors and FP32
+    applies, or on FP32 vectors; when they stall (the last case: 100
+    iterations never reach 1e-6) FP64 BiCGStab finishes to the FP64
+    tolerance."""
+    w = S.SPHERE_3D_Q4.resized(10, degree=2)
+    O, P, b, xref = _system(w)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    it, rr, ok, outer = G.sbm_solve_ir(P.handle, bd, x, rtol=1e-10, max_outer=60,
+                                       inner_rtol=tol, inner_maxit=maxit,
+                                       inner_solver=G.INNER[inner])
+    assert ok and rr <= 1e-10, (it, rr, outer)
+    assert np.linalg.norm(x.cpu().numpy() - xref) <= 1e-7 * np.linalg.norm(xref)
+
+
 @pytest.mark.parametrize("mode", ["fp32", "tf32", "bf16"])
 def test_mixed_precision_ir_bicgstab_inner(mode):
     """FP64 refinement around an FP32 BiCGStab inner solve reaches the FP64
