@@ -41,7 +41,7 @@ FP64_PIPE_GOPS = SMS * SM_MAX_MHZ * 1e6 * FP64_LANES_PER_SM_CLK / 1e9
 # DRAM bytes (read + write) of one launch of the FP64 cell kernel, from one
 # ncu capture per (workload, tile shape) of the kernel as it stands
 # (profiles/apply_f64_sphere3d_q4_n96_kernels.md); other shapes: not captured
-CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 1): 158.541568e6 + 135.054592e6}
+CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 1): 157.921024e6 + 135.633408e6}
 L2_BYTES = 129 * 1024 * 1024
 REF_BUDGET_S = 90.0              # wall-clock budget of the --impl reference run
 
@@ -76,10 +76,12 @@ def cell_ops(d, p, n_cells):
     """FP64/FP32 operations the cell kernel executes per apply: (FMAs, other).
 
     3D: the exact cell operator in the eigenbasis of the 1D pencil (K, M),
-    A_K = h (V x V x V) diag(lam_i + lam_j + lam_k) (V x V x V)^T: per line of
-    the tile 6 one-dimensional transforms in even/odd form, ((n+1)/2)^2 +
-    (n/2)^2 FMAs each, n products (the diagonal), and 3 folds + 3 unfolds of
-    2 (n/2) additions each (p = 4: 1950 FMAs + 725 other per cell).
+    A_K = h (V x V x V) diag(lam_i + lam_j + lam_k) (V x V x V)^T, with the
+    x-direction's transform, scaling and transform back merged into the
+    matrix h K + mu M of each x-line: per line of the tile 5 one-dimensional
+    products in even/odd form, ((n+1)/2)^2 + (n/2)^2 FMAs each, and 3 folds +
+    3 unfolds of 2 (n/2) additions each (p = 4: 1625 FMAs + 600 other per
+    cell).
     2D: 4 one-dimensional matrix applications per line (Algorithm 1 in
     tensor-product form), even/odd split for n >= 5 with 3 folds and 3
     unfolds per line pair."""
@@ -87,8 +89,8 @@ def cell_ops(d, p, n_cells):
     lines = n ** (d - 1)
     h, he = n // 2, (n + 1) // 2
     if d == 3:
-        fma = 6 * (he * he + h * h)
-        other = n + 12 * h
+        fma = 5 * (he * he + h * h)
+        other = 12 * h
     elif n >= 5:
         fma = 4 * (he * he + h * h)
         other = 6 * 2 * h

@@ -146,7 +146,9 @@ struct ChunkSmem {
   static constexpr int TILE = (D == 3) ? R * ND : 2 * R * ND;  // scalars before the runs
   static constexpr int XS = (D == 3) ? L * SM : XZ;
   static constexpr int WORDS = (L * SM + 31) / 32;              // run-element bits
-  static constexpr size_t bytes = (size_t)(TILE + XS) * sizeof(T) + (size_t)(L + WORDS) * 4;
+  static constexpr int XL = (D == 3) ? L * XLineOp<T, N>::kSize : 0;  // x-line operators
+  static constexpr size_t bytes =
+      (size_t)(TILE + XS + XL) * sizeof(T) + (size_t)(L + WORDS) * 4;
 };
 
 template <typename T, int D, int N, int R>
@@ -164,15 +166,15 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   // per-cell results, node (j0, j1, j2) of cell c at c ND + j0 + n j1 + n^2 j2
   // (3D: the tile; 2D: the run area, free after the first phase)
   T* Z = (D == 3) ? tile : Xs;
-  int* Ls = reinterpret_cast<int*>(Xs + CS::XS);            // [L] run starts
+  T* XLs = Xs + CS::XS;                                      // 3D: [L] x-line operators
+  int* Ls = reinterpret_cast<int*>(XLs + CS::XL);            // [L] run starts
   uint32_t* Bs = reinterpret_cast<uint32_t*>(Ls + L);        // run-element bits
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
-  // 3D: h (lam_i + lam_a + lam_b) for this thread's x-line of modes (a, b)
-  T sc[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    sc[i] = (D == 3) ? (t.hlam[i] + t.hlam[tl % N]) + t.hlam[tl / N] : T(0);
+  // 3D: h K + mu M for the x-line of modes (a, b) = (tl % n, tl / n), in
+  // shared memory (visible after the first chunk's first barrier)
+  if (D == 3 && c == 0) XLineOp<T, N>(t, tl % N, tl / N).store(XLs + tl * XLineOp<T, N>::kSize);
+  const XLineShared<T, N> xop{XLs + tl * XLineOp<T, N>::kSize};
   const T* __restrict__ xr = a.x + blockIdx.y * a.ldx;
   const T* fo = a.face_out + blockIdx.y * a.ld_face;
   T* ycb = a.ycol + blockIdx.y * a.ld_ycol;
@@ -203,7 +205,7 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
     const bool act = c < nc;
     T out[N];
     if constexpr (D == 3)
-      cell_fd_3d<T, N>(t, Xs, (tl / N) * SM + P * c + (tl % N), N * SM, tile, c, tl, act, sc,
+      cell_fd_3d<T, N>(t, Xs, (tl / N) * SM + P * c + (tl % N), N * SM, tile, c, tl, act, xop,
                        out);
     else
       cell_sweeps_2d<T, N>(t, Xs, P * c + tl, SM, AE, c, tl, act, out);

@@ -75,10 +75,8 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
     // phase read; 2D the x-line tl, once every thread is past the sweeps
     T out[N];
     if constexpr (D == 3) {
-      T sc[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) sc[i] = (t.hlam[i] + t.hlam[tl % N]) + t.hlam[tl / N];
-      cell_fd_3d<T, N>(t, X, c * ND + tl, N * N, A, c, tl, act, sc, out);
+      const XLineOp<T, N> xop(t, tl % N, tl / N);
+      cell_fd_3d<T, N>(t, X, c * ND + tl, N * N, A, c, tl, act, xop, out);
       if (act) {
 #pragma unroll
         for (int m = 0; m < N; ++m) R[tl + N * N * m] = out[m];

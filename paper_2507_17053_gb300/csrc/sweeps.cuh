@@ -7,7 +7,7 @@
 // with the exact 1D mass M and stiffness K on [0,1], instead of the 4d
 // sweeps of interpolate / differentiate / integrate.  2D: 4 one-dimensional
 // sweeps, a = M_y u, e = K_y u;  y = K_x a + M_x e.  3D: the eigenbasis form
-// below (5 phases, 6 transforms per line).  Each thread owns one line of the
+// below (5 phases, 5 even/odd products per line).  Each thread owns one line of the
 // (p+1)^d tile per phase (registers); the tile is staged in shared memory
 // between phases.
 #pragma once
@@ -190,21 +190,91 @@ __device__ __forceinline__ void modes_to_line(const Folded<T>& V, const T (&w)[N
 //
 // With M = V V^T and K = V diag(lam) V^T (the generalised eigenvectors of
 // (K, M), scaled), the exact cell operator factors as
-//   A_K = h (V x V x V) diag(lam_i + lam_j + lam_k) (V x V x V)^T,
-// five line phases over one scalar tile per cell, in place (a thread reads
-// its line, then writes the same nodes): z-lines to z-modes, y-lines to
-// y-modes, x-lines to x-modes / scale / back, y-modes back, z-modes back.
-// Every 1D transform is an even/odd split product (V's columns are even or
-// odd), so a line costs 6 (ceil(n/2)^2 + floor(n/2)^2) FMAs, n products and
-// 3 folds + 3 unfolds of 2 floor(n/2) additions each -- 107 operations per
+//   A_K = h (V x V x V) diag(lam_i + lam_j + lam_k) (V x V x V)^T.
+// After the z- and y-transforms, the x-line of y-mode a and z-mode b needs
+//   V diag(h lam_i + h lam_a + h lam_b) V^T = h K + mu_ab M,  mu_ab = h (lam_a + lam_b),
+// a symmetric matrix of the 1D pencil that is applied directly (XLineOp)
+// instead of a transform, a scaling and a transform back.  Five line phases
+// over one scalar tile per cell, in place (a thread reads its line, then
+// writes the same nodes): z-lines to z-modes, y-lines to y-modes, x-lines
+// through h K + mu_ab M, y-modes back, z-modes back.  Every 1D product is an
+// even/odd split product (V's columns are even or odd, K and M are
+// centrosymmetric), so a line costs 5 (ceil(n/2)^2 + floor(n/2)^2) FMAs and
+// 6 folds or unfolds of 2 floor(n/2) additions each -- 89 operations per
 // line at p = 4, against 131 for the 7-sweep form.  Tile layout: node (j0, j1, j2) at
 // j0 + n j1 + n^2 j2.  The z-line (j0, j1) = line tl of cell c is read from
-// X[xb + xs * j2]; sc[i] = h (lam_i + lam_a + lam_b) for the thread's
-// x-line of modes (a, b) = (tl % n, tl / n).  The z-line result of line tl is
-// returned in out[] (nodal, j2 = 0..n-1); the tile then holds nothing useful.
+// X[xb + xs * j2]; xop is h K + mu_ab M for the thread's x-line of modes
+// (a, b) = (tl % n, tl / n).  The z-line result of line tl is returned in
+// out[] (nodal, j2 = 0..n-1); the tile then holds nothing useful.
+
+// h K + mu M in even/odd form (both blocks symmetric), built once per thread.
 template <typename T, int N>
+struct XLineOp {
+  static constexpr int H = N / 2, HE = (N + 1) / 2;
+  T E[HE][HE];
+  T O[H > 0 ? H : 1][H > 0 ? H : 1];
+  __device__ __forceinline__ XLineOp(const KTab<T>& t, int a, int b) {
+    const T mu = t.hlam[a] + t.hlam[b];
+#pragma unroll
+    for (int i = 0; i < HE; ++i)
+#pragma unroll
+      for (int j = i; j < HE; ++j) E[i][j] = E[j][i] = fma(mu, t.fM.E[i][j], t.fKh.E[i][j]);
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+#pragma unroll
+      for (int j = i; j < H; ++j) O[i][j] = O[j][i] = fma(mu, t.fM.O[i][j], t.fKh.O[i][j]);
+  }
+  __device__ __forceinline__ void apply(const T (&v)[N], T (&y)[N]) const {
+    const LineFold<T, N> f(v);
+    LineAcc<T, N> acc;
+#pragma unroll
+    for (int i = 0; i < HE; ++i)
+#pragma unroll
+      for (int j = 0; j < HE; ++j) acc.s[i] = fma(E[i][j], f.e[j], acc.s[i]);
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+#pragma unroll
+      for (int j = 0; j < H; ++j) acc.d[i] = fma(O[i][j], f.o[j], acc.d[i]);
+    acc.unfold(y);
+  }
+  static constexpr int kSize = HE * HE + H * H;   // scalars of one line's operator
+  // into shared memory (E row-major, then O), for XLineShared
+  __device__ __forceinline__ void store(T* m) const {
+#pragma unroll
+    for (int i = 0; i < HE; ++i)
+#pragma unroll
+      for (int j = 0; j < HE; ++j) m[i * HE + j] = E[i][j];
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+#pragma unroll
+      for (int j = 0; j < H; ++j) m[HE * HE + i * H + j] = O[i][j];
+  }
+};
+
+// The same operator read from shared memory at each use (no registers held
+// across the kernel).
+template <typename T, int N>
+struct XLineShared {
+  static constexpr int H = N / 2, HE = (N + 1) / 2;
+  const T* m;
+  __device__ __forceinline__ void apply(const T (&v)[N], T (&y)[N]) const {
+    const LineFold<T, N> f(v);
+    LineAcc<T, N> acc;
+#pragma unroll
+    for (int i = 0; i < HE; ++i)
+#pragma unroll
+      for (int j = 0; j < HE; ++j) acc.s[i] = fma(m[i * HE + j], f.e[j], acc.s[i]);
+#pragma unroll
+    for (int i = 0; i < H; ++i)
+#pragma unroll
+      for (int j = 0; j < H; ++j) acc.d[i] = fma(m[HE * HE + i * H + j], f.o[j], acc.d[i]);
+    acc.unfold(y);
+  }
+};
+
+template <typename T, int N, typename XOp>
 __device__ __forceinline__ void cell_fd_3d(const KTab<T>& t, const T* X, int xb, int xs, T* tile,
-                                           int c, int tl, bool act, const T (&sc)[N],
+                                           int c, int tl, bool act, const XOp& xop,
                                            T (&out)[N]) {
   constexpr int L = N * N, ND = L * N;
   const int a = tl % N, b = tl / N;
@@ -227,14 +297,11 @@ __device__ __forceinline__ void cell_fd_3d(const KTab<T>& t, const T* X, int xb,
     for (int k = 0; k < N; ++k) cell[a + N * k + L * b] = w[k];
   }
   __syncthreads();
-  if (act) {                       // x-lines (y-mode a, z-mode b): modes, scale, back
-    T v[N], w[N], y[N];
+  if (act) {                       // x-lines (y-mode a, z-mode b): h K + mu_ab M
+    T v[N], y[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = cell[N * tl + j];
-    line_to_modes<T, N>(t.fVt, v, w);
-#pragma unroll
-    for (int i = 0; i < N; ++i) w[i] *= sc[i];
-    modes_to_line<T, N>(t.fV, w, y);
+    xop.apply(v, y);
 #pragma unroll
     for (int j = 0; j < N; ++j) cell[N * tl + j] = y[j];
   }
