@@ -196,7 +196,13 @@ int sbm_apply_f64(sbm_problem* prob, const double* x, double* y, void* stream);
  * Same as sbm_apply_f64 with host arrays: copies x to the device, applies,
  * copies y back and synchronises the stream before returning (the path a
  * caller without device buffers takes; the staging buffers are allocated
- * once per problem on first use).
+ * once per problem on first use).  Continuous Galerkin problems run it as a
+ * pipeline over slabs of whole cell layers along the last axis: the copy of
+ * the next slab's part of x, the current slab's kernels (its faces beside
+ * the previous slab's cells) and the copy of the part of y the slab
+ * completes overlap, on streams of the problem ordered after the caller's
+ * stream.  The result is bitwise that of sbm_apply_f64.  Page-locked host
+ * arrays let the copies run concurrently with the kernels.
  */
 int sbm_apply_f64_host(sbm_problem* prob, const double* x_host, double* y_host, void* stream);
 

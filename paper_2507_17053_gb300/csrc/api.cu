@@ -1,5 +1,7 @@
 // C ABI of the SBM operator library (declarations and contracts in include/sbm.h).
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -136,6 +138,17 @@ static void free_device(DeviceData* dd) {
   cudaFree(dd->nbr);
   cudaFree(dd->stage_x);
   cudaFree(dd->stage_y);
+  for (cudaEvent_t ev : dd->ev_in)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : dd->ev_face)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : dd->ev_done)
+    if (ev) cudaEventDestroy(ev);
+  if (dd->face_st) cudaStreamDestroy(dd->face_st);
+  if (dd->ev_fork) cudaEventDestroy(dd->ev_fork);
+  if (dd->ev_join) cudaEventDestroy(dd->ev_join);
+  if (dd->copy_in) cudaStreamDestroy(dd->copy_in);
+  if (dd->copy_out) cudaStreamDestroy(dd->copy_out);
   *dd = DeviceData();
 }
 
@@ -218,6 +231,64 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   }
   fstart[Nc] = (int32_t)fkind.size();
 
+  // CG: slabs of the pipelined host-buffer apply -- whole cell layers along
+  // the last axis (cells are ordered layer by layer, the DoF numbering is
+  // monotone in the lattice plane along that axis), cut where the cell count
+  // first reaches each share of kSlabCuts
+  std::vector<int64_t> ycut{0, hp.n_dofs};
+  std::vector<int> slab_cell{0, (int)Nc};
+  if (!hp.desc.dg) {
+    const int N = hp.N, p = hp.p, dl = d - 1;
+    const int64_t M = (int64_t)p * N + 1;                 // lattice planes
+    std::vector<int64_t> per(N, 0);
+    for (int64_t i = 0; i < Nc; ++i) per[hp.cells[(int64_t)dd->order[i] * d + dl]]++;
+    std::vector<int> zb{0};
+    int64_t cum = 0, last = 0;
+    const int ncut = (int)(sizeof(kSlabCuts) / sizeof(kSlabCuts[0]));
+    for (int z = 0, k = 0; z + 1 < N && k < ncut; ++z) {
+      cum += per[z];
+      if (cum > last && (double)cum >= kSlabCuts[k] * (double)Nc) {
+        zb.push_back(z + 1);
+        last = cum;
+        while (k < ncut && (double)cum >= kSlabCuts[k] * (double)Nc) ++k;
+      }
+    }
+    zb.push_back(N);
+    // first DoF of each lattice plane (of the next non-empty one if empty)
+    std::vector<int64_t> pf(M + 1, INT64_MAX);
+    pf[M] = hp.n_dofs;
+    for (int64_t c = 0; c < Nc; ++c) {
+      const int64_t cz = hp.cells[c * d + dl];
+      for (int line = 0; line < L; ++line) {
+        const int64_t kz = p * cz + ((d == 3) ? line / n : line);
+        pf[kz] = std::min<int64_t>(pf[kz], hp.lines[c * L + line]);
+      }
+    }
+    for (int64_t kz = M - 1; kz >= 0; --kz) pf[kz] = std::min(pf[kz], pf[kz + 1]);
+    const int ns = (int)zb.size() - 1;
+    dd->nslab = ns;
+    ycut.assign(ns + 1, hp.n_dofs);
+    slab_cell.assign(ns + 1, (int)Nc);
+    dd->slab_x.assign(ns, hp.n_dofs);
+    int64_t before = 0;
+    for (int s = 0, z = 0; s < ns; ++s) {
+      for (; z < zb[s]; ++z) before += per[z];
+      slab_cell[s] = (int)before;
+      ycut[s] = pf[(int64_t)p * zb[s]];
+      dd->slab_x[s] = pf[std::min<int64_t>((int64_t)p * zb[s + 1] + 1, M)];
+    }
+    dd->slab_y = ycut;
+    dd->slab_face.assign(ns + 1, 0);
+    for (int s = 0; s <= ns; ++s) dd->slab_face[s] = fstart[slab_cell[s]];
+    for (int v = 0; v < 2; ++v) {
+      dd->chunks[v].slab_chunk.assign(ns + 1, 0);
+      for (int s = 0; s <= ns; ++s)
+        dd->chunks[v].slab_chunk[s] =
+            (int)(std::lower_bound(ch_first[v].begin(), ch_first[v].end(), slab_cell[s]) -
+                  ch_first[v].begin());
+    }
+  }
+
   std::vector<int32_t> nbr;
   if (hp.desc.dg) {
     nbr.assign(Nc * 2 * d, -1);
@@ -254,7 +325,7 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
         goto err;
       const int R = v == 0 ? chunk_cells(d, n) : std::max(chunk_cells(d, n) / 2, 1);
       if ((e = device_chunk_tables(dd->lines, Nc, L, n, hp.n_dofs, ch_first[v], ch_col[v], R,
-                                   dd->chunks[v].first, &dd->chunks[v])) != cudaSuccess)
+                                   dd->chunks[v].first, ycut, &dd->chunks[v])) != cudaSuccess)
         goto err;
     }
     // ordered positions grouped by the parity colour of the cell (diagonal kernel)
@@ -286,6 +357,24 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
       goto err;
   }
   if ((e = device_face_phi(hp, fsrc, &dd->face_phi, &dd->face_phi32)) != cudaSuccess) goto err;
+  if (dd->nslab > 1) {
+    // copy streams and events of the pipelined host-buffer apply
+    const unsigned fl = cudaEventDisableTiming;
+    if ((e = cudaStreamCreateWithFlags(&dd->copy_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&dd->copy_out, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&dd->face_st, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&dd->ev_fork, fl)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&dd->ev_join, fl)) != cudaSuccess)
+      goto err;
+    dd->ev_in.assign(dd->nslab, nullptr);
+    dd->ev_face.assign(dd->nslab, nullptr);
+    dd->ev_done.assign(dd->nslab, nullptr);
+    for (int s = 0; s < dd->nslab; ++s)
+      if ((e = cudaEventCreateWithFlags(&dd->ev_in[s], fl)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&dd->ev_face[s], fl)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&dd->ev_done[s], fl)) != cudaSuccess)
+        goto err;
+  }
   return SBM_OK;
 err:
   free_device(dd);
@@ -420,12 +509,57 @@ int sbm_apply_f64_host(sbm_problem* prob, const double* x_host, double* y_host, 
     if ((e = cudaMalloc((void**)&dd.stage_y, bytes)) != cudaSuccess) return cuda_fail(e, "stage");
   }
   cudaStream_t st = (cudaStream_t)stream;
-  if ((e = cudaMemcpyAsync(dd.stage_x, x_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-    return cuda_fail(e, "H2D");
-  int s = sbm_apply_f64(prob, dd.stage_x, dd.stage_y, stream);
-  if (s != SBM_OK) return s;
-  if ((e = cudaMemcpyAsync(y_host, dd.stage_y, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-    return cuda_fail(e, "D2H");
+  if (dd.nslab > 1) {
+    // pipelined by slabs: the copy of x in, the slabs' kernels and the copy
+    // of the finished parts of y out overlap
+    if ((e = cudaEventRecord(dd.ev_fork, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(dd.copy_in, dd.ev_fork, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(dd.face_st, dd.ev_fork, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(dd.copy_out, dd.ev_fork, 0)) != cudaSuccess)
+      return cuda_fail(e, "fork");
+    int64_t xdone = 0;
+    for (int s = 0; s < dd.nslab; ++s) {
+      const int64_t x1 = dd.slab_x[s], y0 = dd.slab_y[s], y1 = dd.slab_y[s + 1];
+      if (x1 > xdone &&
+          (e = cudaMemcpyAsync(dd.stage_x + xdone, x_host + xdone, (size_t)(x1 - xdone) * 8,
+                               cudaMemcpyHostToDevice, dd.copy_in)) != cudaSuccess)
+        return cuda_fail(e, "H2D");
+      xdone = std::max(xdone, x1);
+      if ((e = cudaEventRecord(dd.ev_in[s], dd.copy_in)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(dd.face_st, dd.ev_in[s], 0)) != cudaSuccess)
+        return cuda_fail(e, "event");
+      if ((e = launch_cg_apply_slab(prob->hp, dd, dd.stage_x, dd.stage_y, s, 1, dd.face_st)) !=
+          cudaSuccess)
+        return cuda_fail(e, "sbm_apply_f64_host");
+      // the chunks of slab s wait for its faces (and so for its part of x)
+      if ((e = cudaEventRecord(dd.ev_face[s], dd.face_st)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(st, dd.ev_face[s], 0)) != cudaSuccess)
+        return cuda_fail(e, "event");
+      if ((e = launch_cg_apply_slab(prob->hp, dd, dd.stage_x, dd.stage_y, s, 2, st)) !=
+          cudaSuccess)
+        return cuda_fail(e, "sbm_apply_f64_host");
+      if ((e = cudaEventRecord(dd.ev_done[s], st)) != cudaSuccess ||
+          (e = cudaStreamWaitEvent(dd.copy_out, dd.ev_done[s], 0)) != cudaSuccess)
+        return cuda_fail(e, "event");
+      if (y1 > y0 &&
+          (e = cudaMemcpyAsync(y_host + y0, dd.stage_y + y0, (size_t)(y1 - y0) * 8,
+                               cudaMemcpyDeviceToHost, dd.copy_out)) != cudaSuccess)
+        return cuda_fail(e, "D2H");
+    }
+    if ((e = cudaEventRecord(dd.ev_join, dd.copy_out)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, dd.ev_join, 0)) != cudaSuccess)
+      return cuda_fail(e, "join");
+    // (face_st's work ends before the last slab's chunks, which copy_out waited for)
+  } else {
+    if ((e = cudaMemcpyAsync(dd.stage_x, x_host, bytes, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "H2D");
+    int s = sbm_apply_f64(prob, dd.stage_x, dd.stage_y, stream);
+    if (s != SBM_OK) return s;
+    if ((e = cudaMemcpyAsync(y_host, dd.stage_y, bytes, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "D2H");
+  }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
   return SBM_OK;
 }

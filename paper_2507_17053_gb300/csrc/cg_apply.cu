@@ -56,7 +56,7 @@ struct ChunkArgs {
   const int32_t* __restrict__ chunk_first; // [nchunk + 1] first ordered cell of each chunk
   const uint8_t* __restrict__ chunk_col;   // [nchunk] colour of each chunk
   int64_t n_dofs;
-  int nchunk;
+  int q0, q1;                              // this launch: chunks [q0, q1)
   // right-hand side blockIdx.y of a multi-RHS launch: offsets of its x and y,
   // its colour buffers and its face results (0 for a single right-hand side)
   int64_t ldx, ld_ycol, ld_face;
@@ -180,7 +180,7 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   T* ycb = a.ycol + blockIdx.y * a.ld_ycol;
   T* yb = a.y + blockIdx.y * a.ldx;
 
-  for (int ch = blockIdx.x; ch < a.nchunk; ch += gridDim.x) {
+  for (int ch = a.q0 + blockIdx.x; ch < a.q1; ch += gridDim.x) {
     const int first = __ldg(a.chunk_first + ch);
     const int nc = __ldg(a.chunk_first + ch + 1) - first;
     const int S = P * nc + 1;                 // values per x-line run
@@ -247,10 +247,12 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
 }
 
 // For the DoFs i = multi[t] that several colours touch:
-// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order (the lowest
-// colour's value is loaded, the others are added to it).  The loop over the
-// further colours is warp-uniform (on GB300 a double addition costs an
-// FP64-pipe slot per warp instruction, whatever its active lanes).
+// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order.  Lane
+// slot j holds the value of the lane's j-th colour (0 past its count); the
+// additions run over the slots up to the warp's largest colour count (on
+// GB300 a double addition costs an FP64-pipe slot per warp instruction,
+// whatever its active lanes, and the list is grouped by colour count, so
+// that count is the warp's own).  Adding a slot's 0 leaves a sum unchanged.
 template <typename T>
 __global__ void assemble_kernel(const T* __restrict__ ycol, const int32_t* __restrict__ multi,
                                 const uint8_t* __restrict__ multi_mask, T* __restrict__ y,
@@ -266,18 +268,20 @@ __global__ void assemble_kernel(const T* __restrict__ ycol, const int32_t* __res
     m = (unsigned)__ldg(multi_mask + t);
   }
   if (ncol < 8) m &= (1u << ncol) - 1u;
+  const unsigned kmax = __reduce_max_sync(0xffffffffu, (unsigned)__popc(m));
   // all loads first (independent), then the sum
   T v[8];
+  unsigned r = m;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) v[c] = ((m >> c) & 1u) ? __ldcs(ycol + (size_t)c * n + i) : T(0);
-  const unsigned c0 = m ? (unsigned)(__ffs(m) - 1) : 0u;
-  T acc = T(0);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    if (c == (int)c0) acc = ((m >> c) & 1u) ? v[c] : acc;
-    if (__any_sync(0xffffffffu, ((m >> c) & 1u) && c != (int)c0))
-      acc += (c != (int)c0) ? v[c] : T(0);
+  for (int j = 0; j < 8; ++j) {
+    const int c = __ffs(r) - 1;
+    v[j] = r ? __ldcs(ycol + (size_t)c * n + i) : T(0);
+    r &= r - 1u;
   }
+  T acc = v[0];
+#pragma unroll
+  for (int j = 1; j < 8; ++j)
+    if ((unsigned)j < kmax) acc += v[j];
   if (t < nmulti) __stcs(y + i, acc);
 }
 
@@ -305,21 +309,34 @@ static cudaError_t chunk_prepare(int* grid_cap) {
   return attr;
 }
 
+// Which part of the operator one apply_r call runs: surrogate faces
+// [f0, f1), chunks [q0, q1), shared DoFs [m0, m1) of the assembly list (all:
+// f1 = q1 = m1 = -1).
+struct Part {
+  int f0 = 0, f1 = -1, q0 = 0, q1 = -1;
+  int64_t m0 = 0, m1 = -1;
+};
+
 // face stage + chunk kernel + assembly, with explicit scratch and nrhs
 // right-hand sides (x, y: nrhs vectors ld apart).
 template <typename T, int D, int N, int R>
 static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const ChunkTable& ct,
                            const T* x, T* y, int64_t ld, int nrhs, T* fo, T* ycol, int face_mode,
-                           cudaStream_t st, Profiler* prof) {
+                           cudaStream_t st, Profiler* prof, Part part) {
   constexpr int L = Shape<D, N>::L;
   const KTab<T> t = make_ktab<T>(hp);
   constexpr size_t smem = ChunkSmem<T, D, N, R>::bytes;
+  if (part.f1 < 0) part.f1 = dd.nface;
+  if (part.q1 < 0) part.q1 = ct.n;
+  if (part.m1 < 0) part.m1 = ct.nmulti;
   cudaError_t err;
   const bool pr = prof && prof->on;
   int nlaunch = 0;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
-  if (dd.nface > 0) {
-    err = (nrhs == 1) ? launch_faces<T>(hp, dd, x, fo, face_mode, st)
+  if (part.f1 > part.f0) {
+    err = (nrhs == 1) ? (face_mode != 0 ? launch_faces<T>(hp, dd, x, fo, face_mode, st)
+                                        : launch_face_kernel<T>(hp, dd, x, fo, st, part.f0,
+                                                                part.f1))
                       : launch_face_kernel_multi<T>(hp, dd, x, ld, nrhs, fo, st);
     if (err != cudaSuccess) return err;
     nlaunch++;
@@ -340,19 +357,22 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   a.chunk_first = ct.first;
   a.chunk_col = ct.colour;
   a.n_dofs = hp.n_dofs;
-  a.nchunk = ct.n;
+  a.q0 = part.q0;
+  a.q1 = part.q1;
   a.ldx = ld;
   a.ld_ycol = (int64_t)dd.ncolours * hp.n_dofs;
   a.ld_face = (int64_t)dd.nface * 2 * L;
-  const int grid = std::min(ct.n, cap);
-  cg_chunk_kernel<T, D, N, R><<<dim3(grid, nrhs), R * L, smem, st>>>(a, t);
-  nlaunch++;
+  if (part.q1 > part.q0) {
+    const int grid = std::min(part.q1 - part.q0, cap);
+    cg_chunk_kernel<T, D, N, R><<<dim3(grid, nrhs), R * L, smem, st>>>(a, t);
+    nlaunch++;
+  }
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
-  const int64_t n = hp.n_dofs;
-  if (ct.nmulti > 0) {
-    assemble_kernel<T><<<dim3((unsigned)((ct.nmulti + 255) / 256), nrhs), 256, 0, st>>>(
-        ycol, ct.multi, ct.multi_mask, y, n, ct.nmulti, dd.ncolours, (int64_t)dd.ncolours * n,
-        ld);
+  const int64_t n = hp.n_dofs, nm = part.m1 - part.m0;
+  if (nm > 0) {
+    assemble_kernel<T><<<dim3((unsigned)((nm + 255) / 256), nrhs), 256, 0, st>>>(
+        ycol, ct.multi + part.m0, ct.multi_mask + part.m0, y, n, nm, dd.ncolours,
+        (int64_t)dd.ncolours * n, ld);
     nlaunch++;
   }
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -369,23 +389,35 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
 template <typename T, int D, int N>
 static cudaError_t apply_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                            int64_t ld, int nrhs, T* fo, T* ycol, int face_mode, int variant,
-                           cudaStream_t st, Profiler* prof) {
+                           cudaStream_t st, Profiler* prof, int slab, int stages) {
   constexpr int R = ChunkShape<D, N>::R;
   constexpr int RH = (R / 2) > 0 ? R / 2 : 1;
-  if (variant == 1 && RH < R)
-    return apply_r<T, D, N, RH>(hp, dd, dd.chunks[1], x, y, ld, nrhs, fo, ycol, face_mode, st,
-                                prof);
-  return apply_r<T, D, N, R>(hp, dd, dd.chunks[0], x, y, ld, nrhs, fo, ycol, face_mode, st,
-                             prof);
+  const int v = (variant == 1 && RH < R) ? 1 : 0;
+  const ChunkTable& ct = dd.chunks[v];
+  Part part;
+  if (slab >= 0) {
+    const bool faces = stages & 1, cells = stages & 2;
+    part.f0 = dd.slab_face[slab];
+    part.f1 = faces ? dd.slab_face[slab + 1] : part.f0;
+    part.q0 = ct.slab_chunk[slab];
+    part.q1 = cells ? ct.slab_chunk[slab + 1] : part.q0;
+    part.m0 = ct.slab_multi[slab];
+    part.m1 = cells ? ct.slab_multi[slab + 1] : part.m0;
+  }
+  if (v == 1)
+    return apply_r<T, D, N, RH>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part);
+  return apply_r<T, D, N, R>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part);
 }
 
 template <typename T>
 static cudaError_t dispatch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                             int64_t ld, int nrhs, T* fo, T* ycol, int face_mode, int variant,
-                            cudaStream_t st, Profiler* prof) {
+                            cudaStream_t st, Profiler* prof, int slab = -1,
+                            int stages = 3) {
 #define SBM_CASE(DD, NN)                                                                  \
   if (hp.d == DD && hp.n == NN)                                                           \
-    return apply_t<T, DD, NN>(hp, dd, x, y, ld, nrhs, fo, ycol, face_mode, variant, st, prof);
+    return apply_t<T, DD, NN>(hp, dd, x, y, ld, nrhs, fo, ycol, face_mode, variant, st, prof, \
+                              slab, stages);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE
@@ -403,6 +435,16 @@ template cudaError_t launch_cg_apply<double>(const HostProblem&, const DeviceDat
                                              int);
 template cudaError_t launch_cg_apply<float>(const HostProblem&, const DeviceData&, const float*,
                                             float*, cudaStream_t, Profiler*, int);
+
+// Slab s of the FP64 apply (the pipelined host-buffer apply): stages 1 =
+// the surrogate faces of the cells of slab s, 2 = their chunks and the shared
+// DoFs the slab completes; after both, y is final on the DoFs [slab_y[s],
+// slab_y[s+1]) given x on [0, slab_x[s]).
+cudaError_t launch_cg_apply_slab(const HostProblem& hp, const DeviceData& dd, const double* x,
+                                 double* y, int slab, int stages, cudaStream_t st) {
+  return dispatch<double>(hp, dd, x, y, 0, 1, dd.face_out, dd.ycol, 0, dd.variant[0], st,
+                          nullptr, slab, stages);
+}
 
 // The same launches with caller-provided scratch: per-face results
 // ([F][2L]) and colour buffers ([ncolours][n_dofs]).

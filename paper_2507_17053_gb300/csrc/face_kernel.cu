@@ -32,7 +32,7 @@ struct FaceArgs {
   const int32_t* __restrict__ face_kind;   // k | (s << 2)
   const T* __restrict__ face_phi;          // [F][L][D][N], or the shifts [F][L][D] (Taylor)
   T* __restrict__ out;                     // [F][2L]
-  int nface;
+  int face0, nface;                        // this launch: faces [face0, nface)
   int dg;
   int64_t ldx, ld_out;                     // right-hand side blockIdx.y offsets
 };
@@ -54,7 +54,7 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
   T* X = reinterpret_cast<T*>(smem_raw);
   T* SC = X + FPB * ND;            // NS L per face
   const int tid = threadIdx.x;
-  const int f0 = blockIdx.x * FPB;
+  const int f0 = a.face0 + blockIdx.x * FPB;
   const int nf = min(FPB, a.nface - f0);
   for (int r = tid; r < nf * ND; r += blockDim.x) {
     const int f = r / ND, loc = r - f * ND;
@@ -246,9 +246,9 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
 
 template <typename T, int D, int N, int EXT>
 static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
-                          cudaStream_t st, int64_t ldx = 0, int nrhs = 1) {
+                          cudaStream_t st, int64_t ldx, int nrhs, int fb, int fe) {
   constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, FPB = Shape<D, N>::CPB;
-  if (dd.nface == 0) return cudaSuccess;
+  if (fe <= fb) return cudaSuccess;
   const KTab<T> t = make_ktab<T>(hp);
   FaceArgs<T> a;
   a.x = x;
@@ -258,35 +258,38 @@ static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* 
   a.face_kind = dd.face_kind;
   a.face_phi = face_phi_of<T>(dd);
   a.out = out;
-  a.nface = dd.nface;
+  a.face0 = fb;
+  a.nface = fe;
   a.dg = hp.desc.dg;
   a.ldx = ldx;
   a.ld_out = (int64_t)dd.nface * 2 * L;
   const size_t smem = (size_t)(FPB * ND + FPB * FaceScratch<EXT>::n * L) * sizeof(T);
-  sface_kernel<T, D, N, EXT><<<dim3((dd.nface + FPB - 1) / FPB, nrhs), FPB * L, smem, st>>>(a, t);
+  sface_kernel<T, D, N, EXT><<<dim3((fe - fb + FPB - 1) / FPB, nrhs), FPB * L, smem, st>>>(a, t);
   return cudaGetLastError();
 }
 
 template <typename T, int D, int N>
 static cudaError_t face_x(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
-                          cudaStream_t st, int64_t ldx = 0, int nrhs = 1) {
+                          cudaStream_t st, int64_t ldx = 0, int nrhs = 1, int fb = 0,
+                          int fe = -1) {
+  if (fe < 0) fe = dd.nface;
   return hp.desc.extension == SBM_EXT_TAYLOR1
-             ? face_t<T, D, N, 1>(hp, dd, x, out, st, ldx, nrhs)
-             : face_t<T, D, N, 0>(hp, dd, x, out, st, ldx, nrhs);
+             ? face_t<T, D, N, 1>(hp, dd, x, out, st, ldx, nrhs, fb, fe)
+             : face_t<T, D, N, 0>(hp, dd, x, out, st, ldx, nrhs, fb, fe);
 }
 
 template <typename T>
 cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
-                               cudaStream_t st) {
+                               cudaStream_t st, int fb, int fe) {
 #define SBM_CASE(DD, NN) \
-  if (hp.d == DD && hp.n == NN) return face_x<T, DD, NN>(hp, dd, x, out, st);
+  if (hp.d == DD && hp.n == NN) return face_x<T, DD, NN>(hp, dd, x, out, st, 0, 1, fb, fe);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE
   return cudaErrorInvalidValue;
 }
 template cudaError_t launch_face_kernel<double>(const HostProblem&, const DeviceData&,
-                                                const double*, double*, cudaStream_t);
+                                                const double*, double*, cudaStream_t, int, int);
 
 template <typename T>
 cudaError_t launch_face_kernel_multi(const HostProblem& hp, const DeviceData& dd, const T* x,
@@ -305,6 +308,6 @@ template cudaError_t launch_face_kernel_multi<float>(const HostProblem&, const D
                                                      const float*, int64_t, int, float*,
                                                      cudaStream_t);
 template cudaError_t launch_face_kernel<float>(const HostProblem&, const DeviceData&,
-                                               const float*, float*, cudaStream_t);
+                                               const float*, float*, cudaStream_t, int, int);
 
 }  // namespace sbm

@@ -53,6 +53,12 @@ struct KTab {
 template <typename T>
 KTab<T> make_ktab(const HostProblem& hp);
 
+constexpr int kMaxSlabs = 16;   // slabs of the pipelined host-buffer apply, at most
+// Their cumulative shares of the cells: small first and last slabs (the copy
+// of x before the first kernel, the copy of y after the last one), large
+// ones between (full launches).
+constexpr double kSlabCuts[] = {0.04, 0.16, 0.40, 0.64, 0.84, 0.96};
+
 // CG chunking: runs of up to R consecutive active cells of one x-row.
 struct ChunkTable {
   int n = 0;
@@ -60,18 +66,26 @@ struct ChunkTable {
   uint8_t* colour = nullptr;     // [n] colour of each chunk
   uint32_t* run_bits = nullptr;  // [n][bit_words]: bit l*S + kk of chunk ch set if element kk
   int bit_words = 0;             //   of its run l is a DoF that several colours touch
-  int32_t* multi = nullptr;      // [nmulti] DoFs touched by two colours or more, ascending
+  int32_t* multi = nullptr;      // [nmulti] DoFs touched by two colours or more, grouped by
+                                 //   colour count (2, 3-4, 5-8), ascending within a group
   uint8_t* multi_mask = nullptr; // [nmulti] their colour masks
   int64_t nmulti = 0;
+  // slabs of the pipelined host-buffer apply: chunks [slab_chunk[s],
+  // slab_chunk[s+1]), shared DoFs multi[slab_multi[s], slab_multi[s+1])
+  std::vector<int> slab_chunk;
+  std::vector<int64_t> slab_multi;
 };
 
 // Device-built set-up tables (setup_gpu.cu).  For one chunking: the colour set
 // of every DoF (from the chunk-ordered line table `lines` on the device), the
 // list of DoFs several colours share and the per-chunk run bits, into ct.
+// The shared DoFs are listed slab by slab (slab s: DoFs [ycut[s], ycut[s+1]);
+// ct->slab_multi receives the offsets), then by colour count.
 cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, int64_t n_dofs,
                                 const std::vector<int32_t>& ch_first,
                                 const std::vector<uint8_t>& ch_col, int R,
-                                const int32_t* first_dev, ChunkTable* ct);
+                                const int32_t* first_dev, const std::vector<int64_t>& ycut,
+                                ChunkTable* ct);
 
 // The 1D Lagrange values at every shifted surrogate point (exact extension) or
 // the shift vectors (first-order Taylor), in kernel face order (fsrc[k] = the
@@ -109,6 +123,18 @@ struct DeviceData {
   int32_t* nbr = nullptr;        // DG [Nc * 2d] neighbour rank per (k, s), -1 = surrogate
   double* stage_x = nullptr;     // host-apply staging buffers (allocated on first use)
   double* stage_y = nullptr;
+  // CG: the pipelined host-buffer apply cuts the cells into nslab slabs of
+  // whole cell layers along the last axis (the DoF numbering's slowest);
+  // slab s has the faces [slab_face[s], slab_face[s+1]), needs x on the DoFs
+  // [0, slab_x[s]) and makes y final on [slab_y[s], slab_y[s+1]).  Its copies
+  // run on copy_in / copy_out, its face kernel on face_st (beside the
+  // previous slab's cells), ordered by ev_in[s], ev_face[s], ev_done[s].
+  int nslab = 0;
+  std::vector<int> slab_face;
+  std::vector<int64_t> slab_x, slab_y;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr, face_st = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_face, ev_done;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // Optional kernel timing: CUDA events on the apply's stream at the phase
@@ -145,10 +171,11 @@ template <typename T> inline T* face_out_of(const DeviceData& dd);
 template <> inline double* face_out_of<double>(const DeviceData& dd) { return dd.face_out; }
 template <> inline float* face_out_of<float>(const DeviceData& dd) { return dd.face_out32; }
 
-// All surrogate faces into the per-face scratch (face_kernel.cu).
+// The surrogate faces [fb, fe) of the kernel face order (all: 0, -1) into
+// the per-face scratch (face_kernel.cu).
 template <typename T>
 cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
-                               cudaStream_t st);
+                               cudaStream_t st, int fb = 0, int fe = -1);
 // The same for nrhs right-hand sides (x: nrhs vectors ldx apart; out: nrhs
 // copies of the per-face scratch).
 template <typename T>
@@ -197,6 +224,10 @@ inline cudaError_t launch_faces(const HostProblem& hp, const DeviceData& dd, con
   }
   return launch_face_kernel<T>(hp, dd, x, out, st);
 }
+// Slab s of the CG FP64 apply on the problem's own scratch (cg_apply.cu):
+// stages 1 = its surrogate faces, 2 = its cells and the assembly it completes.
+cudaError_t launch_cg_apply_slab(const HostProblem& hp, const DeviceData& dd, const double* x,
+                                 double* y, int slab, int stages, cudaStream_t st);
 // FP64 diagonal.
 cudaError_t launch_diag_f64(const HostProblem& hp, const DeviceData& dd, double* diag,
                             cudaStream_t st);

@@ -383,21 +383,50 @@ __global__ void k_colour_masks(int64_t nc, int L, int n, const int32_t* __restri
   }
 }
 
-__global__ void k_multi_flags(const uint32_t* __restrict__ mask, int64_t n, int32_t* __restrict__ flag) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n;
-       g += (int64_t)gridDim.x * blockDim.x)
-    flag[g] = (__popc(mask[g]) >= 2) ? 1 : 0;
+// Shared DoFs are listed slab by slab (DoF ranges [cut[s], cut[s+1])), and
+// within a slab by colour count: group 0 = 2 colours, 1 = 3..4, 2 = 5..8
+// (ascending DoF index within a group), so that a warp of the assembly
+// kernel adds about as many values for each of its DoFs.
+struct SlabCuts {
+  int n;                         // slabs
+  int64_t cut[kMaxSlabs + 1];    // DoF cut points
+  int64_t base[kMaxSlabs][3];    // list offset of (slab, group)
+  int64_t first[kMaxSlabs][3];   // group scan value at the slab's first DoF
+};
+
+__device__ __forceinline__ int multi_group(uint32_t m) {
+  const int k = __popc(m);
+  return k < 2 ? -1 : (k == 2 ? 0 : (k <= 4 ? 1 : 2));
 }
 
+__global__ void k_multi_flags(const uint32_t* __restrict__ mask, int64_t n, int group,
+                              int32_t* __restrict__ flag) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n;
+       g += (int64_t)gridDim.x * blockDim.x)
+    flag[g] = (multi_group(mask[g]) == group) ? 1 : 0;
+}
+
+// pos: exclusive scan of the group's flags over all DoFs
 __global__ void k_multi_write(const uint32_t* __restrict__ mask, const int32_t* __restrict__ flag,
-                              const int64_t* __restrict__ pos, int64_t n, int32_t* __restrict__ multi,
+                              const int64_t* __restrict__ pos, const SlabCuts sc, int group,
+                              int64_t n, int32_t* __restrict__ multi,
                               uint8_t* __restrict__ multi_mask) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n;
        g += (int64_t)gridDim.x * blockDim.x)
     if (flag[g]) {
-      multi[pos[g]] = (int32_t)g;
-      multi_mask[pos[g]] = (uint8_t)mask[g];
+      int s = 0;
+      while (s + 1 < sc.n && g >= sc.cut[s + 1]) ++s;
+      const int64_t at = sc.base[s][group] + (pos[g] - sc.first[s][group]);
+      multi[at] = (int32_t)g;
+      multi_mask[at] = (uint8_t)mask[g];
     }
+}
+
+// out[s] = pos[cut[s]] (cut[s] < n) or total (cut[s] == n), s = 0..ns
+__global__ void k_scan_at(const int64_t* __restrict__ pos, const int64_t* __restrict__ total,
+                          const SlabCuts sc, int64_t n, int64_t* __restrict__ out) {
+  const int s = threadIdx.x;
+  if (s <= sc.n) out[s] = (sc.cut[s] < n) ? pos[sc.cut[s]] : *total;
 }
 
 // run element (l, kk) of chunk k shared by several colours -> bit l*S + kk
@@ -462,7 +491,8 @@ __global__ void k_face_phi(const LagArgs a, int64_t F, const int64_t* __restrict
 cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, int64_t n_dofs,
                                 const std::vector<int32_t>& ch_first,
                                 const std::vector<uint8_t>& ch_col, int R,
-                                const int32_t* first_dev, ChunkTable* ct) {
+                                const int32_t* first_dev, const std::vector<int64_t>& ycut,
+                                ChunkTable* ct) {
   DevBufs B;
   const int nch = (int)ch_col.size();
   std::vector<uint8_t> col(nc);
@@ -471,26 +501,54 @@ cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, 
   uint8_t* col_d;
   uint32_t* mask;
   int32_t* flag;
-  int64_t *pos, *tot;
+  int64_t *pos, *tot, *at;
+  SlabCuts sc;
+  sc.n = (int)ycut.size() - 1;
+  if (sc.n < 1 || sc.n > kMaxSlabs) return cudaErrorInvalidValue;
+  for (int s = 0; s <= sc.n; ++s) sc.cut[s] = ycut[s];
   cudaError_t e;
   if ((e = B.alloc(&col_d, (size_t)nc)) != cudaSuccess ||
       (e = B.alloc(&mask, (size_t)n_dofs)) != cudaSuccess ||
       (e = B.alloc(&flag, (size_t)n_dofs)) != cudaSuccess ||
       (e = B.alloc(&pos, (size_t)n_dofs)) != cudaSuccess || (e = B.alloc(&tot, 1)) != cudaSuccess ||
+      (e = B.alloc(&at, (size_t)kMaxSlabs + 1)) != cudaSuccess ||
       (e = cudaMemcpy(col_d, col.data(), (size_t)nc, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(mask, 0, (size_t)n_dofs * 4)) != cudaSuccess)
     return e;
   k_colour_masks<<<grid_for(nc * L * n), 256>>>(nc, L, n, lines, col_d, mask);
-  k_multi_flags<<<grid_for(n_dofs), 256>>>(mask, n_dofs, flag);
-  if ((e = exclusive_scan(flag, n_dofs, pos, tot, B)) != cudaSuccess) return e;
+  // per group: the scan values at the slab cuts give the (slab, group) counts
+  int64_t sv[3][kMaxSlabs + 1];
+  for (int grp = 0; grp < 3; ++grp) {
+    k_multi_flags<<<grid_for(n_dofs), 256>>>(mask, n_dofs, grp, flag);
+    if ((e = exclusive_scan(flag, n_dofs, pos, tot, B)) != cudaSuccess) return e;
+    k_scan_at<<<1, kMaxSlabs + 1>>>(pos, tot, sc, n_dofs, at);
+    if ((e = cudaMemcpy(sv[grp], at, (size_t)(sc.n + 1) * 8, cudaMemcpyDeviceToHost)) !=
+        cudaSuccess)
+      return e;
+  }
   int64_t nm = 0;
-  if ((e = cudaMemcpy(&nm, tot, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) return e;
+  ct->slab_multi.assign(sc.n + 1, 0);
+  for (int s = 0; s < sc.n; ++s) {
+    ct->slab_multi[s] = nm;
+    for (int grp = 0; grp < 3; ++grp) {
+      sc.base[s][grp] = nm;
+      sc.first[s][grp] = sv[grp][s];
+      nm += sv[grp][s + 1] - sv[grp][s];
+    }
+  }
+  ct->slab_multi[sc.n] = nm;
   ct->nmulti = nm;
   if (nm > 0) {
     if ((e = cudaMalloc((void**)&ct->multi, (size_t)nm * 4)) != cudaSuccess ||
         (e = cudaMalloc((void**)&ct->multi_mask, (size_t)nm)) != cudaSuccess)
       return e;
-    k_multi_write<<<grid_for(n_dofs), 256>>>(mask, flag, pos, n_dofs, ct->multi, ct->multi_mask);
+    for (int grp = 0; grp < 3; ++grp) {
+      if (sv[grp][sc.n] == sv[grp][0]) continue;
+      k_multi_flags<<<grid_for(n_dofs), 256>>>(mask, n_dofs, grp, flag);
+      if ((e = exclusive_scan(flag, n_dofs, pos, tot, B)) != cudaSuccess) return e;
+      k_multi_write<<<grid_for(n_dofs), 256>>>(mask, flag, pos, sc, grp, n_dofs, ct->multi,
+                                               ct->multi_mask);
+    }
   }
   const int P = n - 1;
   const int words = (L * (P * R + 1) + 31) / 32;

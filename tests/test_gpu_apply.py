@@ -74,15 +74,32 @@ def test_whole_box_and_one_cell_mesh():
         _check_full(S._wl("one", d, 4, 1, S.ball(d, (0.0,) * d, 0.9)))
 
 
-def test_host_entry_point_equals_device_apply():
-    w = S.SPHERE_3D_Q4.resized(10)
+# two balls with empty cell layers between them along z (3D) / y (2D)
+_TWO_BALLS_3D = S._wl("two_balls_3d", 3, 3, 16, (S.BALLS, (0.1, 0.0, -0.6, 0.3,
+                                                          -0.1, 0.05, 0.55, 0.35)))
+_TWO_BALLS_2D = S._wl("two_balls_2d", 2, 4, 24, (S.BALLS, (0.0, -0.6, 0.3, 0.1, 0.6, 0.3)))
+
+
+@pytest.mark.parametrize("w", [S.SPHERE_3D_Q4.resized(10), S.SPHERE_3D_Q4.resized(24),
+                               S.DISK_2D_Q2, S.ELLIPSOID_3D_Q6.resized(9), _TWO_BALLS_3D,
+                               _TWO_BALLS_2D, S.SPHERE_3D_Q4.resized(24, degree=1)],
+                         ids=lambda w: w.name)
+def test_host_entry_point_equals_device_apply(w):
+    """The host-buffer entry point pipelines the copies with the kernels
+    slab by slab (cell layers along the last axis); its result is bitwise the
+    device apply's, with either tile shape."""
     P = G.Problem.from_workload(w)
     x = S.random_vector(3, P.n_dofs, "uniform")
-    yd = P.apply_f64(torch.from_numpy(x).cuda()).cpu().numpy()
     xh = torch.from_numpy(x).pin_memory()
-    yh = torch.empty(P.n_dofs, dtype=torch.float64).pin_memory()
-    P.apply_f64_host(xh, yh)
-    np.testing.assert_array_equal(yh.numpy(), yd)
+    for shape in (0, 1):
+        G.sbm_set_tile_shape(P.handle, shape, shape)
+        yd = P.apply_f64(torch.from_numpy(x).cuda()).cpu().numpy()
+        yh = torch.full((P.n_dofs,), np.nan, dtype=torch.float64).pin_memory()
+        P.apply_f64_host(xh, yh)
+        np.testing.assert_array_equal(yh.numpy(), yd)
+        # pageable host buffers too
+        yp = P.apply_f64_host(x.copy())
+        np.testing.assert_array_equal(yp, yd)
 
 
 def _sample_rows(O, rng, nrand=10000, nface_cells=200):
