@@ -50,6 +50,7 @@ KTab<T> make_ktab(const HostProblem& hp) {
     t.W[q] = (T)(hd1 * w);
   }
   t.h_inv = (T)(1.0 / hp.h);
+  t.hface = (T)hd1;
   t.sigma = (T)hp.sigma;
   auto fold = [n](const double (&A)[kMaxN][kMaxN], double scale, Folded<T>* f) {
     const int H = n / 2, HE = (n + 1) / 2;

@@ -13,8 +13,11 @@
 //    evaluated from both sides: twice the face arithmetic, no write conflict);
 //  * surrogate face: Algorithm 3, computed for all faces beforehand by the
 //    face kernel (face_kernel.cu) and folded in here from its scratch.
-// Face arithmetic is sum-factorised: nodal traces -> tangential Gauss points
-// -> pointwise terms -> transposed interpolation -> added to the cell result.
+// Interior-face arithmetic in nodal form: the face integrands are linear in
+// the nodal traces and the face quadrature is exact, so interpolation to the
+// Gauss points, weights and transposed interpolation collapse into the 1D
+// mass matrices: nodal traces -> pointwise combination -> (M x M) -> added to
+// the cell result.
 #include "sweeps.cuh"
 
 namespace sbm {
@@ -49,9 +52,7 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
   T* A = reinterpret_cast<T*>(smem_raw);       // sweep tile, then the result tile
   Pair2* AE = reinterpret_cast<Pair2*>(smem_raw);
   T* X = A + (D == 3 ? 1 : 2) * CPB * ND;      // CPB input tiles
-  T* T1 = X + CPB * ND;        // face scratch, CPB * L each
-  T* T2 = T1 + CPB * L;
-  T* U1 = T2 + CPB * L;
+  T* U1 = X + CPB * ND;        // face scratch, CPB * L each
   T* U2 = U1 + CPB * L;
   T* P1 = U2 + CPB * L;
   T* P2 = P1 + CPB * L;
@@ -93,8 +94,6 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
   __syncthreads();
 
   int fptr = act ? __ldg(a.face_start + pos) : 0;   // next surrogate face of this cell
-  T* t1 = T1 + c * L;
-  T* t2 = T2 + c * L;
   T* u1 = U1 + c * L;
   T* u2 = U2 + c * L;
   T* p1 = P1 + c * L;
@@ -118,11 +117,17 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
       const T sg = s ? T(1) : T(-1);
       const T* fo = nullptr;
       if (act && !interior) fo = a.face_out + (size_t)(fptr++) * 2 * L;
-      // A. nodal traces (own side and, for interior faces, the neighbour's)
+      // A. nodal traces (own side and, for interior faces, the neighbour's),
+      // and the two integrands in nodal form: with Gauss quadrature exact on
+      // the face, interpolating to the Gauss points, weighting and
+      // interpolating back is h^(d-1) (M x M) (the exact 1D mass matrices), so
+      //   value test:  h^(d-1) (M x M) sg (sigma_F [u] - h^-1 {d_k u}),
+      //   normal-derivative test:  h^(d-1) (M x M) (-[u] / (2 h))
       if (act) {
         T um = Xc[kend * sk + bt], dm = T(0);
 #pragma unroll
         for (int j = 0; j < N; ++j) dm = fma(s ? t.D1[j] : t.D0[j], Xc[j * sk + bt], dm);
+        T a1 = T(0), a2 = T(0);
         if (interior) {
           const T* xn = a.x + (size_t)nb * ND;
           const int nend = s ? 0 : N - 1;
@@ -130,99 +135,44 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
 #pragma unroll
           for (int j = 0; j < N; ++j)
             dnb = fma(s ? t.D0[j] : t.D1[j], __ldg(xn + j * sk + bt), dnb);
-          t1[tl] = s ? (um - un) : (un - um);        // [u] = u_K1 - u_K2
-          t2[tl] = T(0.5) * (dm + dnb);                 // {d_k u} (reference)
-        } else {
-          t1[tl] = T(0);
-          t2[tl] = T(0);
+          const T jump = s ? (um - un) : (un - um);        // [u] = u_K1 - u_K2
+          const T avg = T(0.5) * (dm + dnb);               // {d_k u} (reference)
+          a1 = (sg * t.hface) * (a.sigma_f * jump - t.h_inv * avg);
+          a2 = (T(-0.5) * t.hface * t.h_inv) * jump;
         }
+        p1[tl] = a1;
+        p2[tl] = a2;
       }
       __syncthreads();
-      // B. tangential interpolation to the Gauss points
-      if (D == 3) {
-        if (act) {
-          const int qa = tl % N, jb = tl / N;
-          T v1 = T(0), v2 = T(0);
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            v1 = fma(t.S[qa][j], t1[j + N * jb], v1);
-            v2 = fma(t.S[qa][j], t2[j + N * jb], v2);
-          }
-          u1[tl] = v1;
-          u2[tl] = v2;
-        }
-        __syncthreads();
-        if (act) {
-          const int qa = tl % N, qb = tl / N;
-          T v1 = T(0), v2 = T(0);
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            v1 = fma(t.S[qb][j], u1[qa + N * j], v1);
-            v2 = fma(t.S[qb][j], u2[qa + N * j], v2);
-          }
-          t1[tl] = v1;   // reuse: values at the Gauss points
-          t2[tl] = v2;
-        }
-      } else {
-        if (act) {
-          T v1 = T(0), v2 = T(0);
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            v1 = fma(t.S[tl][j], t1[j], v1);
-            v2 = fma(t.S[tl][j], t2[j], v2);
-          }
-          u1[tl] = v1;
-          u2[tl] = v2;
-        }
-      }
-      __syncthreads();
-      // C. pointwise integrands
-      if (act) {
-        const T g1 = (D == 3) ? t1[tl] : u1[tl];
-        const T g2 = (D == 3) ? t2[tl] : u2[tl];
-        const T W = t.W[tl];
-        T val, grd;
-        if (interior) {
-          const T Tv = a.sigma_f * g1 - t.h_inv * g2;
-          val = W * sg * Tv;
-          grd = T(-0.5) * W * g1 * t.h_inv;
-        } else {
-          val = T(0);
-          grd = T(0);
-        }
-        p1[tl] = val;
-        p2[tl] = grd;
-      }
-      __syncthreads();
-      // D. transposed interpolation, E. add to the cell result
+      // B. (M x M) on both integrands, the first axis, then the second
       T rv = T(0), rg = T(0);
       if (D == 3) {
         if (act) {
-          const int ja = tl % N, qb = tl / N;
+          const int ia = tl % N, jb = tl / N;
           T v1 = T(0), v2 = T(0);
 #pragma unroll
-          for (int q = 0; q < N; ++q) {
-            v1 = fma(t.S[q][ja], p1[q + N * qb], v1);
-            v2 = fma(t.S[q][ja], p2[q + N * qb], v2);
+          for (int j = 0; j < N; ++j) {
+            v1 = fma(t.M[ia][j], p1[j + N * jb], v1);
+            v2 = fma(t.M[ia][j], p2[j + N * jb], v2);
           }
           u1[tl] = v1;
           u2[tl] = v2;
         }
         __syncthreads();
         if (act) {
-          const int ja = tl % N, jb = tl / N;
+          const int ia = tl % N, ib = tl / N;
 #pragma unroll
-          for (int q = 0; q < N; ++q) {
-            rv = fma(t.S[q][jb], u1[ja + N * q], rv);
-            rg = fma(t.S[q][jb], u2[ja + N * q], rg);
+          for (int j = 0; j < N; ++j) {
+            rv = fma(t.M[ib][j], u1[ia + N * j], rv);
+            rg = fma(t.M[ib][j], u2[ia + N * j], rg);
           }
         }
       } else {
         if (act) {
 #pragma unroll
-          for (int q = 0; q < N; ++q) {
-            rv = fma(t.S[q][tl], p1[q], rv);
-            rg = fma(t.S[q][tl], p2[q], rg);
+          for (int j = 0; j < N; ++j) {
+            rv = fma(t.M[tl][j], p1[j], rv);
+            rg = fma(t.M[tl][j], p2[j], rg);
           }
         }
       }
@@ -249,7 +199,7 @@ static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x,
                         cudaStream_t st, Profiler* prof, int face_mode) {
   constexpr int L = DgShape<D, N>::L, ND = DgShape<D, N>::ND, CPB = DgShape<D, N>::CPB;
   const KTab<T> t = make_ktab<T>(hp);
-  const size_t smem = (size_t)(((D == 3) ? 2 : 3) * CPB * ND + 6 * CPB * L) * sizeof(T);
+  const size_t smem = (size_t)(((D == 3) ? 2 : 3) * CPB * ND + 4 * CPB * L) * sizeof(T);
   cudaError_t err;
   if (smem > 48 * 1024) {
     err = cudaFuncSetAttribute(dg_apply_kernel<T, D, N>,

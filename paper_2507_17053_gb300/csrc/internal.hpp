@@ -41,6 +41,7 @@ struct KTab {
   T D1[kMaxN];           // phi_j'(1)
   T W[kMaxN * kMaxN];    // face weights h^(d-1) w_qa w_qb (tangential Gauss index q)
   T h_inv;
+  T hface;               // h^(d-1), the face Jacobian
   T sigma;
   Folded<T> fM, fK, fMh, fKh;  // even/odd parts of M, K, Mh, Kh (GLL nodes are symmetric)
   // eigenbasis of the pencil (K, M) (M = V V^T, K = V diag(lam) V^T; even
