@@ -247,12 +247,15 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
 }
 
 // For the DoFs i = multi[t] that several colours touch:
-// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order.  Lane
-// slot j holds the value of the lane's j-th colour (0 past its count); the
-// additions run over the slots up to the warp's largest colour count (on
-// GB300 a double addition costs an FP64-pipe slot per warp instruction,
-// whatever its active lanes, and the list is grouped by colour count, so
-// that count is the warp's own).  Adding a slot's 0 leaves a sum unchanged.
+// y_i = sum_{c in mask_i} ycol[c][i], colours in increasing order.  Lane by
+// lane the j-th step adds the value of the lane's j-th colour (0 past its
+// count), for j up to the warp's largest colour count.  FP64: a loop with a
+// warp-uniform, run-time trip count, so the additions a warp issues are its
+// own count minus one (on GB300 a double addition costs an FP64-pipe slot
+// per warp instruction, whatever its active lanes; the list is grouped by
+// colour count, so most warps need one).  FP32: all loads first, then the
+// unrolled sum (the additions are cheap, the load latency is not).  Adding
+// a 0 leaves a sum unchanged.
 template <typename T>
 __global__ void assemble_kernel(const T* __restrict__ ycol, const int32_t* __restrict__ multi,
                                 const uint8_t* __restrict__ multi_mask, T* __restrict__ y,
@@ -269,19 +272,32 @@ __global__ void assemble_kernel(const T* __restrict__ ycol, const int32_t* __res
   }
   if (ncol < 8) m &= (1u << ncol) - 1u;
   const unsigned kmax = __reduce_max_sync(0xffffffffu, (unsigned)__popc(m));
-  // all loads first (independent), then the sum
-  T v[8];
-  unsigned r = m;
+  T acc = T(0);
+  if constexpr (std::is_same<T, double>::value) {
+    if (m) {
+      acc = __ldcs(ycol + (size_t)(__ffs(m) - 1) * n + i);
+      m &= m - 1u;
+    }
+    for (unsigned j = 1; j < kmax; ++j) {
+      T v = T(0);
+      if (m) {
+        v = __ldcs(ycol + (size_t)(__ffs(m) - 1) * n + i);
+        m &= m - 1u;
+      }
+      acc += v;
+    }
+  } else {
+    T v[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int c = __ffs(r) - 1;
-    v[j] = r ? __ldcs(ycol + (size_t)c * n + i) : T(0);
-    r &= r - 1u;
+    for (int j = 0; j < 8; ++j) {
+      v[j] = m ? __ldcs(ycol + (size_t)(__ffs(m) - 1) * n + i) : T(0);
+      m &= m - 1u;
+    }
+    acc = v[0];
+#pragma unroll
+    for (int j = 1; j < 8; ++j)
+      if ((unsigned)j < kmax) acc += v[j];
   }
-  T acc = v[0];
-#pragma unroll
-  for (int j = 1; j < 8; ++j)
-    if ((unsigned)j < kmax) acc += v[j];
   if (t < nmulti) __stcs(y + i, acc);
 }
 
