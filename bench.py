@@ -553,6 +553,57 @@ def batched(G, torch, steps=10):
     return res
 
 
+def batched_solve(G, torch):
+    """Time to a true relative residual of 1e-10 for a batch of independent
+    systems: the 8 rotated-ellipsoid CG problems of S.solve_batch() (p = 2, 3;
+    the batch generator's positive-real ones: BiCGStab needs no eigenvalue
+    in the left half-plane) x 4 right-hand sides (x ~ U(-1, 1)), solved (a)
+    one system after another with the single-problem FP64 BiCGStab, (b) all
+    together by the batched FP64 BiCGStab, (c) all together by the batched
+    FP64 refinement with FP32-apply inner solves."""
+    ws = S.solve_batch()
+    ps = [G.Problem.from_workload(w) for w in ws]
+    nrhs = 4
+    B = G.Batch(ps, nrhs, autotune=True)
+    bs = [torch.from_numpy(np.concatenate([S.random_vector(w.seed + 7 + r, p.n_dofs, "uniform")
+                                           for r in range(nrhs)])).cuda()
+          for w, p in zip(ws, ps)]
+    xs = [torch.empty_like(b) for b in bs]
+    res = {"problems": len(ps), "nrhs": nrhs, "systems": len(ps) * nrhs,
+           "dofs_total": sum(p.n_dofs for p in ps) * nrhs,
+           "n_dofs_range": [min(p.n_dofs for p in ps), max(p.n_dofs for p in ps)],
+           "rtol": 1e-10}
+    # (a) one after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its, worst, ok = [], 0.0, True
+    for p, b in zip(ps, bs):
+        for r in range(nrhs):
+            br = b[r * p.n_dofs:(r + 1) * p.n_dofs].contiguous()
+            x = torch.zeros_like(br)
+            it, rr, conv = G.sbm_bicgstab(p.handle, br, x, rtol=1e-10, maxit=20000)
+            its.append(it)
+            worst = max(worst, rr)
+            ok &= conv
+    torch.cuda.synchronize()
+    res["sequential_bicgstab_fp64"] = {"seconds": time.perf_counter() - t0, "converged": ok,
+                                       "iters_total": int(sum(its)), "iters_max": int(max(its)),
+                                       "worst_rel_residual": worst}
+    for mode in ("fp64", "mixed"):
+        B.solve(bs, xs, mode=mode, rtol=1e-10, check=False)      # workspace, graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, iters, relres, outer = B.solve(bs, xs, mode=mode, rtol=1e-10, check=False)
+        torch.cuda.synchronize()
+        res[f"batched_{mode}"] = {"seconds": time.perf_counter() - t0,
+                                  "converged": st == G.SBM_OK,
+                                  "iters_max": int(iters.max()), "iters_total": int(iters.sum()),
+                                  "worst_rel_residual": float(relres.max()),
+                                  **({"outer": outer} if mode == "mixed" else {})}
+    B.close()
+    return res
+
+
 def profile_applies(args, w):
     import torch
 
@@ -697,7 +748,8 @@ def run_ours(args, w):
     }
     if not args.skip_extras:
         for key, fn in (("solves", solve_times), ("other_workloads", other_workloads),
-                        ("batched_64x8", batched), ("extension_taylor1", extension_study),
+                        ("batched_64x8", batched), ("batched_solve", batched_solve),
+                        ("extension_taylor1", extension_study),
                         ("multiple_balls", multiball_study),
                         ("activity_criterion", activity_study)):
             try:

@@ -302,6 +302,43 @@ int sbm_batch_set_tile_shape(sbm_batch* batch, int problem, int variant);
 /* Free the batch (not its problems). */
 void sbm_batch_destroy(sbm_batch* batch);
 
+enum { SBM_BATCH_SOLVE_FP64 = 0, SBM_BATCH_SOLVE_MIXED = 1 };
+
+/*
+ * Solve A_k x = b for every problem k and right-hand side of the batch (the
+ * paper states no solver; Section 4.2 notes that the operator application
+ * dominates iterative solvers).  Every system runs its own BiCGStab
+ * iteration -- its own scalars, residual tests and stopping -- but the
+ * iterations advance together: each step applies the whole batch at once
+ * (sbm_batch_apply_*) and runs every vector operation as one launch over all
+ * systems, with per-system deterministic reductions (bitwise-reproducible
+ * results); systems that have finished stop updating.
+ *  mode SBM_BATCH_SOLVE_FP64: BiCGStab with FP64 applies from x = 0 to
+ *    |b - A x| <= rtol |b| per system, at most maxit iterations (restarted
+ *    from the best iterate after a breakdown, up to 20 times).
+ *  mode SBM_BATCH_SOLVE_MIXED: FP64 iterative refinement: r = b - A x in
+ *    FP64, an inner BiCGStab with FP64 vectors and FP32 applies for A d = r
+ *    to inner_rtol |r| or inner_maxit iterations, x += d where the inner
+ *    solve reduced its residual; a system leaves the refinement once its
+ *    residual no longer halves per step; at most maxit refinements; systems
+ *    above rtol then finish with the FP64 BiCGStab from their current x
+ *    (at most 20000 iterations).
+ * b[k], x[k]: device arrays of nrhs * n_dofs_k doubles, laid out as for
+ * sbm_batch_apply (x is output only; the solve starts from 0).
+ * iters[k * nrhs + r] (optional, host): BiCGStab iterations of that system
+ * (two applies each; inner and finishing ones summed); relres[k * nrhs + r]
+ * (optional, host): true relative residual |b - A x| / |b| in FP64 at exit;
+ * outer (optional): refinement steps taken.  Device workspace: 11 FP64 and
+ * 2 FP32 vectors of the batch's total length, allocated on first use and
+ * kept with the batch.  Synchronous on stream.
+ * Errors: SBM_ERR_ARG, SBM_ERR_STATE (other device), SBM_ERR_OOM,
+ * SBM_ERR_CUDA, SBM_ERR_NOT_CONVERGED (a system above rtol; x holds the
+ * last iterates and relres says which).
+ */
+int sbm_batch_solve(sbm_batch* batch, const double* const* b, double* const* x, int mode,
+                    double rtol, int maxit, double inner_rtol, int inner_maxit, int* iters,
+                    double* relres, int* outer, void* stream);
+
 /* ---- solvers (the paper gives none; these drive the operator) ----------- */
 enum { SBM_PRECOND_NONE = 0, SBM_PRECOND_JACOBI = 1 };
 

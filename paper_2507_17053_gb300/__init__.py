@@ -105,6 +105,11 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int)]),
     "sbm_batch_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "sbm_batch_destroy": (None, [ctypes.c_void_p]),
+    "sbm_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.c_void_p]),
     "sbm_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "sbm_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _c_i64p]),
     "sbm_device_status": (ctypes.c_int, [ctypes.c_void_p]),
@@ -247,6 +252,7 @@ def sbm_diagonal(handle: int, diag, stream=None) -> None:
 FACE_MODE = {"fp32": 0, "tf32": 1, "bf16": 2}
 PRECOND = {"none": 0, "jacobi": 1}
 INNER = {"gmres": 0, "bicgstab": 1, "bicgstab_mixed": 2}
+BATCH_SOLVE = {"fp64": 0, "mixed": 1}
 
 
 def sbm_apply_f32(handle: int, x, y, face_mode=0, stream=None) -> None:
@@ -380,6 +386,35 @@ class Batch:
             _check(lib().sbm_batch_apply_f64(self.handle, xa, ya, _stream(stream)),
                    "sbm_batch_apply_f64")
         return ys
+
+    def solve(self, bs, xs, mode="mixed", rtol=1e-10, maxit=None, inner_rtol=1e-2,
+              inner_maxit=300, stream=None, check=True):
+        """Solve A_k xs[k] = bs[k] for every problem and right-hand side
+        (float64 tensors of nrhs * n_dofs_k).  Returns (status, iters,
+        relres, outer): per-system BiCGStab iterations and true relative
+        residuals, indexed k * nrhs + r; raises SbmError on failure unless
+        check is False (then status may be SBM_ERR_NOT_CONVERGED)."""
+        import numpy as np
+        import torch
+        n = len(self.problems)
+        for p, b, x in zip(self.problems, bs, xs):
+            if (b.numel() != p.n_dofs * self.nrhs or x.numel() != b.numel()
+                    or b.dtype != torch.float64 or x.dtype != torch.float64):
+                raise ValueError("batch vector has the wrong size or dtype")
+        if maxit is None:
+            maxit = 20000 if mode == "fp64" else 50
+        ba = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        xa = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        nsys = n * self.nrhs
+        iters = np.zeros(nsys, dtype=np.int32)
+        relres = np.zeros(nsys, dtype=np.float64)
+        outer = ctypes.c_int()
+        st = lib().sbm_batch_solve(self.handle, ba, xa, BATCH_SOLVE[mode], rtol, maxit,
+                                   inner_rtol, inner_maxit, iters.ctypes.data,
+                                   relres.ctypes.data, ctypes.byref(outer), _stream(stream))
+        if check:
+            _check(st, "sbm_batch_solve")
+        return st, iters, relres, outer.value
 
     def tile_shape(self, k):
         v = ctypes.c_int()

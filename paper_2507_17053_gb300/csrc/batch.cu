@@ -15,30 +15,9 @@
 #include <string>
 #include <vector>
 
-#include "internal.hpp"
+#include "batch.hpp"
 
 using namespace sbm;
-
-struct sbm_batch {
-  std::vector<sbm_problem*> probs;
-  int nrhs = 0;
-  int device = 0;
-  std::vector<int> order;           // problems, largest first
-  std::vector<int> variant;         // cell-kernel tile shape per problem
-  std::map<int, int> tuned;         // degree -> variant
-  std::vector<cudaStream_t> streams;
-  cudaStream_t cap = nullptr;
-  cudaEvent_t fork = nullptr;
-  std::vector<cudaEvent_t> join;
-  std::vector<float*> face32, col32;
-  std::vector<double*> face64, col64;
-  struct Graph {
-    std::vector<const void*> ptrs;
-    int prec;
-    cudaGraphExec_t exec;
-  };
-  std::vector<Graph> graphs;
-};
 
 namespace {
 
@@ -186,6 +165,7 @@ int autotune(sbm_batch* B) {
 }
 
 void destroy(sbm_batch* B) {
+  batch_solve_release(B);
   for (auto& g : B->graphs) cudaGraphExecDestroy(g.exec);
   for (auto* p : B->face32) cudaFree(p);
   for (auto* p : B->col32) cudaFree(p);

@@ -184,6 +184,23 @@ def batched_ellipsoids(nprob: int = 64, nrhs: int = 8, seed: int = BATCH_SEED,
     return out
 
 
+# Problems of batched_ellipsoids(nprob=24, n_range=(8, 14), p_range=(2, 3))
+# whose SBM matrix has its spectrum in the open right half-plane and on which
+# plain BiCGStab converges (eigenvalues of the oracle's assembled matrix and
+# SciPy's BiCGStab; pinned in test_oracle_spectrum.py).  On these coarse
+# meshes most p = 3 problems are indefinite (a few eigenvalues with negative
+# real part), and one positive-real p = 3 problem (index 21) still makes
+# BiCGStab diverge; only long-restart GMRES solves those.  The batched-solve
+# comparisons use the rest.
+SOLVE_BATCH = (1, 13, 15, 16, 17, 20, 23)
+
+
+def solve_batch() -> list[Workload]:
+    """The batched-solve workload: 7 problems (p = 2 or 3, 725 to 3 153 DoFs)."""
+    ws = batched_ellipsoids(nprob=24, n_range=(8, 14), p_range=(2, 3))
+    return [ws[i] for i in SOLVE_BATCH]
+
+
 def rhs_seed(w: Workload, r: int) -> int:
     """Seed of right-hand side r of a workload (r = 0 is the workload's own seed)."""
     return w.seed + r

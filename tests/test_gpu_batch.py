@@ -62,3 +62,64 @@ def test_batch_rejects_dg_and_bad_sizes():
     bad = [torch.zeros(3, device="cuda"), torch.zeros(3, device="cuda")]
     with pytest.raises(ValueError):
         B.apply(bad, bad)
+
+
+def _solve_batch():
+    ws = S.solve_batch()[:5] + [S.DISK_2D_Q2]
+    return ws, [G.Problem.from_workload(w) for w in ws]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_batch_solve_reaches_tolerance(mode):
+    """Every system of the batch reaches |b - A x| <= 1e-10 |b|, checked with
+    the single-problem FP64 apply; repeated solves are bitwise equal; the
+    smallest system's solution matches the oracle's direct solve."""
+    import scipy.sparse.linalg as spla
+
+    from oracle.operator import Problem as OracleProblem
+    ws, ps = _solve_batch()
+    nrhs = 2
+    B = G.Batch(ps, nrhs, autotune=False)
+    bs = [torch.from_numpy(np.concatenate([S.random_vector(w.seed + 7 + r, p.n_dofs, "uniform")
+                                           for r in range(nrhs)])).cuda()
+          for w, p in zip(ws, ps)]
+    xs = [torch.full_like(b, float("nan")) for b in bs]
+    st, iters, relres, outer = B.solve(bs, xs, mode=mode, rtol=1e-10, check=False)
+    assert st == G.SBM_OK, (G.STATUS.get(st), relres, iters, outer)
+    assert relres.shape == (len(ps) * nrhs,) and np.all(relres <= 1e-10)
+    assert np.all(iters > 0)
+    if mode == "mixed":
+        assert outer >= 1
+    for p, b, x in zip(ps, bs, xs):
+        for r in range(nrhs):
+            sl = slice(r * p.n_dofs, (r + 1) * p.n_dofs)
+            res = b[sl] - p.apply_f64(x[sl].contiguous())
+            assert float(res.norm() / b[sl].norm()) <= 1.5e-10
+    xs2 = [torch.empty_like(b) for b in bs]
+    B.solve(bs, xs2, mode=mode, rtol=1e-10)
+    for x, x2 in zip(xs, xs2):
+        assert torch.equal(x, x2)
+    k = min(range(len(ps)), key=lambda i: ps[i].n_dofs)
+    O = OracleProblem.from_workload(ws[k])
+    A = O.assemble().tocsc()
+    for r in range(nrhs):
+        sl = slice(r * ps[k].n_dofs, (r + 1) * ps[k].n_dofs)
+        ref = spla.spsolve(A, bs[k][sl].cpu().numpy())
+        assert np.abs(xs[k][sl].cpu().numpy() - ref).max() <= 1e-6 * np.abs(ref).max()
+    B.close()
+
+
+def test_batch_solve_rejects_bad_arguments():
+    ws, ps = _solve_batch()
+    B = G.Batch(ps[:2], 1, autotune=False)
+    bs = [torch.zeros(p.n_dofs, dtype=torch.float64, device="cuda") for p in ps[:2]]
+    xs = [torch.empty_like(b) for b in bs]
+    for kw in ({"rtol": 0.0}, {"maxit": 0}, {"mode": "mixed", "inner_rtol": 1.5}):
+        with pytest.raises(G.SbmError) as e:
+            B.solve(bs, xs, **kw)
+        assert G.STATUS[e.value.status] == "SBM_ERR_ARG"
+    # zero right-hand sides: x = 0, relative residual 0
+    st, iters, relres, _ = B.solve(bs, xs, mode="fp64")
+    assert st == G.SBM_OK and np.all(relres == 0.0)
+    assert all(float(x.abs().max()) == 0.0 for x in xs)
+    B.close()
