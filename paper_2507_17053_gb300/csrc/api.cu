@@ -146,6 +146,8 @@ static void free_device(DeviceData* dd) {
   for (cudaEvent_t ev : dd->ev_done)
     if (ev) cudaEventDestroy(ev);
   if (dd->face_st) cudaStreamDestroy(dd->face_st);
+  if (dd->cap_st) cudaStreamDestroy(dd->cap_st);
+  for (auto& g : dd->host_graphs) cudaGraphExecDestroy(g.exec);
   if (dd->ev_fork) cudaEventDestroy(dd->ev_fork);
   if (dd->ev_join) cudaEventDestroy(dd->ev_join);
   if (dd->copy_in) cudaStreamDestroy(dd->copy_in);
@@ -364,6 +366,7 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
     if ((e = cudaStreamCreateWithFlags(&dd->copy_in, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&dd->copy_out, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&dd->face_st, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&dd->cap_st, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&dd->ev_fork, fl)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&dd->ev_join, fl)) != cudaSuccess)
       goto err;
@@ -381,6 +384,51 @@ err:
   free_device(dd);
   return e == cudaErrorMemoryAllocation ? fail(SBM_ERR_OOM, "device allocation failed")
                                         : cuda_fail(e, "upload");
+}
+
+// The slab pipeline of the host-buffer apply, enqueued after the work on
+// origin and joined back to it: per slab, the copy of its part of x
+// (copy_in), its face kernel (face_st), its chunks and completed assembly
+// (origin), the copy of the part of y it finishes (copy_out).
+cudaError_t enqueue_host_pipeline(const HostProblem& hp, const DeviceData& dd, const double* x_host,
+                                  double* y_host, cudaStream_t origin) {
+  cudaError_t e;
+  if ((e = cudaEventRecord(dd.ev_fork, origin)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(dd.copy_in, dd.ev_fork, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(dd.face_st, dd.ev_fork, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(dd.copy_out, dd.ev_fork, 0)) != cudaSuccess)
+    return e;
+  int64_t xdone = 0;
+  for (int s = 0; s < dd.nslab; ++s) {
+    const int64_t x1 = dd.slab_x[s], y0 = dd.slab_y[s], y1 = dd.slab_y[s + 1];
+    if (x1 > xdone &&
+        (e = cudaMemcpyAsync(dd.stage_x + xdone, x_host + xdone, (size_t)(x1 - xdone) * 8,
+                             cudaMemcpyHostToDevice, dd.copy_in)) != cudaSuccess)
+      return e;
+    xdone = std::max(xdone, x1);
+    if ((e = cudaEventRecord(dd.ev_in[s], dd.copy_in)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(dd.face_st, dd.ev_in[s], 0)) != cudaSuccess)
+      return e;
+    if ((e = launch_cg_apply_slab(hp, dd, dd.stage_x, dd.stage_y, s, 1, dd.face_st)) !=
+        cudaSuccess)
+      return e;
+    // the chunks of slab s wait for its faces (and so for its part of x)
+    if ((e = cudaEventRecord(dd.ev_face[s], dd.face_st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(origin, dd.ev_face[s], 0)) != cudaSuccess)
+      return e;
+    if ((e = launch_cg_apply_slab(hp, dd, dd.stage_x, dd.stage_y, s, 2, origin)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(dd.ev_done[s], origin)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(dd.copy_out, dd.ev_done[s], 0)) != cudaSuccess)
+      return e;
+    if (y1 > y0 &&
+        (e = cudaMemcpyAsync(y_host + y0, dd.stage_y + y0, (size_t)(y1 - y0) * 8,
+                             cudaMemcpyDeviceToHost, dd.copy_out)) != cudaSuccess)
+      return e;
+  }
+  // (face_st's work ends before the last slab's chunks, which copy_out waited for)
+  if ((e = cudaEventRecord(dd.ev_join, dd.copy_out)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(origin, dd.ev_join, 0);
 }
 
 int sbm_fail_detail(int code, const std::string& msg) { return fail(code, msg); }
@@ -511,46 +559,39 @@ int sbm_apply_f64_host(sbm_problem* prob, const double* x_host, double* y_host, 
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (dd.nslab > 1) {
-    // pipelined by slabs: the copy of x in, the slabs' kernels and the copy
-    // of the finished parts of y out overlap
-    if ((e = cudaEventRecord(dd.ev_fork, st)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(dd.copy_in, dd.ev_fork, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(dd.face_st, dd.ev_fork, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(dd.copy_out, dd.ev_fork, 0)) != cudaSuccess)
-      return cuda_fail(e, "fork");
-    int64_t xdone = 0;
-    for (int s = 0; s < dd.nslab; ++s) {
-      const int64_t x1 = dd.slab_x[s], y0 = dd.slab_y[s], y1 = dd.slab_y[s + 1];
-      if (x1 > xdone &&
-          (e = cudaMemcpyAsync(dd.stage_x + xdone, x_host + xdone, (size_t)(x1 - xdone) * 8,
-                               cudaMemcpyHostToDevice, dd.copy_in)) != cudaSuccess)
-        return cuda_fail(e, "H2D");
-      xdone = std::max(xdone, x1);
-      if ((e = cudaEventRecord(dd.ev_in[s], dd.copy_in)) != cudaSuccess ||
-          (e = cudaStreamWaitEvent(dd.face_st, dd.ev_in[s], 0)) != cudaSuccess)
-        return cuda_fail(e, "event");
-      if ((e = launch_cg_apply_slab(prob->hp, dd, dd.stage_x, dd.stage_y, s, 1, dd.face_st)) !=
-          cudaSuccess)
-        return cuda_fail(e, "sbm_apply_f64_host");
-      // the chunks of slab s wait for its faces (and so for its part of x)
-      if ((e = cudaEventRecord(dd.ev_face[s], dd.face_st)) != cudaSuccess ||
-          (e = cudaStreamWaitEvent(st, dd.ev_face[s], 0)) != cudaSuccess)
-        return cuda_fail(e, "event");
-      if ((e = launch_cg_apply_slab(prob->hp, dd, dd.stage_x, dd.stage_y, s, 2, st)) !=
-          cudaSuccess)
-        return cuda_fail(e, "sbm_apply_f64_host");
-      if ((e = cudaEventRecord(dd.ev_done[s], st)) != cudaSuccess ||
-          (e = cudaStreamWaitEvent(dd.copy_out, dd.ev_done[s], 0)) != cudaSuccess)
-        return cuda_fail(e, "event");
-      if (y1 > y0 &&
-          (e = cudaMemcpyAsync(y_host + y0, dd.stage_y + y0, (size_t)(y1 - y0) * 8,
-                               cudaMemcpyDeviceToHost, dd.copy_out)) != cudaSuccess)
-        return cuda_fail(e, "D2H");
+    // page-locked buffers: the pipeline is captured once per buffer pair and
+    // replayed (its copies need page-locked memory inside a graph)
+    cudaPointerAttributes ax{}, ay{};
+    const bool locked = cudaPointerGetAttributes(&ax, x_host) == cudaSuccess &&
+                        cudaPointerGetAttributes(&ay, y_host) == cudaSuccess &&
+                        ax.type == cudaMemoryTypeHost && ay.type == cudaMemoryTypeHost;
+    cudaGetLastError();    // clear a pageable-pointer query's error state
+    if (locked) {
+      cudaGraphExec_t exec = nullptr;
+      for (const auto& g : dd.host_graphs)
+        if (g.x == x_host && g.y == y_host && g.variant == dd.variant[0]) exec = g.exec;
+      if (!exec) {
+        cudaGraph_t graph;
+        if ((e = cudaStreamBeginCapture(dd.cap_st, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+          return cuda_fail(e, "capture");
+        const cudaError_t le = enqueue_host_pipeline(prob->hp, dd, x_host, y_host, dd.cap_st);
+        e = cudaStreamEndCapture(dd.cap_st, &graph);
+        if (le != cudaSuccess) return cuda_fail(le, "sbm_apply_f64_host");
+        if (e != cudaSuccess) return cuda_fail(e, "capture end");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        if (dd.host_graphs.size() >= 4) {           // keep the most recent buffer pairs
+          cudaGraphExecDestroy(dd.host_graphs.front().exec);
+          dd.host_graphs.erase(dd.host_graphs.begin());
+        }
+        dd.host_graphs.push_back({x_host, y_host, dd.variant[0], exec});
+      }
+      if ((e = cudaGraphLaunch(exec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    } else if ((e = enqueue_host_pipeline(prob->hp, dd, x_host, y_host, st)) != cudaSuccess) {
+      return cuda_fail(e, "sbm_apply_f64_host");
     }
-    if ((e = cudaEventRecord(dd.ev_join, dd.copy_out)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(st, dd.ev_join, 0)) != cudaSuccess)
-      return cuda_fail(e, "join");
-    // (face_st's work ends before the last slab's chunks, which copy_out waited for)
   } else {
     if ((e = cudaMemcpyAsync(dd.stage_x, x_host, bytes, cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)

@@ -135,6 +135,16 @@ struct DeviceData {
   std::vector<int64_t> slab_x, slab_y;
   cudaStream_t copy_in = nullptr, copy_out = nullptr, face_st = nullptr;
   std::vector<cudaEvent_t> ev_in, ev_face, ev_done;
+  // the pipeline captured per page-locked (x, y) buffer pair and FP64 tile
+  // shape (at most 4 kept), and the stream it is captured on
+  struct HostGraph {
+    const void* x;
+    const void* y;
+    int variant;
+    cudaGraphExec_t exec;
+  };
+  std::vector<HostGraph> host_graphs;
+  cudaStream_t cap_st = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
@@ -225,6 +235,11 @@ inline cudaError_t launch_faces(const HostProblem& hp, const DeviceData& dd, con
   }
   return launch_face_kernel<T>(hp, dd, x, out, st);
 }
+// The slab pipeline of the host-buffer apply on the problem's streams,
+// forked from and joined back to origin (api.cu).
+cudaError_t enqueue_host_pipeline(const HostProblem& hp, const DeviceData& dd, const double* x_host,
+                                  double* y_host, cudaStream_t origin);
+
 // Slab s of the CG FP64 apply on the problem's own scratch (cg_apply.cu):
 // stages 1 = its surrogate faces, 2 = its cells and the assembly it completes.
 cudaError_t launch_cg_apply_slab(const HostProblem& hp, const DeviceData& dd, const double* x,

@@ -82,21 +82,31 @@ _TWO_BALLS_2D = S._wl("two_balls_2d", 2, 4, 24, (S.BALLS, (0.0, -0.6, 0.3, 0.1, 
 
 @pytest.mark.parametrize("w", [S.SPHERE_3D_Q4.resized(10), S.SPHERE_3D_Q4.resized(24),
                                S.DISK_2D_Q2, S.ELLIPSOID_3D_Q6.resized(9), _TWO_BALLS_3D,
-                               _TWO_BALLS_2D, S.SPHERE_3D_Q4.resized(24, degree=1)],
+                               _TWO_BALLS_2D, S.SPHERE_3D_Q4.resized(24, degree=1),
+                               S.TORUS_3D_DG_Q3.resized(12)],
                          ids=lambda w: w.name)
 def test_host_entry_point_equals_device_apply(w):
     """The host-buffer entry point pipelines the copies with the kernels
-    slab by slab (cell layers along the last axis); its result is bitwise the
-    device apply's, with either tile shape."""
+    slab by slab (cell layers along the last axis; with page-locked buffers
+    as a CUDA graph captured per buffer pair and replayed); its result is
+    bitwise the device apply's, with either tile shape, on a replay with new
+    contents in the same buffers, and with pageable buffers."""
     P = G.Problem.from_workload(w)
     x = S.random_vector(3, P.n_dofs, "uniform")
     xh = torch.from_numpy(x).pin_memory()
-    for shape in (0, 1):
+    for shape in ((0,) if w.dg else (0, 1)):
         G.sbm_set_tile_shape(P.handle, shape, shape)
         yd = P.apply_f64(torch.from_numpy(x).cuda()).cpu().numpy()
         yh = torch.full((P.n_dofs,), np.nan, dtype=torch.float64).pin_memory()
         P.apply_f64_host(xh, yh)
         np.testing.assert_array_equal(yh.numpy(), yd)
+        # the same buffers again, new contents (the captured graph replays)
+        x2 = S.random_vector(4, P.n_dofs, "uniform")
+        xh.copy_(torch.from_numpy(x2))
+        yh.fill_(float("nan"))
+        P.apply_f64_host(xh, yh)
+        np.testing.assert_array_equal(yh.numpy(), P.apply_f64(torch.from_numpy(x2).cuda()).cpu().numpy())
+        xh.copy_(torch.from_numpy(x))
         # pageable host buffers too
         yp = P.apply_f64_host(x.copy())
         np.testing.assert_array_equal(yp, yd)
