@@ -147,9 +147,45 @@ struct ChunkSmem {
   static constexpr int XS = (D == 3) ? L * SM : XZ;
   static constexpr int WORDS = (L * SM + 31) / 32;              // run-element bits
   static constexpr int XL = (D == 3) ? L * XLineOp<T, N>::kSize : 0;  // x-line operators
+  // two run areas and two run-start tables: the next chunk's runs are copied
+  // in (cp.async) while the current chunk is computed
   static constexpr size_t bytes =
-      (size_t)(TILE + XS + XL) * sizeof(T) + (size_t)(L + WORDS) * 4;
+      (size_t)(TILE + 2 * XS + XL) * sizeof(T) + (size_t)(2 * L + WORDS) * 4;
 };
+
+// Asynchronous global -> shared copy of one element (cp.async, no register
+// round trip); the copies of a thread are grouped by commit and waited for
+// by group.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int Pending>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(Pending) : "memory");
+}
+
+// Issue the copies of a chunk's L x-line runs (S values each, run l from
+// Ls[l]) into Xs (row stride SM).  idx -> (run l, position kk) without an
+// integer division: idx < L*S <= 1600, so (idx + 1/2)/S in FP32 is within
+// 1e-5 of the exact quotient, far inside its distance 1/(2S) >= 0.0038 from
+// an integer.
+template <typename T, int L, int SM>
+__device__ __forceinline__ void gather_runs_async(const T* __restrict__ xr, const int* Ls, T* Xs,
+                                                  int S, int tid, int nthr) {
+  const float invS = 1.0f / (float)S;
+  for (int idx = tid; idx < L * S; idx += nthr) {
+    const int l = __float2int_rz(((float)idx + 0.5f) * invS), kk = idx - l * S;
+    cp_async_elem(Xs + l * SM + kk, xr + (int64_t)Ls[l] + kk);
+  }
+}
 
 template <typename T, int D, int N, int R>
 __global__ void __launch_bounds__(R * Shape<D, N>::L)
@@ -162,13 +198,10 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   T* tile = reinterpret_cast<T*>(smem_raw);   // 3D: [R][ND] scalar tile
   P2* AE = reinterpret_cast<P2*>(smem_raw);   // 2D: pair tile (8/16-byte aligned); phase 2
   P2* BG = AE;                                //     runs in place
-  T* Xs = tile + CS::TILE;                    // [L][SM] the chunk's x-line runs
-  // per-cell results, node (j0, j1, j2) of cell c at c ND + j0 + n j1 + n^2 j2
-  // (3D: the tile; 2D: the run area, free after the first phase)
-  T* Z = (D == 3) ? tile : Xs;
-  T* XLs = Xs + CS::XS;                                      // 3D: [L] x-line operators
-  int* Ls = reinterpret_cast<int*>(XLs + CS::XL);            // [L] run starts
-  uint32_t* Bs = reinterpret_cast<uint32_t*>(Ls + L);        // run-element bits
+  T* Xbuf = tile + CS::TILE;                  // [2][L][SM] x-line runs (current, next)
+  T* XLs = Xbuf + 2 * CS::XS;                                // 3D: [L] x-line operators
+  int* Lbuf = reinterpret_cast<int*>(XLs + CS::XL);          // [2][L] run starts
+  uint32_t* Bs = reinterpret_cast<uint32_t*>(Lbuf + 2 * L);  // run-element bits
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
   // 3D: h K + mu M for the x-line of modes (a, b) = (tl % n, tl / n), in
@@ -180,28 +213,45 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   T* ycb = a.ycol + blockIdx.y * a.ld_ycol;
   T* yb = a.y + blockIdx.y * a.ldx;
 
-  for (int ch = a.q0 + blockIdx.x; ch < a.q1; ch += gridDim.x) {
+  // prologue: the first chunk's run starts, then its runs in flight
+  int ch = a.q0 + blockIdx.x, buf = 0;
+  if (ch < a.q1) {
+    const int first = __ldg(a.chunk_first + ch);
+    const int S = P * (__ldg(a.chunk_first + ch + 1) - first) + 1;
+    for (int i = tid; i < L; i += blockDim.x) Lbuf[i] = __ldg(a.lines + (size_t)first * L + i);
+    __syncthreads();
+    gather_runs_async<T, L, SM>(xr, Lbuf, Xbuf, S, tid, R * L);
+  }
+  cp_async_commit();
+  for (; ch < a.q1; ch += gridDim.x, buf ^= 1) {
+    T* Xs = Xbuf + buf * CS::XS;              // this chunk's runs
+    const int* Ls = Lbuf + buf * L;
+    // per-cell results, node (j0, j1, j2) of cell c at c ND + j0 + n j1 +
+    // n^2 j2 (3D: the tile; 2D: the run area, free after the first phase)
+    T* Z = (D == 3) ? tile : Xs;
     const int first = __ldg(a.chunk_first + ch);
     const int nc = __ldg(a.chunk_first + ch + 1) - first;
     const int S = P * nc + 1;                 // values per x-line run
-    // idx -> (run l, position kk) without an integer division: idx < L*S
-    // <= 1600, so (idx + 1/2)/S in FP32 is within 1e-5 of the exact
-    // quotient, far inside its distance 1/(2S) >= 0.0038 from an integer
     const float invS = 1.0f / (float)S;
-    // the chunk's run starts and run-element bits, then a coalesced gather
-    // of the L runs
+    // the next chunk's run starts, then its runs into the other buffer (the
+    // previous iteration's last barrier freed it); they land while this
+    // chunk is computed
+    const int nx = ch + gridDim.x;
+    if (nx < a.q1) {
+      const int f2 = __ldg(a.chunk_first + nx);
+      const int S2 = P * (__ldg(a.chunk_first + nx + 1) - f2) + 1;
+      int* Ln = Lbuf + (buf ^ 1) * L;
+      for (int i = tid; i < L; i += blockDim.x) Ln[i] = __ldg(a.lines + (size_t)f2 * L + i);
+      __syncthreads();
+      gather_runs_async<T, L, SM>(xr, Ln, Xbuf + (buf ^ 1) * CS::XS, S2, tid, R * L);
+    }
+    cp_async_commit();
     {
-      const int* lines0 = a.lines + (size_t)first * L;
       const uint32_t* bits = a.run_bits + (size_t)ch * a.bit_words;
-      for (int i = tid; i < L; i += blockDim.x) Ls[i] = __ldg(lines0 + i);
       for (int i = tid; i < (L * S + 31) / 32; i += blockDim.x) Bs[i] = __ldg(bits + i);
     }
-    __syncthreads();
-    for (int idx = tid; idx < L * S; idx += blockDim.x) {
-      const int l = __float2int_rz(((float)idx + 0.5f) * invS), kk = idx - l * S;
-      Xs[l * SM + kk] = __ldg(xr + (int64_t)Ls[l] + kk);
-    }
-    __syncthreads();
+    cp_async_wait<1>();                       // this chunk's runs (this thread's copies) ...
+    __syncthreads();                          // ... and everyone's
     const bool act = c < nc;
     T out[N];
     if constexpr (D == 3)
@@ -242,8 +292,9 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
       if ((Bs[idx >> 5] >> (idx & 31)) & 1u) yc[g] = v;
       else yb[g] = v;
     }
-    __syncthreads();                          // Xs / Z / Ls / Bs are reused by the next chunk
+    __syncthreads();                          // Xs / Z / Ls / Bs are reused
   }
+  cp_async_wait<0>();
 }
 
 // For the DoFs i = multi[t] that several colours touch:
