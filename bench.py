@@ -41,7 +41,8 @@ FP64_PIPE_GOPS = SMS * SM_MAX_MHZ * 1e6 * FP64_LANES_PER_SM_CLK / 1e9
 # DRAM bytes (read + write) of one launch of the FP64 cell kernel, from one
 # ncu capture per (workload, tile shape) of the kernel as it stands
 # (profiles/apply_f64_sphere3d_q4_n96_kernels.md); other shapes: not captured
-CELL_TRAFFIC = {}
+CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 0): 127.59e6 + 107.57e6,
+                ("sphere3d_cg_q4_n96", 1): 157.950720e6 + 133.191680e6}
 L2_BYTES = 129 * 1024 * 1024
 REF_BUDGET_S = 90.0              # wall-clock budget of the --impl reference run
 
