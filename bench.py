@@ -278,7 +278,8 @@ def solve_times(G, torch):
     with FP32 applies (short inner solves: 1e-2, at most 300 iterations; an
     FP64 BiCGStab finish when they stall).  3D sphere, Q2, N = 64 (413,013
     DoFs): BiCGStab and GMRES(200) in FP64, and the two BiCGStab refinements.
-    Each time is the median of 3 solves after a warm-up solve (the solves are
+    The disk also: BiCGStab on the FP32 apply with FP64 reliable updates (on
+    the sphere it stalls near 2e-5; see the solver notes).  Each time is the median of 3 solves after a warm-up solve (the solves are
     deterministic: the same iterations every time).  (At p >= 3 in 3D no
     unpreconditioned Krylov method reaches 1e-10 on this operator; see the
     solver notes.)"""
@@ -318,6 +319,10 @@ def solve_times(G, torch):
             inner_maxit=mi, inner_solver=G.INNER[inner]))
         d2[name] = {"converged": ok, "inner_iters": it, "outer": outer, "rel_residual": rr,
                     "seconds": dt, "inner_rtol": tol, "inner_maxit": mi}
+    (it, rr, ok, rep), dt = run(b, lambda x: G.sbm_bicgstab_mixed(P.handle, b, x, rtol=1e-10,
+                                                                 maxit=20000))
+    d2["bicgstab_mixed_reliable"] = {"converged": ok, "iters": it, "fp32_applies": 2 * it,
+                                     "fp64_applies": rep + 2, "rel_residual": rr, "seconds": dt}
     out["disk2d_q2"] = d2
 
     w = S.SPHERE_3D_Q4.resized(64, degree=2)

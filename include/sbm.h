@@ -422,6 +422,27 @@ int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int
                  int inner_solver, int* iters, int* outer, double* relres, void* stream);
 
 /*
+ * BiCGStab with FP64 vectors and scalars whose iterations apply the FP32
+ * operator (sbm_apply_f32 with face_mode, converted in and out), with
+ * reliable updates: whenever the recursive residual has fallen tenfold since
+ * the last update it is replaced by the true residual b - A x computed with
+ * the FP64 operator (sbm_apply_f64), so the iteration keeps its Krylov space
+ * (no restart) while converging to the FP64 solution; the initial and final
+ * residuals are FP64.  A breakdown restarts from the best iterate, as
+ * sbm_bicgstab.  When the true residual stops halving between updates (the
+ * FP32 operator's rounding limits the corrections on ill-conditioned
+ * systems) FP64 BiCGStab finishes from the current x within the remaining
+ * iteration budget.  b, x: device arrays of n_dofs doubles (x: initial guess
+ * in, solution out).  iters: iterations (two applies each, FP32 then FP64);
+ * replacements: reliable updates (one FP64 apply each); relres: true FP64
+ * relative residual at exit.  Synchronous.  Errors: as sbm_bicgstab, plus
+ * those of the face mode (SBM_ERR_ARG, SBM_ERR_UNSUPPORTED).
+ */
+int sbm_bicgstab_mixed(sbm_problem* prob, const double* b, double* x, double rtol, int maxit,
+                       int face_mode, int* iters, int* replacements, double* relres,
+                       void* stream);
+
+/*
  * Manufactured data (host, FP64; no CUDA call).  manufactured = 0:
  * u = prod_i sin(pi x_i), f = d pi^2 u; manufactured = 1 (2D only):
  * u = 2 cos(x_1) sin(x_2), f = 2 u (the paper's Appendix A solution).

@@ -95,6 +95,12 @@ _SIGS = {
                                                               ctypes.POINTER(ctypes.c_int),
                                                               ctypes.POINTER(ctypes.c_double),
                                                               ctypes.c_void_p]),
+    "sbm_bicgstab_mixed": (ctypes.c_int, [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int,
+                                                                    ctypes.c_int,
+                                                                    ctypes.POINTER(ctypes.c_int),
+                                                                    ctypes.POINTER(ctypes.c_int),
+                                                                    ctypes.POINTER(ctypes.c_double),
+                                                                    ctypes.c_void_p]),
     "sbm_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sbm_interpolate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sbm_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -297,6 +303,16 @@ def sbm_bicgstab_f32(handle: int, b, x, rtol=1e-5, maxit=10000, face_mode=0, str
     st = lib().sbm_bicgstab_f32(handle, _ptr(b), _ptr(x), rtol, maxit, int(face_mode),
                                 ctypes.byref(it), ctypes.byref(rr), _stream(stream))
     return _solve_call("sbm_bicgstab_f32", st, it, rr, raise_not_converged)
+
+
+def sbm_bicgstab_mixed(handle: int, b, x, rtol=1e-10, maxit=20000, face_mode=0, stream=None,
+                       raise_not_converged=False):
+    """Returns (iterations, true relative residual, converged, reliable updates)."""
+    it, rep, rr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    st = lib().sbm_bicgstab_mixed(handle, _ptr(b), _ptr(x), rtol, maxit, int(face_mode),
+                                  ctypes.byref(it), ctypes.byref(rep), ctypes.byref(rr),
+                                  _stream(stream))
+    return _solve_call("sbm_bicgstab_mixed", st, it, rr, raise_not_converged) + (rep.value,)
 
 
 def sbm_solve_ir(handle: int, b, x, rtol=1e-10, max_outer=30, restart=100, inner_rtol=1e-4,

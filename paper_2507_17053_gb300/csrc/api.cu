@@ -766,6 +766,25 @@ int sbm_solve_ir(sbm_problem* prob, const double* b, double* x, double rtol, int
   return solve_result(s, info, iters, relres, "sbm_solve_ir");
 }
 
+int sbm_bicgstab_mixed(sbm_problem* prob, const double* b, double* x, double rtol, int maxit,
+                       int face_mode, int* iters, int* replacements, double* relres,
+                       void* stream) {
+  if (!prob || !b || !x || b == x) return fail(SBM_ERR_ARG, "bad vector argument");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (!(rtol > 0) || maxit < 1) return fail(SBM_ERR_ARG, "bad solver parameter");
+  const int fm = check_face_mode(prob, face_mode);
+  if (fm != SBM_OK) return fm;
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace ws;
+  SolveInfo info;
+  SolveStatus s = solve_bicgstab_reliable(apply64_fn(prob), apply32_fn(prob, face_mode),
+                                          prob->hp.n_dofs, b, x, rtol, maxit, st, ws, &info,
+                                          replacements);
+  cudaStreamSynchronize(st);
+  ws.release();
+  return solve_result(s, info, iters, relres, "sbm_bicgstab_mixed");
+}
+
 int sbm_rhs(const sbm_problem* prob, int manufactured, double* b_host) {
   if (!prob || !b_host) return fail(SBM_ERR_ARG, "NULL argument");
   if (!manufactured_ok(manufactured, prob->hp.d)) return fail(SBM_ERR_ARG, "unknown solution id");

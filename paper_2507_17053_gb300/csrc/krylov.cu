@@ -709,6 +709,47 @@ __global__ void k_bi_beta(const double* __restrict__ part, BiState* st) {
   }
 }
 
+// reliable update: r = b - q (q = A x with the accurate operator); partials
+// of (r^, r), (r, r)
+template <typename T>
+__global__ void k_bi_replace(const T* __restrict__ b, const T* __restrict__ q,
+                             T* __restrict__ r, const T* __restrict__ rh, int64_t n,
+                             double* __restrict__ part) {
+  __shared__ double sh[RED_THREADS];
+  double srh = 0.0, srr = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T ri = (T)((double)b[i] - (double)q[i]);
+    r[i] = ri;
+    srh = fma((double)rh[i], (double)ri, srh);
+    srr = fma((double)ri, (double)ri, srr);
+  }
+  srh = block_sum(srh, sh);
+  srr = block_sum(srr, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = srh;
+    part[RED_BLOCKS + blockIdx.x] = srr;
+  }
+}
+
+// rho = (r^, r) and rr = (r, r) of the replaced residual; convergence test
+__global__ void k_bi_replace_fin(const double* __restrict__ part, BiState* st) {
+  __shared__ double sh[RED_THREADS];
+  if (st->done) return;
+  double v[2];
+  for (int j = 0; j < 2; ++j) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) s += part[j * RED_BLOCKS + i];
+    v[j] = block_sum(s, sh);
+  }
+  if (threadIdx.x == 0) {
+    st->rr = v[1];
+    st->rho = v[0];
+    if (v[1] <= st->tol2 * st->bb) st->done = 1;
+    else if (!isfinite(v[1]) || !(v[0] != 0.0)) st->done = 2;
+  }
+}
+
 // p = r + beta (p - omega v)
 template <typename T>
 __global__ void k_bi_p(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ v,
@@ -783,23 +824,58 @@ SolveStatus Bicgstab<T>::solve(bool x_zero, double rtol, int maxit, cudaStream_t
   int total = 0, restarts = 0, status = SBM_NOT_DONE;
   double relres = INFINITY, best = INFINITY;
   bool zero = x_zero;
+  const bool reliable = (bool)apply_hi;
+  const ApplyFn<T>& ap_true = reliable ? apply_hi : apply;   // first and final residuals
   while (true) {
     BiState init{};
     init.tol2 = rtol * rtol;
     init.maxit = maxit - total;
     CK(cudaMemcpyAsync(dst, &init, sizeof(BiState), cudaMemcpyHostToDevice, st));
-    if (!zero) CK(apply(x, v, st));
+    if (!zero) CK(ap_true(x, v, st));
     k_bi_init<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, zero ? nullptr : v, r, rh, p, n, part);
     k_bi_init_fin<<<1, RED_THREADS, 0, st>>>(part, dst);
     CK(cudaGetLastError());
     zero = false;
     int done = 0;
+    double rr_ref = -1.0;        // recursive residual at the last reliable update
+    double rr_true = INFINITY;   // true residual at the last reliable update
+    bool replaced = false, stalled = false;
     while (true) {
       CK(cudaMemcpyAsync(hs, dst, sizeof(BiState), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       done = hs->done;
+      if (rr_ref < 0.0) {
+        // a true residual (the first one, or just replaced)
+        rr_ref = hs->rr;
+        // one that no longer halves between updates: the reduced-precision
+        // iteration has stalled (the caller finishes)
+        if (replaced) stalled = !done && hs->rr > 0.25 * rr_true;
+        rr_true = hs->rr;
+        replaced = false;
+        // with reliable updates: keep the iterate of least true residual
+        if (reliable && std::isfinite(hs->rr) && hs->rr < best) {
+          best = hs->rr;
+          CK(cudaMemcpyAsync(xb, x, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        }
+      }
+      if (stalled) {
+        done = 3;
+        break;
+      }
+      // reliable update: the true residual replaces the recursive one
+      if (reliable && !done && std::isfinite(hs->rr) &&
+          hs->rr < reliable_factor * reliable_factor * rr_ref) {
+        CK(apply_hi(x, t, st));
+        k_bi_replace<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(b, t, r, rh, n, part);
+        k_bi_replace_fin<<<1, RED_THREADS, 0, st>>>(part, dst);
+        CK(cudaGetLastError());
+        ++replacements;
+        rr_ref = -1.0;           // re-read: the reference is the replaced residual
+        replaced = true;
+        continue;
+      }
       // keep the iterate of least (recursive) residual seen at a chunk end
-      if (std::isfinite(hs->rr) && hs->rr < best) {
+      if (!reliable && std::isfinite(hs->rr) && hs->rr < best) {
         best = hs->rr;
         CK(cudaMemcpyAsync(xb, x, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st));
       }
@@ -807,9 +883,10 @@ SolveStatus Bicgstab<T>::solve(bool x_zero, double rtol, int maxit, cudaStream_t
       CK(cudaGraphLaunch(exec, st));
     }
     total += hs->iters;
-    // after a breakdown, divergence or the iteration cap, continue from the
-    // best iterate rather than the last one
-    if (done != 1 && !(hs->rr <= best))
+    // after a breakdown, divergence, a stall or the iteration cap, continue
+    // from the best iterate rather than the last one (reliable updates: the
+    // best true residual; otherwise the best recursive one)
+    if (done != 1 && (reliable || !(hs->rr <= best)))
       CK(cudaMemcpyAsync(x, xb, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st));
     if (hs->bb == 0.0) {
       relres = 0.0;
@@ -817,7 +894,7 @@ SolveStatus Bicgstab<T>::solve(bool x_zero, double rtol, int maxit, cudaStream_t
       break;
     }
     // true residual of the current iterate
-    CK(apply(x, v, st));
+    CK(ap_true(x, v, st));
     k_residual<T><<<vec_grid(n), 256, 0, st>>>(b, v, n);
     CK(multi_dot<T>(v, 0, v, n, 1, part, part + RED_BLOCKS, st));
     double rr;
@@ -838,6 +915,48 @@ SolveStatus Bicgstab<T>::solve(bool x_zero, double rtol, int maxit, cudaStream_t
 
 template struct Bicgstab<double>;
 template struct Bicgstab<float>;
+
+// ---- BiCGStab on the FP32 apply with FP64 reliable updates -------------------
+
+SolveStatus solve_bicgstab_reliable(const ApplyFn<double>& apply64,
+                                    const ApplyFn<float>& apply32, int64_t n, const double* b,
+                                    double* x, double rtol, int maxit, cudaStream_t st,
+                                    Workspace& ws, SolveInfo* info, int* replacements) {
+  float *xa = nullptr, *ya = nullptr;
+  CK(ws.alloc((void**)&xa, n * 4));
+  CK(ws.alloc((void**)&ya, n * 4));
+  ApplyFn<double> apply_mixed = [&](const double* xin, double* yout, cudaStream_t s) {
+    k_convert_scaled<float, double><<<vec_grid(n), 256, 0, s>>>(xa, xin, 1.0, n);
+    cudaError_t e = apply32(xa, ya, s);
+    if (e != cudaSuccess) return e;
+    k_convert_scaled<double, float><<<vec_grid(n), 256, 0, s>>>(yout, ya, 1.0, n);
+    return cudaGetLastError();
+  };
+  Bicgstab<double> bi;
+  bi.apply_hi = apply64;
+  cudaError_t e = bi.setup(apply_mixed, n, b, x, ws);
+  SolveStatus s{SBM_ERR_CUDA, e};
+  if (e == cudaSuccess) s = bi.solve(false, rtol, maxit, st, info);
+  if (replacements) *replacements = bi.replacements;
+  bi.destroy();
+  // FP64 finish when the reduced-precision iteration stalled (the FP32
+  // operator's rounding, about kappa * 6e-8 of |b|, limits its corrections)
+  if (s.status == SBM_ERR_NOT_CONVERGED && std::isfinite(info->relres) &&
+      info->iters < maxit) {
+    Bicgstab<double> bf;
+    SolveInfo fi{};
+    e = bf.setup(apply64, n, b, x, ws);
+    SolveStatus f{SBM_ERR_CUDA, e};
+    if (e == cudaSuccess) f = bf.solve(false, rtol, maxit - info->iters, st, &fi);
+    bf.destroy();
+    if (f.status == SBM_ERR_CUDA) return f;
+    info->iters += fi.iters;
+    info->relres = fi.relres;
+    info->restarts += 1;
+    s = f;
+  }
+  return s;
+}
 
 // ---- FP64 iterative refinement around an FP32 inner solve --------------------
 

@@ -65,12 +65,29 @@ struct Bicgstab {
   void* hstate = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // Reliable updates (set apply_hi): the iterations run on `apply` (e.g.
+  // FP32 applies), and whenever the recursive residual has fallen by
+  // reliable_factor since the last update it is replaced by the true
+  // residual b - apply_hi(x); the first and the final residuals use
+  // apply_hi too.
+  ApplyFn<T> apply_hi;
+  double reliable_factor = 0.1;
+  int replacements = 0;
   cudaError_t setup(const ApplyFn<T>& apply, int64_t n, const T* b, T* x, Workspace& ws);
   // x_zero: x holds zeros on entry (skips the first residual's apply).
   // info->iters counts iterations (two operator applications each).
   SolveStatus solve(bool x_zero, double rtol, int maxit, cudaStream_t st, SolveInfo* info);
   void destroy();
 };
+
+// BiCGStab in FP64 vectors and scalars on the FP32 apply (converted in and
+// out around every application) with reliable updates: the recursive
+// residual is replaced by the true FP64 residual b - A64 x whenever it has
+// fallen tenfold since the last replacement.
+SolveStatus solve_bicgstab_reliable(const ApplyFn<double>& apply64,
+                                    const ApplyFn<float>& apply32, int64_t n, const double* b,
+                                    double* x, double rtol, int maxit, cudaStream_t st,
+                                    Workspace& ws, SolveInfo* info, int* replacements);
 
 // FP64 iterative refinement: r = b - A64 x in FP64, inner FP32 solve
 // (GMRES(restart) or BiCGStab, SBM_INNER_*) of A32 c = r/|r| to inner_rtol,
