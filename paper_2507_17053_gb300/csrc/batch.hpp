@@ -19,6 +19,7 @@ struct BatchSolveWs {
   float *a32 = nullptr, *b32 = nullptr;
   double* part = nullptr;          // [3][ntile] tile partial sums
   double* sums = nullptr;          // [2][nsys] per-system sums
+  int32_t* use = nullptr;          // [nsys] refinement: keep this system's correction
   void* state = nullptr;           // [nsys] per-system BiCGStab state
   void* hstate = nullptr;          // pinned host copy
   int32_t *tsys = nullptr, *tlen = nullptr, *tfirst = nullptr;

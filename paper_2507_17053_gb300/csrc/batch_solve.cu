@@ -488,6 +488,7 @@ cudaError_t ensure_ws(sbm_batch* B) {
       (e = alloc((void**)&w.b32, (size_t)n * 4)) != cudaSuccess ||
       (e = alloc((void**)&w.part, (size_t)3 * w.ntile * 8)) != cudaSuccess ||
       (e = alloc((void**)&w.sums, (size_t)2 * w.nsys * 8)) != cudaSuccess ||
+      (e = alloc((void**)&w.use, (size_t)w.nsys * 4)) != cudaSuccess ||
       (e = alloc(&w.state, sizeof(BSys) * w.nsys)) != cudaSuccess ||
       (e = alloc((void**)&w.tsys, 4 * tsys.size())) != cudaSuccess ||
       (e = alloc((void**)&w.tlen, 4 * tlen.size())) != cudaSuccess ||
@@ -575,9 +576,9 @@ extern "C" int sbm_batch_solve(sbm_batch* batch, const double* const* b, double*
         // keep the correction only where the inner solve reduced its residual
         use[s] = active[s] && std::isfinite(hs[s].best) && std::min(hs[s].rr, hs[s].best) < hs[s].bb;
       }
-      CKC(cudaMemcpyAsync(w.sums, use.data(), 4 * (size_t)c.nsys, cudaMemcpyHostToDevice, c.st),
+      CKC(cudaMemcpyAsync(w.use, use.data(), 4 * (size_t)c.nsys, cudaMemcpyHostToDevice, c.st),
           "mask upload");
-      k_add_masked<<<c.m.ntile, kThr, 0, c.st>>>(c.m, w.x, w.d, (const int32_t*)w.sums);
+      k_add_masked<<<c.m.ntile, kThr, 0, c.st>>>(c.m, w.x, w.d, w.use);
       CKC(cudaGetLastError(), "refinement update");
       nouter++;
     }
