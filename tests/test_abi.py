@@ -57,6 +57,12 @@ def test_null_arguments(lib):
     assert lib.sbm_create(None, ctypes.byref(out)) == 1 and out.value is None
     assert lib.sbm_apply_f64(None, None, None, None) == 1
     assert lib.sbm_sizes(None, None, None, None, None) == 1
+    assert lib.sbm_apply_f64_host(None, None, None, None) == 1
+    assert lib.sbm_bicgstab_mixed(None, None, None, 1e-10, 10, 0, None, None, None, None) == 1
+    assert lib.sbm_batch_solve(None, None, None, 0, 1e-10, 10, 1e-2, 10, None, None, None,
+                               None) == 1
+    assert lib.sbm_batch_create(None, 0, 1, 0, ctypes.byref(out)) == 1
+    lib.sbm_batch_destroy(None)   # no-op
     lib.sbm_destroy(None)   # no-op
 
 
@@ -68,6 +74,15 @@ def test_apply_before_device_setup_is_a_state_error():
     with pytest.raises(G.SbmError) as e:
         G.sbm_apply_f64(P.handle, 16, 16, 0)
     assert G.STATUS[e.value.status] == "SBM_ERR_ARG"
+    # the host-buffer apply and the solvers check the state before any device work
+    for call in (lambda: G.sbm_apply_f64_host(P.handle, 16, 32, 0),
+                 lambda: G.sbm_bicgstab(P.handle, 16, 32, rtol=1e-10, maxit=10, stream=0),
+                 lambda: G.sbm_bicgstab_mixed(P.handle, 16, 32, rtol=1e-10, maxit=10,
+                                              stream=0),
+                 lambda: G.sbm_solve_ir(P.handle, 16, 32, stream=0)):
+        with pytest.raises(G.SbmError) as e:
+            call()
+        assert G.STATUS[e.value.status] == "SBM_ERR_STATE"
 
 
 def _compare_geometry(w):
