@@ -160,13 +160,29 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(v, dist, dev):
+    """The largest of every rank's v (the job's time is its slowest rank's)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank in `seconds` (the max over ranks): weak scaling."""
+    return world * units_per_rank / seconds
+
+
 def dist_init(n):
     import torch
     if n <= 1 or "RANK" not in os.environ:
         return 0, 1, None
     import torch.distributed as dist
-    backend = "nccl" if torch.cuda.is_available() else "gloo"
-    dist.init_process_group(backend)
+    if not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return dist.get_rank(), dist.get_world_size(), dist
 
 
@@ -262,10 +278,7 @@ def time_applies(P, fn, x, y, steps, warmup, st, dist=None, dev=None, clocks=Non
     ms = e0.elapsed_time(e1)
     phases, launches = G.sbm_profile_read(P.handle)
     G.sbm_profile_enable(P.handle, False)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     return ms, [p / steps for p in phases], launches, clk
 
 
@@ -693,16 +706,12 @@ def run_ours(args, w):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         P.apply_f64_host(xh, yh)
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
 
     if rank != 0:
         return
-    value = world * n * args.steps / (ms * 1e-3) / 1e9
-    value32 = world * n * args.steps / (ms32 * 1e-3) / 1e9
+    value = job_rate(world, n * args.steps, ms * 1e-3) / 1e9
+    value32 = job_rate(world, n * args.steps, ms32 * 1e-3) / 1e9
     pk, pk_src = peaks()
     cfma, cadd = cell_ops(w.dim, w.degree, P.n_cells)
     cflops = 2 * cfma + cadd
@@ -723,7 +732,7 @@ def run_ours(args, w):
                    "tile_shape_f64_f32": list(shapes),
                    "l2": f"inputs larger than L2: x, y, colour buffers and tables "
                          f"{(2 * 8 * n + 8 * 8 * n) / 1e6:.0f} MB > 129 MB"},
-        "e2e": {"value": world * n * e2e_steps / e2e_s / 1e9, "unit": "GDoF/s",
+        "e2e": {"value": job_rate(world, n * e2e_steps, e2e_s) / 1e9, "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": FP64_PIPE_GOPS,
