@@ -106,135 +106,187 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
     if (EXT) Tv[tl] = Xf[kend * sk + bt];
   }
   __syncthreads();
-  // 2. to the tangential Gauss points (Taylor: also the value and its
-  //    derivatives along the tangential axes ta, tb -- axis ta is the one
-  //    of stride sa, interpolated first)
-  T dg = T(0), uv = T(0), da = T(0), db = T(0);
-  if (D == 3) {
-    if (act) {
-      const int qa = tl % N, jb = tl / N;
-      T dv = T(0), va = T(0), vd = T(0);
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        dv = fma(t.S[qa][j], Td[j + N * jb], dv);
-        if (EXT) {
-          va = fma(t.S[qa][j], Tv[j + N * jb], va);
-          vd = fma(t.Dg[qa][j], Tv[j + N * jb], vd);
-        }
-      }
-      Da[tl] = dv;
-      if (EXT) {
-        VA[tl] = va;
-        VD[tl] = vd;
-      }
-    }
-    __syncthreads();
-    if (act) {
-      const int qa = tl % N, qb = tl / N;
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        dg = fma(t.S[qb][j], Da[qa + N * j], dg);
-        if (EXT) {
-          uv = fma(t.S[qb][j], VA[qa + N * j], uv);
-          da = fma(t.S[qb][j], VD[qa + N * j], da);
-          db = fma(t.Dg[qb][j], VA[qa + N * j], db);
-        }
-      }
-    }
-  } else {
-    if (act) {
-#pragma unroll
-      for (int j = 0; j < N; ++j) {
-        dg = fma(t.S[tl][j], Td[j], dg);
-        if (EXT) {
-          uv = fma(t.S[tl][j], Tv[j], uv);
-          da = fma(t.Dg[tl][j], Tv[j], da);
-        }
-      }
-    }
-  }
-  // 3. the extension at x~_q, pointwise integrands
-  if (act && EXT) {
-    // E u = u + d . grad u, grad = (1/h) reference gradient; reference
-    // derivatives: along k dg, along ta da, along tb db
-    const T* dq = a.face_phi + ((size_t)f * L + tl) * D;
-    const int ta = (D == 2) ? 1 - k : (k == 0 ? 1 : 0);
-    const int tb = (k == 2) ? 1 : 2;
-    T g = fma(__ldg(dq + k), dg, __ldg(dq + ta) * da);
-    if (D == 3) g = fma(__ldg(dq + tb), db, g);
-    const T e = fma(t.h_inv, g, uv);
-    const T W = t.W[tl];
-    val[tl] = W * (t.sigma * e - sg * t.h_inv * dg);
-    grd[tl] = -W * e * sg * t.h_inv;
-  }
-  if (act && !EXT) {
-    const T* pq = a.face_phi + ((size_t)f * L + tl) * D * N;
-    T p0[N], p1[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      p0[j] = __ldg(pq + j);
-      p1[j] = __ldg(pq + N + j);
-    }
-    T e = T(0);
+  T rv = T(0), rg = T(0);
+  if constexpr (EXT == 0) {
+    // 2. the exact extension: the normal-derivative integrand is a multiple
+    //    of E u, and the normal-derivative trace enters only through
+    //    (S x S)^T diag(W) (S x S) Td = h^(d-1) (M x M) Td (the face's Gauss
+    //    rule is exact for it), so one transposed interpolation (of W E)
+    //    and one mass product replace the interpolation of Td and two
+    //    transposed interpolations
+    T tm = T(0);                  // (M x M) Td at tangential node tl
     if (D == 3) {
-      T p2[N];
+      if (act) {
+        const int ia = tl % N, jb = tl / N;
+        T v = T(0);
 #pragma unroll
-      for (int j = 0; j < N; ++j) p2[j] = __ldg(pq + 2 * N + j);
+        for (int j = 0; j < N; ++j) v = fma(t.M[ia][j], Td[j + N * jb], v);
+        Da[tl] = v;
+      }
+      __syncthreads();
+      if (act) {
+        const int ia = tl % N, ib = tl / N;
 #pragma unroll
-      for (int j2 = 0; j2 < N; ++j2) {
-        T s1 = T(0);
+        for (int j = 0; j < N; ++j) tm = fma(t.M[ib][j], Da[ia + N * j], tm);
+      }
+    } else if (act) {
+#pragma unroll
+      for (int j = 0; j < N; ++j) tm = fma(t.M[tl][j], Td[j], tm);
+    }
+    // 3. E u at the shifted point of Gauss point tl, weighted
+    if (act) {
+      const T* pq = a.face_phi + ((size_t)f * L + tl) * D * N;
+      T p0[N], p1[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        p0[j] = __ldg(pq + j);
+        p1[j] = __ldg(pq + N + j);
+      }
+      T e = T(0);
+      if (D == 3) {
+        T p2[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) p2[j] = __ldg(pq + 2 * N + j);
+#pragma unroll
+        for (int j2 = 0; j2 < N; ++j2) {
+          T s1 = T(0);
+#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1) {
+            T s0 = T(0);
+#pragma unroll
+            for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xf[j0 + N * j1 + N * N * j2], s0);
+            s1 = fma(p1[j1], s0, s1);
+          }
+          e = fma(p2[j2], s1, e);
+        }
+      } else {
 #pragma unroll
         for (int j1 = 0; j1 < N; ++j1) {
           T s0 = T(0);
 #pragma unroll
-          for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xf[j0 + N * j1 + N * N * j2], s0);
-          s1 = fma(p1[j1], s0, s1);
+          for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xf[j0 + N * j1], s0);
+          e = fma(p1[j1], s0, e);
         }
-        e = fma(p2[j2], s1, e);
       }
-    } else {
-#pragma unroll
-      for (int j1 = 0; j1 < N; ++j1) {
-        T s0 = T(0);
-#pragma unroll
-        for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xf[j0 + N * j1], s0);
-        e = fma(p1[j1], s0, e);
-      }
-    }
-    const T W = t.W[tl];
-    val[tl] = W * (t.sigma * e - sg * t.h_inv * dg);
-    grd[tl] = -W * e * sg * t.h_inv;
-  }
-  __syncthreads();
-  // 4. transposed interpolation back to the tangential nodes
-  T rv = T(0), rg = T(0);
-  if (D == 3) {
-    if (act) {
-      const int ja = tl % N, qb = tl / N;
-      T v1 = T(0), v2 = T(0);
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        v1 = fma(t.S[q][ja], val[q + N * qb], v1);
-        v2 = fma(t.S[q][ja], grd[q + N * qb], v2);
-      }
-      Va[tl] = v1;
-      Ga[tl] = v2;
+      val[tl] = t.W[tl] * e;
     }
     __syncthreads();
-    if (act) {
-      const int ja = tl % N, jb = tl / N;
+    // 4. q = (S x S)^T (W E) at tangential node tl
+    T q = T(0);
+    if (D == 3) {
+      if (act) {
+        const int ja = tl % N, qb = tl / N;
+        T v = T(0);
 #pragma unroll
-      for (int q = 0; q < N; ++q) {
-        rv = fma(t.S[q][jb], Va[ja + N * q], rv);
-        rg = fma(t.S[q][jb], Ga[ja + N * q], rg);
+        for (int g = 0; g < N; ++g) v = fma(t.S[g][ja], val[g + N * qb], v);
+        Va[tl] = v;
+      }
+      __syncthreads();
+      if (act) {
+        const int ja = tl % N, jb = tl / N;
+#pragma unroll
+        for (int g = 0; g < N; ++g) q = fma(t.S[g][jb], Va[ja + N * g], q);
+      }
+    } else if (act) {
+#pragma unroll
+      for (int g = 0; g < N; ++g) q = fma(t.S[g][tl], val[g], q);
+    }
+    // value test: sigma E - dn u (h^-1 for the physical derivative); normal-
+    // derivative test: -E (with the outward sign and h^-1)
+    rv = fma(t.sigma, q, -(sg * t.h_inv * t.hface) * tm);
+    rg = -(sg * t.h_inv) * q;
+  } else {
+    // 2. first-order Taylor extension: the normal derivative, the value and
+    //    its derivatives along the tangential axes ta, tb at the tangential
+    //    Gauss points (axis ta is the one of stride sa, interpolated first)
+    T dg = T(0), uv = T(0), da = T(0), db = T(0);
+    if (D == 3) {
+      if (act) {
+        const int qa = tl % N, jb = tl / N;
+        T dv = T(0), va = T(0), vd = T(0);
+  #pragma unroll
+        for (int j = 0; j < N; ++j) {
+          dv = fma(t.S[qa][j], Td[j + N * jb], dv);
+          if (EXT) {
+            va = fma(t.S[qa][j], Tv[j + N * jb], va);
+            vd = fma(t.Dg[qa][j], Tv[j + N * jb], vd);
+          }
+        }
+        Da[tl] = dv;
+        if (EXT) {
+          VA[tl] = va;
+          VD[tl] = vd;
+        }
+      }
+      __syncthreads();
+      if (act) {
+        const int qa = tl % N, qb = tl / N;
+  #pragma unroll
+        for (int j = 0; j < N; ++j) {
+          dg = fma(t.S[qb][j], Da[qa + N * j], dg);
+          if (EXT) {
+            uv = fma(t.S[qb][j], VA[qa + N * j], uv);
+            da = fma(t.S[qb][j], VD[qa + N * j], da);
+            db = fma(t.Dg[qb][j], VA[qa + N * j], db);
+          }
+        }
+      }
+    } else {
+      if (act) {
+  #pragma unroll
+        for (int j = 0; j < N; ++j) {
+          dg = fma(t.S[tl][j], Td[j], dg);
+          if (EXT) {
+            uv = fma(t.S[tl][j], Tv[j], uv);
+            da = fma(t.Dg[tl][j], Tv[j], da);
+          }
+        }
       }
     }
-  } else {
-    if (act) {
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        rv = fma(t.S[q][tl], val[q], rv);
-        rg = fma(t.S[q][tl], grd[q], rg);
+    // 3. the extension at x~_q, pointwise integrands
+    if (act && EXT) {
+      // E u = u + d . grad u, grad = (1/h) reference gradient; reference
+      // derivatives: along k dg, along ta da, along tb db
+      const T* dq = a.face_phi + ((size_t)f * L + tl) * D;
+      const int ta = (D == 2) ? 1 - k : (k == 0 ? 1 : 0);
+      const int tb = (k == 2) ? 1 : 2;
+      T g = fma(__ldg(dq + k), dg, __ldg(dq + ta) * da);
+      if (D == 3) g = fma(__ldg(dq + tb), db, g);
+      const T e = fma(t.h_inv, g, uv);
+      const T W = t.W[tl];
+      val[tl] = W * (t.sigma * e - sg * t.h_inv * dg);
+      grd[tl] = -W * e * sg * t.h_inv;
+    }
+    __syncthreads();
+    // 4. transposed interpolation back to the tangential nodes
+    if (D == 3) {
+      if (act) {
+        const int ja = tl % N, qb = tl / N;
+        T v1 = T(0), v2 = T(0);
+  #pragma unroll
+        for (int q = 0; q < N; ++q) {
+          v1 = fma(t.S[q][ja], val[q + N * qb], v1);
+          v2 = fma(t.S[q][ja], grd[q + N * qb], v2);
+        }
+        Va[tl] = v1;
+        Ga[tl] = v2;
+      }
+      __syncthreads();
+      if (act) {
+        const int ja = tl % N, jb = tl / N;
+  #pragma unroll
+        for (int q = 0; q < N; ++q) {
+          rv = fma(t.S[q][jb], Va[ja + N * q], rv);
+          rg = fma(t.S[q][jb], Ga[ja + N * q], rg);
+        }
+      }
+    } else {
+      if (act) {
+  #pragma unroll
+        for (int q = 0; q < N; ++q) {
+          rv = fma(t.S[q][tl], val[q], rv);
+          rg = fma(t.S[q][tl], grd[q], rg);
+        }
       }
     }
   }
