@@ -675,11 +675,14 @@ def run_ours(args, w):
             "dofs_per_s": P.n_dofs / (t2 - t0),
             "gpu_geometry": {"create_s": t4 - t3, "device_setup_s": t5 - t4,
                              "dofs_per_s": P.n_dofs / (t5 - t3)},
-            "face_table_bytes_per_dof": (P.n_sfaces * (w.degree + 1) ** (w.dim - 1) * w.dim
-                                         * (w.degree + 1) * 8) / P.n_dofs,
+            "face_table_bytes_per_dof": (P.n_sfaces * (w.degree + 1) ** (w.dim - 1)
+                                         * (w.dim * (w.degree + 1)
+                                            + ((w.degree + 1) ** 2 if w.dim == 3 else 0))
+                                         * 8) / P.n_dofs,
             "note": "sbm_create (host) or sbm_create_gpu (geometry stage on the GPU, numbering "
                     "on the host) + sbm_setup_face_data; face table = FP64 1D values at the "
-                    "shifted points (the FP32 copy adds half)"}
+                    "shifted points and, in 3D, their products over the two non-first axes "
+                    "(the FP32 copy adds half)"}
     shapes = G.sbm_autotune(P.handle)       # tile shapes of the FP64 / FP32 cell kernel
     x_host = S.random_vector(w.seed, P.n_dofs, w.dist)
     x = torch.from_numpy(x_host).to(dev)

@@ -136,6 +136,8 @@ static void free_device(DeviceData* dd) {
   cudaFree(dd->ycol32);
   cudaFree(dd->face_phi);
   cudaFree(dd->face_phi32);
+  cudaFree(dd->face_pp);
+  cudaFree(dd->face_pp32);
   cudaFree(dd->nbr);
   cudaFree(dd->stage_x);
   cudaFree(dd->stage_y);
@@ -360,6 +362,10 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
       goto err;
   }
   if ((e = device_face_phi(hp, fsrc, &dd->face_phi, &dd->face_phi32)) != cudaSuccess) goto err;
+  if (d == 3 && hp.desc.extension == SBM_EXT_EXACT &&
+      (e = device_face_pp((int64_t)fsrc.size(), L, n, dd->face_phi, &dd->face_pp,
+                          &dd->face_pp32)) != cudaSuccess)
+    goto err;
   if (dd->nslab > 1) {
     // copy streams and events of the pipelined host-buffer apply
     const unsigned fl = cudaEventDisableTiming;

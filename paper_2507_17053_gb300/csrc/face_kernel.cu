@@ -31,6 +31,7 @@ struct FaceArgs {
   const int32_t* __restrict__ face_cell;   // face -> ordered cell position
   const int32_t* __restrict__ face_kind;   // k | (s << 2)
   const T* __restrict__ face_phi;          // [F][L][D][N], or the shifts [F][L][D] (Taylor)
+  const T* __restrict__ face_pp;           // 3D exact: [F][N^2][L] products of axes 1 and 2
   T* __restrict__ out;                     // [F][2L]
   int face0, nface;                        // this launch: faces [face0, nface)
   int dg;
@@ -133,33 +134,33 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
 #pragma unroll
       for (int j = 0; j < N; ++j) tm = fma(t.M[tl][j], Td[j], tm);
     }
-    // 3. E u at the shifted point of Gauss point tl, weighted
+    // 3. E u at the shifted point of Gauss point tl, weighted.  3D:
+    //    E u = sum_j0 phi_j0 sum_{j1,j2} P[j1 + n j2] u[j0, j1, j2] with the
+    //    stored products P of the other two axes' values: n^3 + n FMAs
+    //    instead of n^3 + n^2 + n
     if (act) {
       const T* pq = a.face_phi + ((size_t)f * L + tl) * D * N;
-      T p0[N], p1[N];
+      T p0[N];
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        p0[j] = __ldg(pq + j);
-        p1[j] = __ldg(pq + N + j);
-      }
+      for (int j = 0; j < N; ++j) p0[j] = __ldg(pq + j);
       T e = T(0);
       if (D == 3) {
-        T p2[N];
+        const T* pp = a.face_pp + (size_t)f * N * N * L + tl;
+        T acc[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) p2[j] = __ldg(pq + 2 * N + j);
+        for (int j0 = 0; j0 < N; ++j0) acc[j0] = T(0);
 #pragma unroll
-        for (int j2 = 0; j2 < N; ++j2) {
-          T s1 = T(0);
+        for (int j12 = 0; j12 < N * N; ++j12) {
+          const T w = __ldg(pp + (size_t)j12 * L);
 #pragma unroll
-          for (int j1 = 0; j1 < N; ++j1) {
-            T s0 = T(0);
-#pragma unroll
-            for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xf[j0 + N * j1 + N * N * j2], s0);
-            s1 = fma(p1[j1], s0, s1);
-          }
-          e = fma(p2[j2], s1, e);
+          for (int j0 = 0; j0 < N; ++j0) acc[j0] = fma(w, Xf[j0 + N * j12], acc[j0]);
         }
+#pragma unroll
+        for (int j0 = 0; j0 < N; ++j0) e = fma(p0[j0], acc[j0], e);
       } else {
+        T p1[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) p1[j] = __ldg(pq + N + j);
 #pragma unroll
         for (int j1 = 0; j1 < N; ++j1) {
           T s0 = T(0);
@@ -309,6 +310,7 @@ static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* 
   a.face_cell = dd.face_cell;
   a.face_kind = dd.face_kind;
   a.face_phi = face_phi_of<T>(dd);
+  a.face_pp = face_pp_of<T>(dd);
   a.out = out;
   a.face0 = fb;
   a.nface = fe;
