@@ -101,12 +101,15 @@ def cell_ops(d, p, n_cells):
 
 
 def face_flops(d, p, n_sfaces):
-    """FLOPs of the surrogate-face kernel per apply: point evaluation
-    n^(2d-1) + n^(2d-2) + n^d FMAs per face (Algorithm 3's dominant step) plus
-    8 n^d FMAs of sum-factorised trace/interpolation/integration and the fold
-    of the face result into the cell (n^d)."""
+    """FLOPs of the surrogate-face kernel per apply (exact extension): point
+    evaluation per face (Algorithm 3's dominant step) n^(2d-1) + n^d FMAs in
+    3D (with the stored products of two axes' values), n^3 + n^2 in 2D; plus
+    7 n^d FMAs: the normal-derivative trace, its mass product (2 sweeps), one
+    transposed interpolation (2 sweeps) and the fold of the face result into
+    the cell."""
     n = p + 1
-    return 2 * (n ** (2 * d - 1) + n ** (2 * d - 2) + n ** d + 9 * n ** d) * n_sfaces
+    point = n ** 5 + n ** 3 if d == 3 else n ** 3 + n ** 2
+    return 2 * (point + 7 * n ** d) * n_sfaces
 
 
 def peaks():
