@@ -93,3 +93,24 @@ def test_lagrange_derivative_matches_difference_quotient():
     e = 1e-6
     fd = (basis1d.lagrange(nodes, t + e) - basis1d.lagrange(nodes, t - e)) / (2 * e)
     np.testing.assert_allclose(basis1d.lagrange_deriv(nodes, t), fd, atol=1e-6)
+
+
+@pytest.mark.parametrize("p", range(1, 7))
+def test_face_gauss_round_trip_is_the_exact_mass(p):
+    """With p+1 Gauss points the round trip 'interpolate nodal values to the
+    Gauss points, weight, interpolate back' is the exact 1D mass matrix
+    S^T diag(w) S = M, M_ij = int_0^1 phi_i phi_j: the identity the face
+    kernels use to integrate the face terms that are linear in nodal traces
+    in mass form.  M is computed independently by a (2p+4)-point Gauss rule;
+    with p points instead of p+1 the identity fails (degree 2p exceeds
+    2p-1)."""
+    nodes = basis1d.gll_nodes(p)
+    g, w = basis1d.gauss_rule(p + 1)
+    S = basis1d.lagrange(nodes, g)                     # [q][j] = phi_j(g_q)
+    gh, wh = basis1d.gauss_rule(2 * p + 4)
+    Sh = basis1d.lagrange(nodes, gh)
+    M = Sh.T @ np.diag(wh) @ Sh
+    np.testing.assert_allclose(S.T @ np.diag(w) @ S, M, atol=1e-14)
+    gl, wl = basis1d.gauss_rule(p)
+    Sl = basis1d.lagrange(nodes, gl)
+    assert np.abs(Sl.T @ np.diag(wl) @ Sl - M).max() > 1e-6
