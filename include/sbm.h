@@ -202,7 +202,11 @@ int sbm_apply_f64(sbm_problem* prob, const double* x, double* y, void* stream);
  * the previous slab's cells) and the copy of the part of y the slab
  * completes overlap, on streams of the problem ordered after the caller's
  * stream.  The result is bitwise that of sbm_apply_f64.  Page-locked host
- * arrays let the copies run concurrently with the kernels.
+ * arrays let the copies run concurrently with the kernels; with them the
+ * pipeline is captured into a CUDA graph on the first call for a given
+ * (x_host, y_host) pair and tile shape and replayed afterwards (the four
+ * most recent pairs are kept).  Calls on one problem must not overlap (they
+ * share the staging buffers and streams).
  */
 int sbm_apply_f64_host(sbm_problem* prob, const double* x_host, double* y_host, void* stream);
 
