@@ -137,7 +137,6 @@ static void free_device(DeviceData* dd) {
   cudaFree(dd->face_phi);
   cudaFree(dd->face_phi32);
   cudaFree(dd->face_pp);
-  cudaFree(dd->face_pp32);
   cudaFree(dd->nbr);
   cudaFree(dd->stage_x);
   cudaFree(dd->stage_y);
@@ -363,8 +362,8 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
   }
   if ((e = device_face_phi(hp, fsrc, &dd->face_phi, &dd->face_phi32)) != cudaSuccess) goto err;
   if (d == 3 && hp.desc.extension == SBM_EXT_EXACT &&
-      (e = device_face_pp((int64_t)fsrc.size(), L, n, dd->face_phi, &dd->face_pp,
-                          &dd->face_pp32)) != cudaSuccess)
+      (e = device_face_pp((int64_t)fsrc.size(), L, n, dd->face_phi, &dd->face_pp)) !=
+          cudaSuccess)
     goto err;
   if (dd->nslab > 1) {
     // copy streams and events of the pipelined host-buffer apply

@@ -19,6 +19,8 @@
 //   R[node (kend, jt)] += rv[jt],  R[node (j, jt)] += phi_j'(s) rg[jt].
 // Output: out[f * 2L + jt] = rv[jt], out[f * 2L + L + jt] = rg[jt].  Faces
 // write disjoint slots, so there is no ordering hazard and no atomics.
+#include <type_traits>
+
 #include "sweeps.cuh"
 
 namespace sbm {
@@ -31,7 +33,7 @@ struct FaceArgs {
   const int32_t* __restrict__ face_cell;   // face -> ordered cell position
   const int32_t* __restrict__ face_kind;   // k | (s << 2)
   const T* __restrict__ face_phi;          // [F][L][D][N], or the shifts [F][L][D] (Taylor)
-  const T* __restrict__ face_pp;           // 3D exact: [F][N^2][L] products of axes 1 and 2
+  const T* __restrict__ face_pp;           // 3D exact, FP64: [F][N^2][L] products of axes 1, 2
   T* __restrict__ out;                     // [F][2L]
   int face0, nface;                        // this launch: faces [face0, nface)
   int dg;
@@ -134,17 +136,37 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
 #pragma unroll
       for (int j = 0; j < N; ++j) tm = fma(t.M[tl][j], Td[j], tm);
     }
-    // 3. E u at the shifted point of Gauss point tl, weighted.  3D:
+    // 3. E u at the shifted point of Gauss point tl, weighted.  3D FP64:
     //    E u = sum_j0 phi_j0 sum_{j1,j2} P[j1 + n j2] u[j0, j1, j2] with the
     //    stored products P of the other two axes' values: n^3 + n FMAs
-    //    instead of n^3 + n^2 + n
+    //    instead of n^3 + n^2 + n (FP32: the products cost less than their
+    //    loads, the 1D values are contracted axis by axis)
     if (act) {
       const T* pq = a.face_phi + ((size_t)f * L + tl) * D * N;
       T p0[N];
 #pragma unroll
       for (int j = 0; j < N; ++j) p0[j] = __ldg(pq + j);
       T e = T(0);
-      if (D == 3) {
+      if (D == 3 && !std::is_same<T, double>::value) {
+        T p1[N], p2[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          p1[j] = __ldg(pq + N + j);
+          p2[j] = __ldg(pq + 2 * N + j);
+        }
+#pragma unroll
+        for (int j2 = 0; j2 < N; ++j2) {
+          T s1 = T(0);
+#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1) {
+            T s0 = T(0);
+#pragma unroll
+            for (int j0 = 0; j0 < N; ++j0) s0 = fma(p0[j0], Xf[j0 + N * j1 + N * N * j2], s0);
+            s1 = fma(p1[j1], s0, s1);
+          }
+          e = fma(p2[j2], s1, e);
+        }
+      } else if (D == 3) {
         const T* pp = a.face_pp + (size_t)f * N * N * L + tl;
         T acc[N];
 #pragma unroll

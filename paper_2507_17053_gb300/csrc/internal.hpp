@@ -94,9 +94,9 @@ cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, 
 cudaError_t device_face_phi(const HostProblem& hp, const std::vector<int64_t>& fsrc,
                             double** phi, float** phi32);
 // 3D exact extension: the per-point products of the two non-first axes'
-// values from the FP64 table phi ([F][Q][3][n]) into pp / pp32 ([F][n^2][Q]),
+// values from the FP64 table phi ([F][Q][3][n]) into pp ([F][n^2][Q]),
 // allocated here.
-cudaError_t device_face_pp(int64_t F, int L, int n, const double* phi, double** pp, float** pp32);
+cudaError_t device_face_pp(int64_t F, int L, int n, const double* phi, double** pp);
 
 // Device-resident set-up data of one problem.
 struct DeviceData {
@@ -125,10 +125,10 @@ struct DeviceData {
   // at the shifted point; first-order Taylor: [F * Q * d] the shift d_q
   double* face_phi = nullptr;
   float* face_phi32 = nullptr;   // the same table rounded to FP32
-  // 3D exact extension: [F][n^2][Q] the products phi_j1(xi_{q,1}) phi_j2(xi_{q,2})
-  // of the two non-first axes, index j1 + n j2 (point index fastest)
+  // 3D exact extension (FP64 face kernel): [F][n^2][Q] the products
+  // phi_j1(xi_{q,1}) phi_j2(xi_{q,2}) of the two non-first axes, index
+  // j1 + n j2 (point index fastest)
   double* face_pp = nullptr;
-  float* face_pp32 = nullptr;
   int32_t* nbr = nullptr;        // DG [Nc * 2d] neighbour rank per (k, s), -1 = surrogate
   double* stage_x = nullptr;     // host-apply staging buffers (allocated on first use)
   double* stage_y = nullptr;
@@ -212,7 +212,7 @@ template <> inline const double* face_phi_of<double>(const DeviceData& dd) { ret
 template <> inline const float* face_phi_of<float>(const DeviceData& dd) { return dd.face_phi32; }
 template <typename T> inline const T* face_pp_of(const DeviceData& dd);
 template <> inline const double* face_pp_of<double>(const DeviceData& dd) { return dd.face_pp; }
-template <> inline const float* face_pp_of<float>(const DeviceData& dd) { return dd.face_pp32; }
+template <> inline const float* face_pp_of<float>(const DeviceData&) { return nullptr; }
 
 // Surrogate faces on the tensor cores (3D, FP32 apply): face_mode
 // SBM_FACE_TF32 or SBM_FACE_BF16; same output as launch_face_kernel.

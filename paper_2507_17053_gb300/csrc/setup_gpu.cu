@@ -564,7 +564,7 @@ cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, 
 
 // pp[(f n^2 + j12) L + q] = phi[f][q][1][j1] phi[f][q][2][j2], j12 = j1 + n j2
 __global__ void k_face_pp(int64_t F, int L, int n, const double* __restrict__ phi,
-                          double* __restrict__ pp, float* __restrict__ pp32) {
+                          double* __restrict__ pp) {
   const int64_t nn = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < F * nn * L;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -574,22 +574,17 @@ __global__ void k_face_pp(int64_t F, int L, int n, const double* __restrict__ ph
     const int64_t f = fj / nn;
     const int j1 = j12 % n, j2 = j12 / n;
     const double* pq = phi + ((size_t)f * L + q) * 3 * n;
-    const double v = pq[n + j1] * pq[2 * n + j2];
-    pp[t] = v;
-    pp32[t] = (float)v;
+    pp[t] = pq[n + j1] * pq[2 * n + j2];
   }
 }
 
-cudaError_t device_face_pp(int64_t F, int L, int n, const double* phi, double** pp, float** pp32) {
+cudaError_t device_face_pp(int64_t F, int L, int n, const double* phi, double** pp) {
   *pp = nullptr;
-  *pp32 = nullptr;
   if (F == 0) return cudaSuccess;
   const size_t cnt = (size_t)F * n * n * L;
   cudaError_t e;
-  if ((e = cudaMalloc((void**)pp, cnt * 8)) != cudaSuccess ||
-      (e = cudaMalloc((void**)pp32, cnt * 4)) != cudaSuccess)
-    return e;
-  k_face_pp<<<grid_for((int64_t)cnt), 256>>>(F, L, n, phi, *pp, *pp32);
+  if ((e = cudaMalloc((void**)pp, cnt * 8)) != cudaSuccess) return e;
+  k_face_pp<<<grid_for((int64_t)cnt), 256>>>(F, L, n, phi, *pp);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaDeviceSynchronize();
 }
