@@ -38,9 +38,10 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (CUDA cores) nominal dense rate
 # FMA = the nominal 1.25 TFLOP/s).  The FP64 apply is bound by this pipe.
 SMS, SM_MAX_MHZ, FP64_LANES_PER_SM_CLK = 152, 2070, 2
 FP64_PIPE_GOPS = SMS * SM_MAX_MHZ * 1e6 * FP64_LANES_PER_SM_CLK / 1e9
-# DRAM bytes (read + write) of one launch of the FP64 cell kernel, from one
-# ncu capture per (workload, tile shape) of the kernel as it stands
-# (profiles/apply_f64_sphere3d_q4_n96_kernels.md); other shapes: not captured
+# DRAM bytes (read + write) of one launch of the FP64 cell kernel: constants
+# from one ncu capture per (workload, tile shape) of the kernel as it stood
+# when captured (dram__bytes_read.sum + dram__bytes_write.sum), not measured
+# by this run; other shapes: not captured
 CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 0): 127.59e6 + 107.57e6,
                 ("sphere3d_cg_q4_n96", 1): 157.950720e6 + 133.191680e6}
 L2_BYTES = 129 * 1024 * 1024

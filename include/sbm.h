@@ -510,6 +510,26 @@ int sbm_set_tile_shape(sbm_problem* prob, int shape64, int shape32);
  */
 int sbm_selftest_timeout(sbm_problem* prob, void* stream);
 
+/* ---- seeded inputs ------------------------------------------------------- */
+enum { SBM_DIST_UNIFORM = 0, SBM_DIST_NORMAL = 1 };
+
+/*
+ * The input generator of the benchmark workloads ("x ~ U(-1,1) from seed s";
+ * the paper names no generator, so this is the library's convention), for C
+ * callers that want the same vectors as the Python workload descriptions.
+ * Counter-based splitmix64 (Steele, Lea, Flood, OOPSLA 2014): value k of
+ * stream `seed` is the splitmix64 finaliser of seed + (k+1) * 0x9E3779B97F4A7C15
+ * (mod 2^64); u_k = (value >> 11) * 2^-53 in [0, 1).
+ *   SBM_DIST_UNIFORM  out[i] = 2 u_{offset+i} - 1                      (U(-1,1))
+ *   SBM_DIST_NORMAL   out[i] = sqrt(-2 log1p(-u_2j)) cos(2 pi u_2j+1), j = offset+i
+ *                     (Box--Muller, cosine branch; N(0,1))
+ * out_host: n doubles of host memory, written in order (a problem's vector
+ * is filled in its global DoF order).  Host only, synchronous, no CUDA call;
+ * uses the C library's log1p and cos, compiled without fused multiply-adds.
+ * Errors: SBM_ERR_ARG (n < 0, NULL output with n > 0, unknown dist).
+ */
+int sbm_fill_random(int64_t n, uint64_t seed, uint64_t offset, int dist, double* out_host);
+
 /* Human-readable name of a status code (static string). */
 const char* sbm_error_string(int status);
 

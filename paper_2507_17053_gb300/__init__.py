@@ -123,6 +123,8 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_int)]),
     "sbm_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "sbm_selftest_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sbm_fill_random": (ctypes.c_int, [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_int, ctypes.c_void_p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "sbm_last_error_detail": (ctypes.c_char_p, []),
 }
@@ -354,6 +356,19 @@ def sbm_selftest_timeout(handle: int, stream=None) -> None:
 
 def sbm_profile_enable(handle: int, on: bool) -> None:
     _check(lib().sbm_profile_enable(handle, int(bool(on))), "sbm_profile_enable")
+
+
+DIST = {"uniform": 0, "normal": 1}
+
+
+def sbm_fill_random(n: int, seed: int, dist="uniform", offset: int = 0):
+    """The library's seeded input generator: a numpy float64 array of n
+    values (U(-1,1) or N(0,1)) from stream ``seed`` starting at ``offset``."""
+    import numpy as np
+    out = np.empty(n, dtype=np.float64)
+    _check(lib().sbm_fill_random(n, seed & 0xFFFFFFFFFFFFFFFF, offset, DIST.get(dist, -1),
+                                 out.ctypes.data), "sbm_fill_random")
+    return out
 
 
 def sbm_profile_read(handle: int) -> tuple[list, int]:

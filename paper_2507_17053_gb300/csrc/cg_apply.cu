@@ -517,12 +517,13 @@ cudaError_t launch_cg_apply_slab(const HostProblem& hp, const DeviceData& dd, co
 // ([F][2L]) and colour buffers ([ncolours][n_dofs]).
 template <typename T>
 cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                                    T* face_scratch, T* colour_scratch, cudaStream_t st) {
-  return dispatch<T>(hp, dd, x, y, 0, 1, face_scratch, colour_scratch, 0, 0, st, nullptr);
+                                    T* face_scratch, T* colour_scratch, int variant,
+                                    cudaStream_t st) {
+  return dispatch<T>(hp, dd, x, y, 0, 1, face_scratch, colour_scratch, 0, variant, st, nullptr);
 }
 template cudaError_t launch_cg_apply_scratch<double>(const HostProblem&, const DeviceData&,
                                                      const double*, double*, double*, double*,
-                                                     cudaStream_t);
+                                                     int, cudaStream_t);
 
 // nrhs right-hand sides in one set of launches (grid.y = right-hand side);
 // variant 0/1: R or R/2 cells per chunk (chosen by the autotuner).

@@ -227,10 +227,12 @@ template <typename T>
 cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                             cudaStream_t st, Profiler* prof, int face_mode = 0);
 // Apply, CG, with caller-provided scratch (per-face results [F][2L] and the
-// colour buffers [ncolours][n_dofs]) instead of the problem's own.
+// colour buffers [ncolours][n_dofs]) instead of the problem's own; variant =
+// cell-kernel tile shape (0 or 1).
 template <typename T>
 cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                                    T* face_scratch, T* colour_scratch, cudaStream_t st);
+                                    T* face_scratch, T* colour_scratch, int variant,
+                                    cudaStream_t st);
 // Apply, DG: one launch.
 template <typename T>
 cudaError_t launch_dg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,

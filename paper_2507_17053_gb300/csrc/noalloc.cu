@@ -66,8 +66,9 @@ extern "C" int sbm_apply_f64_noalloc(sbm_problem* prob, const double* x, double*
   // colour mask is set), so nothing has to be cleared first.
   double* face_scratch = reinterpret_cast<double*>(base);
   double* colour_scratch = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + face_bytes);
+  // the same cell tile shape as sbm_apply_f64 (the autotuned or pinned one)
   e = launch_cg_apply_scratch<double>(prob->hp, dd, x, y, face_scratch, colour_scratch,
-                                      (cudaStream_t)stream);
+                                      dd.variant[0], (cudaStream_t)stream);
   if (e != cudaSuccess) return sbm_cuda_fail_detail(e, "sbm_apply_f64_noalloc");
   return SBM_OK;
 }

@@ -15,7 +15,9 @@ throughout the repository):
   number generators", OOPSLA 2014).
 * U(-1, 1): ``u = (z >> 11) * 2**-53`` in [0, 1), value ``2u - 1``.
 * N(0, 1): Box--Muller on consecutive pairs (u1, u2) of [0,1) uniforms,
-  ``sqrt(-2 ln(1 - u1)) * cos(2 pi u2)`` (cosine branch only).
+  ``sqrt(-2 ln(1 - u1)) * cos(2 pi u2)`` (cosine branch only), with the C
+  library's log1p and cos.
+* The library exports the same generator (``sbm_fill_random``), bit for bit.
 * Vectors are filled in the global DoF order of the problem they belong to.
 """
 from __future__ import annotations
@@ -47,15 +49,24 @@ def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
     return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
-def uniform_pm1(seed: int, n: int) -> np.ndarray:
-    """U(-1, 1) input vector of length n."""
-    return 2.0 * uniform01(seed, n) - 1.0
+def uniform_pm1(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """U(-1, 1) input vector: values offset .. offset+n-1 of the stream."""
+    return 2.0 * uniform01(seed, n, offset) - 1.0
 
 
-def normal(seed: int, n: int) -> np.ndarray:
-    """N(0, 1) input vector of length n (Box--Muller, cosine branch)."""
-    u = uniform01(seed, 2 * n).reshape(n, 2)
-    return np.sqrt(-2.0 * np.log1p(-u[:, 0])) * np.cos(2.0 * math.pi * u[:, 1])
+# the C library's log1p and cos, element by element: numpy's vectorised
+# versions differ from it (and between machines) in the last bit
+_log1p = np.frompyfunc(math.log1p, 1, 1)
+_cos = np.frompyfunc(math.cos, 1, 1)
+
+
+def normal(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """N(0, 1) input vector of length n (Box--Muller, cosine branch): value
+    j = offset + i from the uniform pair (u_2j, u_2j+1)."""
+    u = uniform01(seed, 2 * n, 2 * offset).reshape(n, 2)
+    lg = _log1p(-u[:, 0]).astype(np.float64)
+    cs = _cos(2.0 * math.pi * u[:, 1]).astype(np.float64)
+    return np.sqrt(-2.0 * lg) * cs
 
 
 def random_vector(seed: int, n: int, dist: str) -> np.ndarray:

@@ -138,3 +138,37 @@ def test_host_rhs_and_interpolant_match_oracle(w):
         u1 = lambda X: 2.0 * np.cos(X[..., 0]) * np.sin(X[..., 1])
         ref1 = O.rhs(lambda X: 2.0 * u1(X), u1)
         assert np.abs(P.rhs(1) - ref1).max() <= 1e-13 * np.abs(ref1).max()
+
+
+@pytest.mark.parametrize("dist", ["uniform", "normal"])
+@pytest.mark.parametrize("seed,offset", [(0, 0), (1, 0), (3, 17), (4 * 1000003 + 21, 5),
+                                         (2 ** 64 - 1, 1000), (12345, 2 ** 40)])
+def test_fill_random_matches_the_workload_generator(dist, seed, offset):
+    """The exported generator gives the workload vectors bit for bit: the
+    same splitmix64 values, the same 53-bit uniforms, the same Box--Muller
+    arithmetic (C library log1p and cos, no fused multiply-adds)."""
+    n = 2000
+    got = G.sbm_fill_random(n, seed, dist, offset)
+    ref = S.uniform_pm1(seed, n, offset) if dist == "uniform" else S.normal(seed, n, offset)
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
+    if offset == 0:
+        assert np.array_equal(got, S.random_vector(seed, n, dist))
+    # a window of a longer stream is the same numbers
+    tail = G.sbm_fill_random(n - 7, seed, dist, offset + 7)
+    assert np.array_equal(tail, got[7:])
+
+
+def test_fill_random_distributions_and_errors(lib):
+    u = G.sbm_fill_random(200000, 9, "uniform")
+    assert u.min() >= -1.0 and u.max() < 1.0 and abs(u.mean()) < 0.01
+    z = G.sbm_fill_random(200000, 9, "normal")
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+    # the first stream value of seed 0 is the published splitmix64 output
+    # for state 0 (the generator's first call): 0xE220A8397B1DCDAF
+    first = S.splitmix64(0, 1)[0]
+    assert int(first) == 0xE220A8397B1DCDAF
+    assert u.size == 200000 and G.sbm_fill_random(0, 1, "uniform").size == 0
+    assert lib.sbm_fill_random(-1, 0, 0, 0, None) == 1
+    assert lib.sbm_fill_random(4, 0, 0, 0, None) == 1
+    buf = (ctypes.c_double * 4)()
+    assert lib.sbm_fill_random(4, 0, 0, 7, buf) == 1

@@ -12,6 +12,9 @@ from oracle.operator import Problem as OracleProblem
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
+# FP32 apply against the FP64 oracle on FP32-rounded x (measured on a GB300:
+# at most 1.5e-7 for p = 1..6; about 3x that)
+F32_TOL = 5e-7
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -146,11 +149,11 @@ def test_autotuned_tile_shapes_keep_parity(w):
     assert _rel(P.apply_f64(xd).cpu().numpy(), ref) <= TOL
     ref32 = O.apply(x.astype(np.float32).astype(np.float64))
     y32 = P.apply_f32(xd.float()).double().cpu().numpy()
-    assert _rel(y32, ref32) <= 1e-5 * w.degree
+    assert _rel(y32, ref32) <= F32_TOL
     # each shape pinned explicitly
     for s in (0, 1):
         G.sbm_set_tile_shape(P.handle, s, s)
         assert _rel(P.apply_f64(xd).cpu().numpy(), ref) <= TOL
-        assert _rel(P.apply_f32(xd.float()).double().cpu().numpy(), ref32) <= 1e-5 * w.degree
+        assert _rel(P.apply_f32(xd.float()).double().cpu().numpy(), ref32) <= F32_TOL
     with pytest.raises(G.SbmError):
         G.sbm_set_tile_shape(P.handle, 2, 0)

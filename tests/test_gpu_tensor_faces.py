@@ -12,9 +12,12 @@ from oracle.operator import Problem as OracleProblem, sin_solution
 
 pytestmark = pytest.mark.gpu
 
-# relative max-norm error bounds against the FP64 oracle (measured values are
-# reported in the design notes): TF32 keeps 10 mantissa bits, BF16 7
-BOUND = {"tf32": 1e-2, "bf16": 8e-2}
+# relative max-norm error bounds against the FP64 oracle, per degree, about
+# 3x the largest error measured on a GB300 for these cases (TF32 keeps 10
+# mantissa bits, BF16 7; measured TF32 1.9e-4 .. 4.3e-4, BF16 1.3e-3 ..
+# 2.6e-3, the p = 2 sphere and p = 3 sphere/torus the largest)
+BOUND = {"tf32": {1: 6e-4, 2: 1.3e-3, 3: 1e-3, 4: 6e-4, 5: 7.5e-4, 6: 9e-4},
+         "bf16": {1: 4e-3, 2: 7.5e-3, 3: 8e-3, 4: 5e-3, 5: 7e-3, 6: 6e-3}}
 
 CASES = [S.SPHERE_3D_Q4.resized(10), S.ELLIPSOID_3D_Q6.resized(8),
          S.SPHERE_3D_Q4.resized(7, degree=2), S.SPHERE_3D_Q4.resized(7, degree=3),
@@ -44,7 +47,8 @@ def test_tensor_face_apply_error(w, mode):
     G.sbm_device_status(P.handle)
     err_tc, err_fp32 = _rel(y_tc, ref), _rel(y_fp32, ref)
     print(f"{w.name} q{w.degree} {mode}: {err_tc:.3e} (fp32 faces {err_fp32:.3e})")
-    assert err_tc <= BOUND[mode]
+    assert err_tc <= BOUND[mode][w.degree]
+    assert err_fp32 <= 5e-7
     # the tensor-core path really ran (it rounds differently from FP32) and a
     # second call gives the same bits
     assert not np.array_equal(y_tc, y_fp32)

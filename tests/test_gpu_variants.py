@@ -75,7 +75,8 @@ F32_CASES = [S.DISK_2D_Q2, S.SPHERE_3D_Q4.resized(12), S.ELLIPSOID_3D_Q6.resized
 def test_f32_apply_error_vs_oracle(w):
     """FP32 apply: relative max-norm error against the FP64 oracle is at the
     FP32 rounding level amplified by the extrapolation at shifted points
-    (bound 1e-5 * p; measured values are reported in the design notes)."""
+    (measured on a GB300: 4e-8 .. 1.5e-7 for p = 1..6, 2D and 3D; bound
+    5e-7, about 3x the largest)."""
     O = OracleProblem.from_workload(w)
     P = G.Problem.from_workload(w)
     x = S.random_vector(w.seed, O.n_dofs, w.dist)
@@ -83,4 +84,4 @@ def test_f32_apply_error_vs_oracle(w):
     ref = O.apply(x.astype(np.float32).astype(np.float64))
     err = _rel(y, ref)
     print(f"{w.name}: fp32 rel err {err:.3e}")
-    assert err <= 1e-5 * w.degree
+    assert err <= 5e-7

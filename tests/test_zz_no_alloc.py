@@ -45,14 +45,24 @@ def test_noalloc_apply_matches_apply_twice(w):
         assert _call_noalloc(P, x, y) == 0, G.lib().sbm_last_error_detail()
         torch.cuda.synchronize()
         assert np.abs(y.cpu().numpy() - ref).max() <= TOL * scale
-    # a second problem in between must not leave anything the next call reads
-    Q = G.Problem.from_workload(S.DISK_2D_Q2.resized(20, degree=3))
-    xq = torch.from_numpy(S.random_vector(9, Q.n_dofs, "uniform")).cuda()
-    assert _call_noalloc(Q, xq, torch.empty_like(xq)) == 0
-    y = torch.empty_like(x)
-    assert _call_noalloc(P, x, y) == 0
-    torch.cuda.synchronize()
-    assert np.abs(y.cpu().numpy() - ref).max() <= TOL * scale
+    # other problems in between, with x full of NaN, leave NaN wherever their
+    # face results and colour buffers fall in the shared array (these cover
+    # a larger region than P's): a value of P's call read before written
+    # would come out NaN
+    for wq in (S.DISK_2D_Q2.resized(20, degree=3), S.SPHERE_3D_Q4.resized(24),
+               S.ELLIPSOID_3D_Q6.resized(10), S.SPHERE_3D_Q4.resized(16, degree=2)):
+        Q = G.Problem.from_workload(wq)
+        xq = torch.full((Q.n_dofs,), float("nan"), dtype=torch.float64, device="cuda")
+        yq = torch.empty_like(xq)
+        assert _call_noalloc(Q, xq, yq) == 0, G.lib().sbm_last_error_detail()
+        torch.cuda.synchronize()
+        assert torch.isnan(yq).all()
+        y = torch.full_like(x, float("nan"))
+        assert _call_noalloc(P, x, y) == 0
+        torch.cuda.synchronize()
+        yh = y.cpu().numpy()
+        assert np.isfinite(yh).all()
+        assert np.abs(yh - ref).max() <= TOL * scale
 
 
 def test_noalloc_rejects_oversized_and_dg_problems():
