@@ -270,20 +270,35 @@ typedef struct sbm_batch sbm_batch;
 
 /*
  * A batch of independent continuous Galerkin problems (any sizes, degrees,
- * geometries), each with nrhs right-hand sides, applied together: every
- * problem's right-hand sides go through one launch of each of its kernels
- * (grid.y = right-hand side), the problems run on a pool of streams, and the
- * whole batch is one CUDA-graph launch (captured on the first call for a
- * given set of vector pointers, replayed afterwards).
+ * geometries), each with nrhs right-hand sides, applied together in ONE
+ * persistent kernel launch (the paper applies one problem at a time; this
+ * batches many).  The launch's blocks
+ * stay resident and take work items from a device ticket counter: first
+ * the surrogate-face items (ranges of faces, Algorithm 3), then the cell
+ * chunk items (ranges of chunks: gather, cell term of Algorithm 1, face
+ * folds, single-writer stores; each waits until its system's face items are
+ * done), then the assembly items (the DoFs several colours share; each
+ * waits for its system's chunk items).  Items are sized and ordered by the
+ * paper's load-balancing weights (Section 3.5: 10 per cell, plus 40 per
+ * surrogate face in 3D and 20 in 2D), scaled across degrees by the cell's
+ * sum-factorisation cost (p+1)^(d+1), heaviest first within each phase.
+ * Every dependency wait is bounded: on expiry the kernel records
+ * SBM_ERR_TIMEOUT (sbm_batch_device_status) instead of hanging.  The
+ * counter reset and the launch are captured into a CUDA graph on the first
+ * call for a given set of vector pointers (eight kept per precision) and
+ * replayed afterwards.
  * probs: nprob problems, all set up (sbm_setup_face_data) on the current
  * device; the batch keeps the pointers (do not destroy a problem before its
- * batch).  autotune_shapes != 0 times the cell kernel's two tile shapes (128
- * or 256 threads' worth of cell lines per block) on the largest problem of
- * every degree and keeps the faster one for all problems of that degree.
- * Device scratch: nrhs copies of each problem's per-face results and colour
- * buffers, per precision, allocated on first use.  Synchronous.
+ * batch).  autotune_shapes != 0 runs the autotuner: per precision and per
+ * degree it times every combination of the cell kernel's tile shape (chunks
+ * of R or R/2 cells, R = 256 / (p+1)^(d-1)) and the face batch (256 or 128
+ * threads' worth of faces per pass) on that degree's problems and keeps the
+ * fastest (sbm_batch_knobs reports the choice and the timings); without it
+ * every degree uses shape 0 and the full face batch.  Device scratch: nrhs
+ * copies of each problem's per-face results and colour buffers, per
+ * precision, allocated on first use (all or nothing).  Synchronous.
  * Errors: SBM_ERR_ARG, SBM_ERR_STATE, SBM_ERR_UNSUPPORTED (DG problem),
- * SBM_ERR_OOM, SBM_ERR_CUDA.
+ * SBM_ERR_OOM, SBM_ERR_CUDA, SBM_ERR_TIMEOUT (a wait expired while tuning).
  */
 int sbm_batch_create(sbm_problem* const* probs, int nprob, int nrhs, int autotune_shapes,
                      sbm_batch** out);
@@ -291,17 +306,50 @@ int sbm_batch_create(sbm_problem* const* probs, int nprob, int nrhs, int autotun
 /*
  * y_k = A_k x_k for every problem k and right-hand side: x[k] and y[k] are
  * device arrays of nrhs * n_dofs_k values (right-hand side r at offset
- * r * n_dofs_k), x[k] != y[k].  The same operator and arithmetic as
- * sbm_apply_f32 / sbm_apply_f64 (bitwise-equal results).  Asynchronous on
- * stream; two batch applies must not overlap (shared scratch).
+ * r * n_dofs_k), x[k] != y[k].  The same operator, arithmetic and summation
+ * order as sbm_apply_f32 / sbm_apply_f64: bitwise-equal results for the
+ * same tile shape.  One graph launch (a counter reset and the persistent
+ * kernel) on stream, asynchronous; two batch applies must not overlap
+ * (shared scratch and counters).
  */
 int sbm_batch_apply_f32(sbm_batch* batch, const float* const* x, float* const* y, void* stream);
 int sbm_batch_apply_f64(sbm_batch* batch, const double* const* x, double* const* y,
                         void* stream);
 
-/* Tile shape (0 or 1) in use for a problem; override it (drops cached graphs). */
+/* Tile shape (0 or 1) of a problem's cell chunks (the FP32 choice; both
+ * precisions after an override); override it for both precisions (drops
+ * the cached graphs; synchronises the device). */
 int sbm_batch_tile_shape(const sbm_batch* batch, int problem, int* variant);
 int sbm_batch_set_tile_shape(sbm_batch* batch, int problem, int variant);
+
+/*
+ * The autotuner's record for one degree and precision (32 or 64):
+ * *tile_shape (0: R cells per chunk, 1: R/2), *face_batch (0: 256/L faces
+ * per pass, 1: 128/L), *tensor_cores (tensor-core face path on: 1, off: 0);
+ * ms[8] (may be NULL): the measured time in ms of that degree's sub-batch
+ * for option index tile_shape + 2 face_batch + 4 tensor_cores, < 0 where
+ * the option was not timed.  Any output may be NULL.
+ * Errors: SBM_ERR_ARG (bad precision, no tuned problem of that degree).
+ */
+int sbm_batch_knobs(const sbm_batch* batch, int precision, int degree, int* tile_shape,
+                    int* face_batch, int* tensor_cores, float* ms);
+
+/*
+ * Synchronise the device and report (then clear) the batch's device error
+ * word: SBM_ERR_TIMEOUT if a bounded dependency wait of an earlier batched
+ * apply expired, SBM_OK otherwise.
+ */
+int sbm_batch_device_status(sbm_batch* batch);
+
+/*
+ * Diagnostic of the persistent kernel's failure path (the paper has no
+ * counterpart): one launch whose only work item waits for a dependency that
+ * nothing produces; the bounded wait expires (about a second), the kernel
+ * records SBM_ERR_TIMEOUT in the batch's error word and returns without
+ * touching any vector.  No fault, no hang; the context stays usable.
+ * Synchronous on stream.
+ */
+int sbm_batch_selftest_timeout(sbm_batch* batch, void* stream);
 
 /* Free the batch (not its problems). */
 void sbm_batch_destroy(sbm_batch* batch);

@@ -111,6 +111,11 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int)]),
     "sbm_batch_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "sbm_batch_destroy": (None, [ctypes.c_void_p]),
+    "sbm_batch_knobs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "sbm_batch_device_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "sbm_batch_selftest_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sbm_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
@@ -454,6 +459,25 @@ class Batch:
 
     def set_tile_shape(self, k, variant):
         _check(lib().sbm_batch_set_tile_shape(self.handle, k, variant), "sbm_batch_set_tile_shape")
+
+    def knobs(self, precision, degree):
+        """The autotuner's choice for one degree: dict with tile_shape,
+        face_batch, tensor_cores and ms (the timed options, index shape +
+        2 face_batch + 4 tensor_cores; None where not timed)."""
+        v, f, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_float * 8)()
+        _check(lib().sbm_batch_knobs(self.handle, precision, degree, ctypes.byref(v),
+                                     ctypes.byref(f), ctypes.byref(t), ms), "sbm_batch_knobs")
+        return {"tile_shape": v.value, "face_batch": f.value, "tensor_cores": t.value,
+                "ms": [float(m) if m >= 0 else None for m in ms]}
+
+    def device_status(self):
+        """Raises SbmError if a bounded wait of an earlier batched apply expired."""
+        _check(lib().sbm_batch_device_status(self.handle), "sbm_batch_device_status")
+
+    def selftest_timeout(self, stream=None):
+        _check(lib().sbm_batch_selftest_timeout(self.handle, _stream(stream)),
+               "sbm_batch_selftest_timeout")
 
 
 def _current_device() -> int:

@@ -1,4 +1,5 @@
-// A batch of independent continuous Galerkin problems (batch.cu: applies;
+// A batch of independent continuous Galerkin problems (batch.cu: the
+// persistent batched apply and its autotuner; batch_kernel.cuh: the kernel;
 // batch_solve.cu: solves).
 #pragma once
 
@@ -6,6 +7,25 @@
 #include <vector>
 
 #include "internal.hpp"
+
+namespace sbm {
+namespace bk {
+struct Item;
+template <typename T>
+struct ProbTable;
+// per precision (batch_f32.cu / batch_f64.cu)
+cudaError_t set_unit_table(int n, const KTab<double>& t);
+cudaError_t set_unit_table(int n, const KTab<float>& t);
+size_t item_smem_f64(int d, int n, int v, int fh, int ext);
+size_t item_smem_f32(int d, int n, int v, int fh, int ext);
+cudaError_t occupancy_f64(size_t smem, int* per_sm);
+cudaError_t occupancy_f32(size_t smem, int* per_sm);
+cudaError_t launch(const ProbTable<double>& tab, const Item* items, int nitems, int nsys,
+                   int nrhs, int* cnt, int* err, size_t smem, int grid, cudaStream_t st);
+cudaError_t launch(const ProbTable<float>& tab, const Item* items, int nitems, int nsys, int nrhs,
+                   int* cnt, int* err, size_t smem, int grid, cudaStream_t st);
+}  // namespace bk
+}  // namespace sbm
 
 // Device workspace of the batched solver, kept across solves so that the
 // batched applies it issues reuse their cached graphs.
@@ -27,25 +47,61 @@ struct BatchSolveWs {
   std::vector<int64_t> off;        // [nprob] first element of each problem
 };
 
-struct sbm_batch {
-  std::vector<sbm_problem*> probs;
-  int nrhs = 0;
-  int device = 0;
-  std::vector<int> order;           // problems, largest first
-  std::vector<int> variant;         // cell-kernel tile shape per problem
-  std::map<int, int> tuned;         // degree -> variant
-  std::vector<cudaStream_t> streams;
-  cudaStream_t cap = nullptr;
-  cudaEvent_t fork = nullptr;
-  std::vector<cudaEvent_t> join;
-  std::vector<float*> face32, col32;
-  std::vector<double*> face64, col64;
+// Knobs of one degree for one precision, chosen by the autotuner: the cell
+// kernel's tile shape (0: R cells per chunk, 1: R/2), the face batch (0:
+// 256/L faces per pass, 1: 128/L), and the measured time of every option
+// tried (ms of that degree's sub-batch; index shape + 2 * face batch; < 0:
+// not tried).
+struct DegreeKnobs {
+  int shape = 0, face_batch = 0;
+  float ms[4] = {-1.f, -1.f, -1.f, -1.f};
+};
+
+// One launch of the persistent kernel: up to bk::kLaunchProbs problems of
+// the batch (global indices in probs; the work list uses local ones), their
+// work list for the current knobs, the launch shape and the offset of its
+// dependency counters.
+struct LaunchPlan {
+  std::vector<int> probs;
+  void* items = nullptr;             // device work list
+  int nitems = 0;
+  std::vector<int> nface_items, nchunk_items;   // [local problem] items per right-hand side
+  size_t smem = 0;                   // dynamic shared memory per block
+  int grid = 0;
+  int cnt_off = 0;                   // ticket + 2 counters per system, from here
+};
+
+// Per-precision state of the batched apply: knobs, launch plans and the
+// captured graphs (one per set of vector pointers).
+struct BatchPrec {
+  std::vector<int> shape;            // [nprob] tile shape per problem
+  std::map<int, DegreeKnobs> knobs;  // degree -> knobs
+  bool dirty = true;                 // plans to rebuild
+  std::vector<LaunchPlan> plans;
+  int* cnt = nullptr;                // device counters of all plans
+  std::vector<void*> face, col;      // [nprob] scratch: nrhs face results / colour buffers
+  void* ktab = nullptr;              // [nprob] device copies of the problems' tables
   struct Graph {
     std::vector<const void*> ptrs;
-    int prec;
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
+};
+
+// Host copies of a problem's chunk boundaries, both tile shapes (for the
+// work list).
+struct ChunkHost {
+  std::vector<int32_t> first[2];
+};
+
+struct sbm_batch {
+  std::vector<sbm_problem*> probs;
+  std::vector<ChunkHost> ch;         // [nprob]
+  int nrhs = 0;
+  int device = 0;
+  cudaStream_t cap = nullptr;        // capture / tuning stream
+  int* err = nullptr;                // device error word (SBM_ERR_TIMEOUT from bounded waits)
+  BatchPrec prec[2];                 // [0] FP32, [1] FP64
   BatchSolveWs ws;
 };
 

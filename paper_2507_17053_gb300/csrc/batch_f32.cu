@@ -1,0 +1,32 @@
+// The persistent batched apply in FP32: the kernel instantiation,
+// its constant-memory unit tables and the host entry points (batch_kernel.cuh).
+#include "batch.hpp"
+#include "batch_kernel.cuh"
+
+namespace sbm {
+namespace bk {
+
+// h-independent 1D tables of degree n - 1 at index n
+__constant__ KTab<float> c_unit_f32[kMaxN + 1];
+
+struct U_f32 {
+  template <int N>
+  __device__ __forceinline__ static const KTab<float>& tab() {
+    return c_unit_f32[N];
+  }
+};
+
+using L_f32 = Launcher<float, U_f32>;
+
+cudaError_t set_unit_table(int n, const KTab<float>& t) {
+  return cudaMemcpyToSymbol(c_unit_f32, &t, sizeof(t), (size_t)n * sizeof(t));
+}
+size_t item_smem_f32(int d, int n, int v, int fh, int ext) { return L_f32::smem(d, n, v, fh, ext); }
+cudaError_t occupancy_f32(size_t smem, int* per_sm) { return L_f32::occupancy(smem, per_sm); }
+cudaError_t launch(const ProbTable<float>& tab, const Item* items, int nitems, int nsys, int nrhs,
+                   int* cnt, int* err, size_t smem, int grid, cudaStream_t st) {
+  return L_f32::launch(tab, items, nitems, nsys, nrhs, cnt, err, smem, grid, st);
+}
+
+}  // namespace bk
+}  // namespace sbm

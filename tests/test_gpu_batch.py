@@ -123,3 +123,62 @@ def test_batch_solve_rejects_bad_arguments():
     assert st == G.SBM_OK and np.all(relres == 0.0)
     assert all(float(x.abs().max()) == 0.0 for x in xs)
     B.close()
+
+
+def test_batch_8rhs_matches_oracle_elementwise():
+    """The persistent batched apply, 8 right-hand sides per problem, against
+    the FP64 oracle element by element: FP64 within 1e-12 and FP32 within
+    5e-7 (relative max norm per system); the autotuner's per-degree choices
+    are recorded with the timings of the options it tried."""
+    from oracle.operator import Problem as OracleProblem
+    ws = S.batched_ellipsoids(nprob=5, n_range=(5, 9)) + [S.DISK_2D_Q2.resized(9, degree=3)]
+    ps = [G.Problem.from_workload(w) for w in ws]
+    os_ = [OracleProblem.from_workload(w) for w in ws]
+    nrhs = 8
+    B = G.Batch(ps, nrhs, autotune=True)
+    xs = [np.concatenate([S.random_vector(S.rhs_seed(w, r), p.n_dofs, "uniform")
+                          for r in range(nrhs)]) for w, p in zip(ws, ps)]
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 5e-7)):
+        xd = [torch.from_numpy(x).to("cuda", dt) for x in xs]
+        ys = [torch.full_like(x, float("nan")) for x in xd]
+        B.apply(xd, ys)
+        B.device_status()
+        for p, O, x, y in zip(ps, os_, xs, ys):
+            yh = y.double().cpu().numpy()
+            for r in range(nrhs):
+                sl = slice(r * p.n_dofs, (r + 1) * p.n_dofs)
+                xr = x[sl] if dt == torch.float64 else x[sl].astype(np.float32).astype(np.float64)
+                ref = O.apply(xr)
+                err = float(np.abs(yh[sl] - ref).max() / np.abs(ref).max())
+                assert err <= tol, (p.n_dofs, r, err)
+    for prec in (32, 64):
+        for deg in sorted({w.degree for w in ws}):
+            k = B.knobs(prec, deg)
+            assert k["tile_shape"] in (0, 1) and k["face_batch"] in (0, 1)
+            timed = [m for m in k["ms"][:4] if m is not None]
+            assert len(timed) == 4 and all(m > 0 for m in timed)
+            best = k["tile_shape"] + 2 * k["face_batch"]
+            assert k["ms"][best] == min(timed)
+    with pytest.raises(G.SbmError):
+        B.knobs(64, 9)
+    B.close()
+
+
+def test_batch_bounded_wait_expires_without_hang():
+    """A work item whose dependency nothing produces: the persistent kernel's
+    bounded wait expires, SBM_ERR_TIMEOUT is reported, and the batch (and
+    the context) stays usable."""
+    ws, ps = _problems()
+    B = G.Batch(ps[:2], 1, autotune=False)
+    B.selftest_timeout()
+    with pytest.raises(G.SbmError) as e:
+        B.device_status()
+    assert G.STATUS[e.value.status] == "SBM_ERR_TIMEOUT"
+    B.device_status()           # cleared
+    xs = [torch.ones(p.n_dofs, dtype=torch.float64, device="cuda") for p in ps[:2]]
+    ys = [torch.empty_like(x) for x in xs]
+    B.apply(xs, ys)
+    B.device_status()
+    for p, x, y in zip(ps[:2], xs, ys):
+        assert torch.equal(y, p.apply_f64(x))
+    B.close()
