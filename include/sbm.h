@@ -374,7 +374,7 @@ enum { SBM_BATCH_SOLVE_FP64 = 0, SBM_BATCH_SOLVE_MIXED = 1 };
  *    solve reduced its residual; a system leaves the refinement once its
  *    residual no longer halves per step; at most maxit refinements; systems
  *    above rtol then finish with the FP64 BiCGStab from their current x
- *    (at most 20000 iterations).
+ *    (at most min(20000, maxit * inner_maxit) iterations).
  * b[k], x[k]: device arrays of nrhs * n_dofs_k doubles, laid out as for
  * sbm_batch_apply (x is output only; the solve starts from 0).
  * iters[k * nrhs + r] (optional, host): BiCGStab iterations of that system
@@ -465,7 +465,8 @@ enum { SBM_INNER_GMRES = 0, SBM_INNER_BICGSTAB = 1, SBM_INNER_BICGSTAB_MIXED = 2
  * first (an inner solve without progress, or max_outer steps spent) -- the
  * FP32 operator's rounding, about condition number x 6e-8 of |b|, limits what
  * an inner solve can reach -- FP64 BiCGStab continues from x to rtol (at most
- * 20000 iterations; counted as one more outer step).  *iters = inner
+ * min(20000, max_outer * inner_maxit) iterations; counted as one more outer
+ * step).  *iters = inner
  * iterations in total, including that finish (a BiCGStab iteration applies
  * the operator twice), *outer = outer steps; same conventions otherwise.
  */
@@ -557,6 +558,19 @@ int sbm_set_tile_shape(sbm_problem* prob, int shape64, int shape32);
  * sbm_device_status reports it.  No fault, no hang; the context stays usable.
  */
 int sbm_selftest_timeout(sbm_problem* prob, void* stream);
+
+/* ---- measurement aids ---------------------------------------------------- */
+
+/*
+ * Fused multiply-add throughput of the current GPU (a measurement aid for
+ * the roofline of the cell kernels; the paper has no counterpart): a kernel
+ * of independent fma.rn chains (8 per thread, 8 blocks of 256 threads per
+ * SM), timed with CUDA events on stream (best of five launches after a
+ * warm-up).  *gfma_per_s receives G FMA thread-operations per second
+ * (x 2 = GFLOP/s).  precision: 64 (double) or 32 (float).  Synchronous;
+ * about 0.1 s.  Errors: SBM_ERR_ARG, SBM_ERR_CUDA.
+ */
+int sbm_peak_probe(int precision, double* gfma_per_s, void* stream);
 
 /* ---- seeded inputs ------------------------------------------------------- */
 enum { SBM_DIST_UNIFORM = 0, SBM_DIST_NORMAL = 1 };

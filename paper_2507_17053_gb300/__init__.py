@@ -128,6 +128,8 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_int)]),
     "sbm_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "sbm_selftest_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "sbm_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_void_p]),
     "sbm_fill_random": (ctypes.c_int, [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                                        ctypes.c_int, ctypes.c_void_p]),
     "sbm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -361,6 +363,13 @@ def sbm_selftest_timeout(handle: int, stream=None) -> None:
 
 def sbm_profile_enable(handle: int, on: bool) -> None:
     _check(lib().sbm_profile_enable(handle, int(bool(on))), "sbm_profile_enable")
+
+
+def sbm_peak_probe(precision: int = 64, stream=None) -> float:
+    """Measured FMA rate of the current GPU: G FMA thread-operations/s."""
+    v = ctypes.c_double()
+    _check(lib().sbm_peak_probe(precision, ctypes.byref(v), _stream(stream)), "sbm_peak_probe")
+    return v.value
 
 
 DIST = {"uniform": 0, "normal": 1}

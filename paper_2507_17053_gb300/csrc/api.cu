@@ -117,6 +117,9 @@ static cudaError_t upload(T** dst, const T* src, size_t count) {
 
 static void free_device(DeviceData* dd) {
   cudaFree(dd->lines);
+  cudaFree(dd->reg_cell_chunk);
+  cudaFree(dd->reg_block_first);
+  cudaFree(dd->reg_mask);
   cudaFree(dd->cell_rank);
   cudaFree(dd->face_start);
   cudaFree(dd->face_kind);
@@ -332,6 +335,7 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
                                    dd->chunks[v].first, ycut, &dd->chunks[v])) != cudaSuccess)
         goto err;
     }
+    if ((e = build_cell_reg_tables(hp, ch_first[0], dd)) != cudaSuccess) goto err;
     // ordered positions grouped by the parity colour of the cell (diagonal kernel)
     {
       std::vector<int32_t> pos;
@@ -819,8 +823,8 @@ int sbm_device_status(sbm_problem* prob) {
   return SBM_OK;
 }
 
-// time both tile shapes of the single apply, in FP64 and FP32, on the
-// problem itself, and keep the faster of each
+// time every tile shape of the single apply (2 where available), in FP64
+// and FP32, on the problem itself, and keep the faster of each
 int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32) {
   if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
@@ -840,7 +844,8 @@ int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32) {
   for (int prec = 0; prec < 2 && e == cudaSuccess; ++prec) {
     float best = 1e30f;
     int bestv = 0;
-    for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+    const int nv = cell_reg_available(prob->hp, prec == 1) ? 3 : 2;
+    for (int v = 0; v < nv && e == cudaSuccess; ++v) {
       prob->dd.variant[prec] = v;
       float tot = 0.f;
       for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
@@ -875,10 +880,14 @@ int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32) {
 int sbm_set_tile_shape(sbm_problem* prob, int shape64, int shape32) {
   if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
-  if (shape64 < -1 || shape64 > 1 || shape32 < -1 || shape32 > 1)
-    return fail(SBM_ERR_ARG, "tile shape must be -1, 0 or 1");
-  if (prob->hp.desc.dg && (shape64 == 1 || shape32 == 1))
+  if (shape64 < -1 || shape64 > 2 || shape32 < -1 || shape32 > 2)
+    return fail(SBM_ERR_ARG, "tile shape must be -1, 0, 1 or 2");
+  if (prob->hp.desc.dg && (shape64 >= 1 || shape32 >= 1))
     return fail(SBM_ERR_UNSUPPORTED, "DG applies have one tile shape");
+  if ((shape64 == 2 && !cell_reg_available(prob->hp, false)) ||
+      (shape32 == 2 && !cell_reg_available(prob->hp, true)))
+    return fail(SBM_ERR_UNSUPPORTED,
+                "tile shape 2 needs a 3D problem with p <= 4 (FP32) or p <= 3 (FP64)");
   if (shape64 >= 0) prob->dd.variant[0] = shape64;
   if (shape32 >= 0) prob->dd.variant[1] = shape32;
   return SBM_OK;

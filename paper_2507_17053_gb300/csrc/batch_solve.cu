@@ -30,7 +30,7 @@ constexpr int kTile = 4096;      // elements per reduction tile
 constexpr int kThr = 256;        // threads per tile block
 constexpr int kChunk = 8;        // iterations between host reads of the state
 constexpr int kFinishRestarts = 20;
-constexpr int kFinishMaxit = 20000;   // FP64 finish of the refinement
+constexpr int kFinishMaxit = 20000;   // FP64 finish of the refinement, at most
 
 // per-system BiCGStab state
 struct BSys {
@@ -596,7 +596,9 @@ extern "C" int sbm_batch_solve(sbm_batch* batch, const double* const* b, double*
     }
     if (!any) break;
     const bool zero = mode == SBM_BATCH_SOLVE_FP64 && rs == 0;
-    const int cap = mode == SBM_BATCH_SOLVE_FP64 ? maxit : kFinishMaxit;
+    const int cap = mode == SBM_BATCH_SOLVE_FP64
+                        ? maxit
+                        : (int)std::min<int64_t>(kFinishMaxit, (int64_t)maxit * inner_maxit);
     CKS(bicgstab(c, false, w.b, w.x, zero, rtol, cap, active, hs));
     CKS(residuals(c, w.x, nullptr, rr, bb, false));
     // restart (fresh shadow residual, from the current iterate) a system

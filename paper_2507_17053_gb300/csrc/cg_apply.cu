@@ -101,7 +101,7 @@ struct Part {
 template <typename T, int D, int N, int R>
 static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const ChunkTable& ct,
                            const T* x, T* y, int64_t ld, int nrhs, T* fo, T* ycol, int face_mode,
-                           cudaStream_t st, Profiler* prof, Part part) {
+                           cudaStream_t st, Profiler* prof, Part part, bool reg) {
   constexpr int L = Shape<D, N>::L;
   const KTab<T> t = make_ktab<T>(hp);
   constexpr size_t smem = ChunkSmem<T, D, N, R>::bytes;
@@ -113,10 +113,8 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   int nlaunch = 0;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   if (part.f1 > part.f0) {
-    err = (nrhs == 1) ? (face_mode != 0 ? launch_faces<T>(hp, dd, x, fo, face_mode, st)
-                                        : launch_face_kernel<T>(hp, dd, x, fo, st, part.f0,
-                                                                part.f1))
-                      : launch_face_kernel_multi<T>(hp, dd, x, ld, nrhs, fo, st);
+    err = face_mode != 0 ? launch_faces<T>(hp, dd, x, fo, face_mode, st)
+                         : launch_face_kernel<T>(hp, dd, x, fo, st, part.f0, part.f1);
     if (err != cudaSuccess) return err;
     nlaunch++;
   }
@@ -141,7 +139,10 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   a.ldx = ld;
   a.ld_ycol = (int64_t)dd.ncolours * hp.n_dofs;
   a.ld_face = (int64_t)dd.nface * 2 * L;
-  if (part.q1 > part.q0) {
+  if (reg) {                 // tile shape 2: one thread per cell (cell_reg.cu)
+    if ((err = launch_cell_reg<T>(hp, dd, x, y, fo, ycol, st)) != cudaSuccess) return err;
+    nlaunch++;
+  } else if (part.q1 > part.q0) {
     const int grid = std::min(part.q1 - part.q0, cap);
     cg_chunk_kernel<T, D, N, R><<<dim3(grid, nrhs), R * L, smem, st>>>(a, t);
     nlaunch++;
@@ -163,8 +164,10 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
 }
 
 // variant 0: R cells per chunk; variant 1: R/2 (a second tile shape for the
-// autotuner).  Both chunkings are built at set-up with the same colouring
-// rule, so the two variants give bitwise-equal results.
+// autotuner); variant 2: the cells of variant 0's chunks one thread each
+// (cell_reg.cu; whole applies only -- a slab of the host pipeline runs
+// variant 0, which gives the same bits).  Both chunkings are built at set-up
+// with the same colouring rule, so the variants give bitwise-equal results.
 template <typename T, int D, int N>
 static cudaError_t apply_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                            int64_t ld, int nrhs, T* fo, T* ycol, int face_mode, int variant,
@@ -172,6 +175,8 @@ static cudaError_t apply_t(const HostProblem& hp, const DeviceData& dd, const T*
   constexpr int R = ChunkShape<D, N>::R;
   constexpr int RH = (R / 2) > 0 ? R / 2 : 1;
   const int v = (variant == 1 && RH < R) ? 1 : 0;
+  const bool reg = variant == 2 && slab < 0 && nrhs == 1 &&
+                   cell_reg_available(hp, std::is_same<T, float>::value);
   const ChunkTable& ct = dd.chunks[v];
   Part part;
   if (slab >= 0) {
@@ -184,8 +189,10 @@ static cudaError_t apply_t(const HostProblem& hp, const DeviceData& dd, const T*
     part.m1 = cells ? ct.slab_multi[slab + 1] : part.m0;
   }
   if (v == 1)
-    return apply_r<T, D, N, RH>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part);
-  return apply_r<T, D, N, R>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part);
+    return apply_r<T, D, N, RH>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part,
+                                false);
+  return apply_r<T, D, N, R>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part,
+                             reg);
 }
 
 template <typename T>
@@ -236,21 +243,5 @@ cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd,
 template cudaError_t launch_cg_apply_scratch<double>(const HostProblem&, const DeviceData&,
                                                      const double*, double*, double*, double*,
                                                      int, cudaStream_t);
-
-// nrhs right-hand sides in one set of launches (grid.y = right-hand side);
-// variant 0/1: R or R/2 cells per chunk (chosen by the autotuner).
-template <typename T>
-cudaError_t launch_cg_apply_multi(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                                  int64_t ld, int nrhs, T* face_scratch, T* colour_scratch,
-                                  int variant, cudaStream_t st) {
-  return dispatch<T>(hp, dd, x, y, ld, nrhs, face_scratch, colour_scratch, 0, variant, st,
-                     nullptr);
-}
-template cudaError_t launch_cg_apply_multi<double>(const HostProblem&, const DeviceData&,
-                                                   const double*, double*, int64_t, int, double*,
-                                                   double*, int, cudaStream_t);
-template cudaError_t launch_cg_apply_multi<float>(const HostProblem&, const DeviceData&,
-                                                  const float*, float*, int64_t, int, float*,
-                                                  float*, int, cudaStream_t);
 
 }  // namespace sbm

@@ -21,6 +21,14 @@ __device__ __forceinline__ T ld_face(const T* p) {
   else return __ldg(p);
 }
 
+// Separately rounded product and sum (never contracted into a fused
+// multiply-add): the face folds round the same way in every kernel that
+// applies them, whatever the compiler knows about their operands.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
 template <typename T>
 struct ChunkArgs {
   const T* __restrict__ x;
@@ -58,7 +66,7 @@ __device__ __forceinline__ void fold_face_z(const KTab<T>& t, const T* __restric
 #pragma unroll
     for (int m = 0; m < N; ++m) {
       out[m] = fma(s ? t.D1[m] : t.D0[m], g, out[m]);
-      if (m == kend) out[m] += v;       // compile-time index: out stays in registers
+      if (m == kend) out[m] = add_rn(out[m], v);  // compile-time index: out stays in registers
     }
   } else {
     // k == 0: j_k = a, tangential (j1, j2) = (b, m);  k == 1: j_k = b, (j0, j2) = (a, m)
@@ -68,9 +76,9 @@ __device__ __forceinline__ void fold_face_z(const KTab<T>& t, const T* __restric
 #pragma unroll
     for (int m = 0; m < N; ++m) {
       const int jt = jo + N * m;
-      T add = dk * ld_face<COH>(rg + jt);
-      if (jk == kend) add += ld_face<COH>(rv + jt);
-      out[m] += add;
+      T add = mul_rn(dk, ld_face<COH>(rg + jt));
+      if (jk == kend) add = add_rn(add, ld_face<COH>(rv + jt));
+      out[m] = add_rn(out[m], add);
     }
   }
 }
@@ -89,7 +97,7 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
 #pragma unroll
     for (int m = 0; m < N; ++m) {
       out[m] = fma(s ? t.D1[m] : t.D0[m], g, out[m]);
-      if (m == kend) out[m] += v;       // compile-time index: out stays in registers
+      if (m == kend) out[m] = add_rn(out[m], v);  // compile-time index: out stays in registers
     }
   } else {
     // k == 1: line tl = (j1, j2), tangential (m, j2);  k == 2: tangential (m, j1)
@@ -99,9 +107,9 @@ __device__ __forceinline__ void fold_face(const KTab<T>& t, const T* __restrict_
 #pragma unroll
     for (int m = 0; m < N; ++m) {
       const int jt = m + N * jo;
-      T add = dk * ld_face<COH>(rg + jt);
-      if (jk == kend) add += ld_face<COH>(rv + jt);
-      out[m] += add;
+      T add = mul_rn(dk, ld_face<COH>(rg + jt));
+      if (jk == kend) add = add_rn(add, ld_face<COH>(rv + jt));
+      out[m] = add_rn(out[m], add);
     }
   }
 }

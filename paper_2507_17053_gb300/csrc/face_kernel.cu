@@ -80,22 +80,6 @@ cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, cons
 template cudaError_t launch_face_kernel<double>(const HostProblem&, const DeviceData&,
                                                 const double*, double*, cudaStream_t, int, int);
 
-template <typename T>
-cudaError_t launch_face_kernel_multi(const HostProblem& hp, const DeviceData& dd, const T* x,
-                                     int64_t ldx, int nrhs, T* out, cudaStream_t st) {
-#define SBM_CASE(DD, NN) \
-  if (hp.d == DD && hp.n == NN) return face_x<T, DD, NN>(hp, dd, x, out, st, ldx, nrhs);
-  SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
-  SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
-#undef SBM_CASE
-  return cudaErrorInvalidValue;
-}
-template cudaError_t launch_face_kernel_multi<double>(const HostProblem&, const DeviceData&,
-                                                      const double*, int64_t, int, double*,
-                                                      cudaStream_t);
-template cudaError_t launch_face_kernel_multi<float>(const HostProblem&, const DeviceData&,
-                                                     const float*, int64_t, int, float*,
-                                                     cudaStream_t);
 template cudaError_t launch_face_kernel<float>(const HostProblem&, const DeviceData&,
                                                const float*, float*, cudaStream_t, int, int);
 

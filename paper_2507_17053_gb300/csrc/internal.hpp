@@ -117,6 +117,13 @@ struct DeviceData {
   int* err_flag = nullptr;       // device error word (SBM_ERR_TIMEOUT from bounded waits)
   ChunkTable chunks[2];          // CG: R and R/2 cells per chunk (two tile shapes)
   int variant[2] = {0, 0};       // tile shape of the single applies: [FP64, FP32]
+  // tile shape 2 (3D CG, n <= 5; cell_reg.cu): one thread per cell on the
+  // chunks of shape 0 -- chunk of every ordered cell, blocks of whole
+  // chunks, per-cell bits of the nodes several colours share
+  int32_t* reg_cell_chunk = nullptr;
+  int32_t* reg_block_first = nullptr;
+  uint32_t* reg_mask = nullptr;
+  int reg_nblocks = 0;
   int32_t* diag_pos = nullptr;   // CG: ordered positions grouped by cell parity (diagonal)
   std::vector<int> diag_col_start;
   double* ycol = nullptr;        // CG [ncolours * n_dofs] colour accumulation buffers (scratch)
@@ -190,23 +197,21 @@ template <typename T> inline T* face_out_of(const DeviceData& dd);
 template <> inline double* face_out_of<double>(const DeviceData& dd) { return dd.face_out; }
 template <> inline float* face_out_of<float>(const DeviceData& dd) { return dd.face_out32; }
 
+// Tile shape 2: the cell term with one thread per cell and the tile in
+// registers (cell_reg.cu); available for 3D CG problems with n <= 5 (FP32)
+// or n <= 4 (FP64); bitwise equal to tile shape 0.
+bool cell_reg_available(const HostProblem& hp, bool fp32);
+cudaError_t build_cell_reg_tables(const HostProblem& hp, const std::vector<int32_t>& ch_first,
+                                  DeviceData* dd);
+template <typename T>
+cudaError_t launch_cell_reg(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
+                            const T* fo, T* ycol, cudaStream_t st);
+
 // The surrogate faces [fb, fe) of the kernel face order (all: 0, -1) into
 // the per-face scratch (face_kernel.cu).
 template <typename T>
 cudaError_t launch_face_kernel(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
                                cudaStream_t st, int fb = 0, int fe = -1);
-// The same for nrhs right-hand sides (x: nrhs vectors ldx apart; out: nrhs
-// copies of the per-face scratch).
-template <typename T>
-cudaError_t launch_face_kernel_multi(const HostProblem& hp, const DeviceData& dd, const T* x,
-                                     int64_t ldx, int nrhs, T* out, cudaStream_t st);
-// CG apply of nrhs right-hand sides with caller scratch (face: nrhs*F*2L,
-// colour: nrhs*ncolours*n_dofs); variant = cell-kernel tile shape (0 or 1).
-template <typename T>
-cudaError_t launch_cg_apply_multi(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                                  int64_t ld, int nrhs, T* face_scratch, T* colour_scratch,
-                                  int variant, cudaStream_t st);
-
 template <typename T> inline const T* face_phi_of(const DeviceData& dd);
 template <> inline const double* face_phi_of<double>(const DeviceData& dd) { return dd.face_phi; }
 template <> inline const float* face_phi_of<float>(const DeviceData& dd) { return dd.face_phi32; }

@@ -544,7 +544,7 @@ template SolveStatus solve_gmres<float, float>(const ApplyFn<float>&, int64_t, c
 // shadow residual r^ = r.
 
 constexpr int BI_CHUNK = 8;
-constexpr int kIrFinishMaxit = 20000;   // FP64 BiCGStab finish of the refinement
+constexpr int kIrFinishMaxit = 20000;   // FP64 BiCGStab finish of the refinement, at most
 
 struct BiState {
   double rho, alpha, omega, beta, rr, bb, tol2;
@@ -1074,7 +1074,8 @@ SolveStatus solve_ir(const ApplyFn<double>& apply64, const ApplyFn<float>& apply
     cudaError_t e = bf.setup(apply64, n, b, x, ws);
     SolveInfo fi{};
     SolveStatus s{SBM_ERR_CUDA, e};
-    if (e == cudaSuccess) s = bf.solve(false, rtol, kIrFinishMaxit, st, &fi);
+    const int cap = (int)std::min<int64_t>(kIrFinishMaxit, (int64_t)maxit * inner_maxit);
+    if (e == cudaSuccess) s = bf.solve(false, rtol, cap, st, &fi);
     bf.destroy();
     if (s.status == SBM_ERR_CUDA) {
       info->iters = inner_total;

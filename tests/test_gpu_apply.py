@@ -156,4 +156,44 @@ def test_autotuned_tile_shapes_keep_parity(w):
         assert _rel(P.apply_f64(xd).cpu().numpy(), ref) <= TOL
         assert _rel(P.apply_f32(xd.float()).double().cpu().numpy(), ref32) <= F32_TOL
     with pytest.raises(G.SbmError):
-        G.sbm_set_tile_shape(P.handle, 2, 0)
+        G.sbm_set_tile_shape(P.handle, 3, 0)
+
+
+# tile shape 2: one thread per cell, the tile in registers (3D, FP32 p <= 4,
+# FP64 p <= 3); the same chunks and summation order as shape 0
+REG_CASES = [S.SPHERE_3D_Q4.resized(n, degree=p) for p, n in ((1, 9), (2, 8), (3, 7), (4, 12))] \
+    + [S.ELLIPSOID_3D_Q6.resized(10, degree=4), S.SPHERE_3D_Q4.resized(17, degree=2)] \
+    + S.batched_ellipsoids(nprob=3, n_range=(7, 11), p_range=(2, 4))
+
+
+@pytest.mark.parametrize("w", REG_CASES, ids=lambda w: f"{w.name}_q{w.degree}")
+def test_register_tile_shape_equals_shape0_and_oracle(w):
+    O, P = _pair(w)
+    x = S.random_vector(w.seed, O.n_dofs, w.dist)
+    xd = torch.from_numpy(x).cuda()
+    ref = O.apply(x)
+    ref32 = O.apply(x.astype(np.float32).astype(np.float64))
+    fp64 = w.degree <= 3
+    G.sbm_set_tile_shape(P.handle, 0, 0)
+    y64_0, y32_0 = P.apply_f64(xd), P.apply_f32(xd.float())
+    G.sbm_set_tile_shape(P.handle, 2 if fp64 else 0, 2)
+    y64, y32 = P.apply_f64(xd), P.apply_f32(xd.float())
+    assert torch.equal(y32, y32_0), "shape 2 differs from shape 0 in FP32"
+    assert torch.equal(y32, P.apply_f32(xd.float())), "repeated apply differs"
+    assert _rel(y32.double().cpu().numpy(), ref32) <= F32_TOL
+    if fp64:
+        assert torch.equal(y64, y64_0), "shape 2 differs from shape 0 in FP64"
+    assert _rel(y64.cpu().numpy(), ref) <= TOL
+    # the host-buffer pipeline runs shape 0 for its slabs: the same bits
+    yh = P.apply_f64_host(x)
+    assert np.array_equal(yh, y64.cpu().numpy())
+
+
+def test_register_tile_shape_rejected_where_unavailable():
+    for w, shapes in ((S.SPHERE_3D_Q4.resized(6, degree=5), (-1, 2)),
+                      (S.SPHERE_3D_Q4.resized(6, degree=4), (2, -1)),
+                      (S.DISK_2D_Q2, (-1, 2))):
+        P = G.Problem.from_workload(w)
+        with pytest.raises(G.SbmError) as e:
+            G.sbm_set_tile_shape(P.handle, *shapes)
+        assert G.STATUS[e.value.status] == "SBM_ERR_UNSUPPORTED"
