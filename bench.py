@@ -613,7 +613,9 @@ def batched(G, torch, steps=10):
     ws = S.batched_ellipsoids()
     ps = [G.Problem.from_workload(w) for w in ws]
     nrhs = 8
-    B = G.Batch(ps, nrhs, autotune=True)
+    # the autotuner may choose tensor-core (TF32) faces for the FP32 applies
+    # per degree; it keeps the fastest option and records every timing
+    B = G.Batch(ps, nrhs, autotune=True, tensor_cores=True)
     tot = sum(p.n_dofs for p in ps) * nrhs
     res = {"problems": len(ps), "nrhs": nrhs, "dof_rhs_per_apply": tot,
            "tile_shape_by_degree": {str(w.degree): B.tile_shape(k) for k, w in enumerate(ws)}}

@@ -289,18 +289,23 @@ typedef struct sbm_batch sbm_batch;
  * replayed afterwards.
  * probs: nprob problems, all set up (sbm_setup_face_data) on the current
  * device; the batch keeps the pointers (do not destroy a problem before its
- * batch).  autotune_shapes != 0 runs the autotuner: per precision and per
- * degree it times every combination of the cell kernel's tile shape (chunks
- * of R or R/2 cells, R = 256 / (p+1)^(d-1)) and the face batch (256 or 128
- * threads' worth of faces per pass) on that degree's problems and keeps the
- * fastest (sbm_batch_knobs reports the choice and the timings); without it
- * every degree uses shape 0 and the full face batch.  Device scratch: nrhs
+ * batch).  flags: SBM_BATCH_AUTOTUNE runs the autotuner: per precision and
+ * per degree it times every combination of the cell kernel's tile shape
+ * (chunks of R or R/2 cells, R = 256 / (p+1)^(d-1)), the face batch (256 or
+ * 128 threads' worth of faces per pass) and, with SBM_BATCH_TENSOR_CORES,
+ * tensor-core faces for the FP32 applies (the shifted point evaluation's
+ * first contraction as one TF32 tcgen05.mma per face, FP32 accumulation in
+ * tensor memory; 3D, exact extension; this changes the FP32 results to TF32
+ * accuracy) on that degree's problems and keeps the fastest
+ * (sbm_batch_knobs reports the choice and the timings); without it every
+ * degree uses shape 0, the full face batch and CUDA-core faces.  Device scratch: nrhs
  * copies of each problem's per-face results and colour buffers, per
  * precision, allocated on first use (all or nothing).  Synchronous.
  * Errors: SBM_ERR_ARG, SBM_ERR_STATE, SBM_ERR_UNSUPPORTED (DG problem),
  * SBM_ERR_OOM, SBM_ERR_CUDA, SBM_ERR_TIMEOUT (a wait expired while tuning).
  */
-int sbm_batch_create(sbm_problem* const* probs, int nprob, int nrhs, int autotune_shapes,
+enum { SBM_BATCH_AUTOTUNE = 1, SBM_BATCH_TENSOR_CORES = 2 };
+int sbm_batch_create(sbm_problem* const* probs, int nprob, int nrhs, int flags,
                      sbm_batch** out);
 
 /*
@@ -335,9 +340,20 @@ int sbm_batch_knobs(const sbm_batch* batch, int precision, int degree, int* tile
                     int* face_batch, int* tensor_cores, float* ms);
 
 /*
+ * Pin the knobs of one degree and precision (32 or 64) instead of the
+ * autotuner's choice: tile shape (0, 1), face batch (0, 1), tensor-core
+ * faces (0, 1; FP32 batches created with SBM_BATCH_TENSOR_CORES only).
+ * Drops the cached graphs; synchronises the device.
+ * Errors: SBM_ERR_ARG (bad value, no problem of that degree),
+ * SBM_ERR_UNSUPPORTED (tensor cores not allowed).
+ */
+int sbm_batch_set_knobs(sbm_batch* batch, int precision, int degree, int tile_shape,
+                        int face_batch, int tensor_cores);
+
+/*
  * Synchronise the device and report (then clear) the batch's device error
- * word: SBM_ERR_TIMEOUT if a bounded dependency wait of an earlier batched
- * apply expired, SBM_OK otherwise.
+ * word: SBM_ERR_TIMEOUT if a bounded dependency wait (or a tensor-core MMA's
+ * completion wait) of an earlier batched apply expired, SBM_OK otherwise.
  */
 int sbm_batch_device_status(sbm_batch* batch);
 

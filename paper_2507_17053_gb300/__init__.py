@@ -115,6 +115,7 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "sbm_batch_device_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "sbm_batch_set_knobs": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_int] * 5),
     "sbm_batch_selftest_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sbm_batch_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -395,13 +396,14 @@ def sbm_profile_read(handle: int) -> tuple[list, int]:
 class Batch:
     """Owning wrapper around an sbm_batch (the problems must outlive it)."""
 
-    def __init__(self, problems, nrhs, autotune=True):
+    def __init__(self, problems, nrhs, autotune=True, tensor_cores=False):
         self.problems = list(problems)
         self.nrhs = nrhs
         arr = (ctypes.c_void_p * len(self.problems))(*[p.handle for p in self.problems])
         h = ctypes.c_void_p()
-        _check(lib().sbm_batch_create(arr, len(self.problems), nrhs, int(bool(autotune)),
-                                      ctypes.byref(h)), "sbm_batch_create")
+        flags = (1 if autotune else 0) | (2 if tensor_cores else 0)
+        _check(lib().sbm_batch_create(arr, len(self.problems), nrhs, flags, ctypes.byref(h)),
+               "sbm_batch_create")
         self.handle = h.value
 
     def close(self):
@@ -479,6 +481,10 @@ class Batch:
                                      ctypes.byref(f), ctypes.byref(t), ms), "sbm_batch_knobs")
         return {"tile_shape": v.value, "face_batch": f.value, "tensor_cores": t.value,
                 "ms": [float(m) if m >= 0 else None for m in ms]}
+
+    def set_knobs(self, precision, degree, tile_shape=0, face_batch=0, tensor_cores=0):
+        _check(lib().sbm_batch_set_knobs(self.handle, precision, degree, tile_shape, face_batch,
+                                         tensor_cores), "sbm_batch_set_knobs")
 
     def device_status(self):
         """Raises SbmError if a bounded wait of an earlier batched apply expired."""

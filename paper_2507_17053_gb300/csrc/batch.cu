@@ -19,6 +19,7 @@
 
 #include "batch.hpp"
 #include "batch_kernel.cuh"
+#include "tc_common.cuh"
 
 using namespace sbm;
 using bk::Item;
@@ -35,17 +36,27 @@ constexpr int pidx() {
   return std::is_same<T, double>::value ? 1 : 0;
 }
 
-size_t item_smem(int pi, int d, int n, int v, int fh, int ext) {
-  return pi ? bk::item_smem_f64(d, n, v, fh, ext) : bk::item_smem_f32(d, n, v, fh, ext);
+size_t item_smem(int pi, int d, int n, int v, int fh, int ext, int tc) {
+  return pi ? bk::item_smem_f64(d, n, v, fh, ext, tc) : bk::item_smem_f32(d, n, v, fh, ext, tc);
 }
-cudaError_t occupancy(int pi, size_t smem, int* per_sm) {
-  return pi ? bk::occupancy_f64(smem, per_sm) : bk::occupancy_f32(smem, per_sm);
+cudaError_t occupancy(int pi, size_t smem, bool tc, int* per_sm) {
+  return pi ? bk::occupancy_f64(smem, tc, per_sm) : bk::occupancy_f32(smem, tc, per_sm);
 }
 
 int face_batch_faces(int d, int n, int fh) {
   const int L = (d == 3) ? n * n : n;
   const int ff = bk::kThreads / L;
   return fh ? std::max(1, ff / 2) : ff;
+}
+
+// Tensor-core faces for problem k in precision pi: FP32, 3D, exact
+// extension, allowed for the batch and chosen for the problem's degree.
+int prob_tc(const sbm_batch* B, int pi, int k) {
+  const BatchPrec& P = B->prec[pi];
+  const sbm_problem* p = B->probs[k];
+  if (pi != 0 || !P.allow_tc || p->hp.d != 3 || p->hp.desc.extension != SBM_EXT_EXACT) return 0;
+  auto kn = P.knobs.find(p->hp.p);
+  return kn == P.knobs.end() ? 0 : kn->second.tc;
 }
 
 // ---- scratch -----------------------------------------------------------------
@@ -132,7 +143,8 @@ void make_items(const sbm_batch* B, int pi, const std::vector<int>& probs, int g
     auto kn = P.knobs.find(p->hp.p);
     const int fh = (kn == P.knobs.end() || p->hp.desc.extension == SBM_EXT_TAYLOR1)
                        ? 0 : kn->second.face_batch;
-    const int fpb = face_batch_faces(d, n, fh);
+    // a tensor-core face item runs its faces one at a time
+    const int fpb = prob_tc(B, pi, k) ? 1 : face_batch_faces(d, n, fh);
     // faces: whole passes of fpb faces, about tf weight per item
     std::vector<std::pair<int, int>> fr;
     const int per = std::max(fpb, (int)std::lround(tf / wface / fpb) * fpb);
@@ -185,7 +197,7 @@ size_t prob_smem(const sbm_batch* B, int pi, int k) {
   auto kn = P.knobs.find(p->hp.p);
   const int fh = kn == P.knobs.end() ? 0 : kn->second.face_batch;
   return item_smem(pi, p->hp.d, p->hp.n, P.shape[k], fh,
-                   p->hp.desc.extension == SBM_EXT_TAYLOR1);
+                   p->hp.desc.extension == SBM_EXT_TAYLOR1, prob_tc(B, pi, k));
 }
 
 void free_plans(std::vector<LaunchPlan>* plans) {
@@ -209,13 +221,18 @@ cudaError_t make_plans(const sbm_batch* B, int pi, const std::vector<int>& probs
     L.probs.assign(probs.begin() + g,
                    probs.begin() + std::min(probs.size(), g + (size_t)bk::kLaunchProbs));
     L.smem = smem_min;
-    for (int k : L.probs) L.smem = std::max(L.smem, prob_smem(B, pi, k));
+    for (int k : L.probs) {
+      L.smem = std::max(L.smem, prob_smem(B, pi, k));
+      if (prob_tc(B, pi, k)) L.tc_cols = tc::kTmemCols;
+    }
     int per_sm = 0;
-    if ((e = occupancy(pi, L.smem, &per_sm)) != cudaSuccess) break;
+    if ((e = occupancy(pi, L.smem, L.tc_cols != 0, &per_sm)) != cudaSuccess) break;
     if (per_sm < 1) {
       e = cudaErrorInvalidConfiguration;
       break;
     }
+    // every resident block holds tc_cols of the SM's 512 tensor-memory columns
+    if (L.tc_cols) per_sm = std::min(per_sm, 512 / L.tc_cols);
     std::vector<Item> items;
     make_items(B, pi, L.probs, per_sm * sms, &items, &L.nface_items, &L.nchunk_items);
     L.nitems = (int)items.size();
@@ -304,7 +321,7 @@ void make_table(const sbm_batch* B, const LaunchPlan& L, const T* const* x, T* c
     q.multi = ct.multi;
     q.mask = ct.multi_mask;
     q.ld_asm_ycol = (int64_t)dd.ncolours * p->hp.n_dofs;
-    q.code = bk::code_of(p->hp.d, p->hp.n, v, ext ? 0 : fh, ext);
+    q.code = bk::code_of(p->hp.d, p->hp.n, v, ext ? 0 : fh, ext, prob_tc(B, pi, k));
     q.ncol = dd.ncolours;
     q.n_face_items = L.nface_items[j];
     q.n_chunk_items = L.nchunk_items[j];
@@ -327,7 +344,7 @@ cudaError_t enqueue(sbm_batch* B, const std::vector<LaunchPlan>& plans, const T*
     make_table<T>(B, L, x, y, tab.get());
     e = bk::launch(*tab, static_cast<const Item*>(L.items), L.nitems,
                    (int)L.probs.size() * B->nrhs, B->nrhs, P.cnt + L.cnt_off, B->err, L.smem,
-                   L.grid, st);
+                   L.grid, L.tc_cols, st);
   }
   return e;
 }
@@ -438,7 +455,8 @@ int autotune(sbm_batch* B) {
       for (int v = 0; v < 2; ++v)
         for (int fh = 0; fh < 2; ++fh)
           smem = std::max(smem, item_smem(pi, p->hp.d, p->hp.n, v, fh,
-                                          p->hp.desc.extension == SBM_EXT_TAYLOR1));
+                                          p->hp.desc.extension == SBM_EXT_TAYLOR1,
+                                          P.allow_tc && pi == 0 && p->hp.d == 3));
       n += (size_t)p->hp.n_dofs * B->nrhs;
     }
     most = std::max(most, n);
@@ -457,11 +475,20 @@ int autotune(sbm_batch* B) {
     if (status != SBM_OK) break;
     DegreeKnobs& kn = P.knobs[deg];
     float best = 1e30f;
-    int bv = 0, bf = 0;
-    for (int opt = 0; opt < 4 && status == SBM_OK; ++opt) {
-      const int v = opt & 1, fh = opt >> 1;
+    int bv = 0, bf = 0, bt = 0;
+    // tensor-core faces: FP32, when the batch allows them and the degree has
+    // a 3D problem with the exact extension (they take one face at a time,
+    // so the face batch is not varied with them)
+    bool tc_ok = false;
+    for (int k : ks)
+      tc_ok |= B->probs[k]->hp.d == 3 && B->probs[k]->hp.desc.extension == SBM_EXT_EXACT;
+    tc_ok = tc_ok && pi == 0 && P.allow_tc;
+    for (int opt = 0; opt < 8 && status == SBM_OK; ++opt) {
+      const int v = opt & 1, fh = (opt >> 1) & 1, tcv = opt >> 2;
+      if (tcv && (!tc_ok || fh)) continue;
       kn.shape = v;
       kn.face_batch = fh;
+      kn.tc = tcv;
       for (int k : ks) P.shape[k] = v;
       float ms = 0.f;
       if ((e = time_subset<T>(B, ks, smem, xbuf, ybuf, &ms)) != cudaSuccess) {
@@ -473,10 +500,12 @@ int autotune(sbm_batch* B) {
         best = ms;
         bv = v;
         bf = fh;
+        bt = tcv;
       }
     }
     kn.shape = bv;
     kn.face_batch = bf;
+    kn.tc = bt;
     for (int k : ks) P.shape[k] = bv;
   }
   cudaStreamSynchronize(B->cap);
@@ -588,6 +617,7 @@ int sbm_batch_create(sbm_problem* const* probs, int nprob, int nrhs, int autotun
   bool ok = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) == cudaSuccess &&
             cudaMalloc((void**)&B->err, sizeof(int)) == cudaSuccess &&
             cudaMemset(B->err, 0, sizeof(int)) == cudaSuccess;
+  B->prec[0].allow_tc = (autotune_shapes & SBM_BATCH_TENSOR_CORES) != 0;
   for (int pi = 0; ok && pi < 2; ++pi) {
     B->prec[pi].shape.assign(nprob, 0);
     ok = cudaMalloc((void**)&B->prec[pi].cnt, cnt_ints(B) * sizeof(int)) == cudaSuccess;
@@ -606,7 +636,7 @@ int sbm_batch_create(sbm_problem* const* probs, int nprob, int nrhs, int autotun
   }
   int st = setup_tables<float>(B);
   if (st == SBM_OK) st = setup_tables<double>(B);
-  if (st == SBM_OK && autotune_shapes) {
+  if (st == SBM_OK && (autotune_shapes & SBM_BATCH_AUTOTUNE)) {
     st = autotune<float>(B);
     if (st == SBM_OK) st = autotune<double>(B);
   }
@@ -655,9 +685,35 @@ int sbm_batch_knobs(const sbm_batch* batch, int precision, int degree, int* tile
   if (it == P.knobs.end()) return sbm_fail_detail(SBM_ERR_ARG, "no tuned problem of that degree");
   if (tile_shape) *tile_shape = it->second.shape;
   if (face_batch) *face_batch = it->second.face_batch;
-  if (tensor_cores) *tensor_cores = 0;
+  if (tensor_cores) *tensor_cores = it->second.tc;
   if (ms)
-    for (int i = 0; i < 8; ++i) ms[i] = i < 4 ? it->second.ms[i] : -1.f;
+    for (int i = 0; i < 8; ++i) ms[i] = it->second.ms[i];
+  return SBM_OK;
+}
+
+int sbm_batch_set_knobs(sbm_batch* batch, int precision, int degree, int tile_shape,
+                        int face_batch, int tensor_cores) {
+  if (!batch || (precision != 32 && precision != 64) || tile_shape < 0 || tile_shape > 1 ||
+      face_batch < 0 || face_batch > 1 || tensor_cores < 0 || tensor_cores > 1)
+    return sbm_fail_detail(SBM_ERR_ARG, "bad argument");
+  const int pi = precision == 64 ? 1 : 0;
+  if (tensor_cores && (pi != 0 || !batch->prec[0].allow_tc))
+    return sbm_fail_detail(SBM_ERR_UNSUPPORTED,
+                           "tensor-core faces: FP32 batches created with SBM_BATCH_TENSOR_CORES");
+  bool any = false;
+  for (size_t k = 0; k < batch->probs.size(); ++k)
+    if (batch->probs[k]->hp.p == degree) any = true;
+  if (!any) return sbm_fail_detail(SBM_ERR_ARG, "no problem of that degree");
+  cudaDeviceSynchronize();
+  BatchPrec& P = batch->prec[pi];
+  DegreeKnobs& kn = P.knobs[degree];
+  kn.shape = tile_shape;
+  kn.face_batch = face_batch;
+  kn.tc = tensor_cores;
+  for (size_t k = 0; k < batch->probs.size(); ++k)
+    if (batch->probs[k]->hp.p == degree) P.shape[k] = tile_shape;
+  P.dirty = true;
+  drop_graphs(P);
   return SBM_OK;
 }
 
@@ -702,7 +758,7 @@ extern "C" int sbm_batch_selftest_timeout(sbm_batch* batch, void* stream) {
   if (e == cudaSuccess) e = cudaMemcpy(di, &it, sizeof(it), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 3 * sizeof(int), (cudaStream_t)stream);
   if (e == cudaSuccess)
-    e = bk::launch(*tab, static_cast<const Item*>(di), 1, 1, 1, cnt, batch->err, 0, 1,
+    e = bk::launch(*tab, static_cast<const Item*>(di), 1, 1, 1, cnt, batch->err, 0, 1, 0,
                    (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   cudaFree(di);

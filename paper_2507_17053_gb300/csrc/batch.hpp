@@ -16,14 +16,15 @@ struct ProbTable;
 // per precision (batch_f32.cu / batch_f64.cu)
 cudaError_t set_unit_table(int n, const KTab<double>& t);
 cudaError_t set_unit_table(int n, const KTab<float>& t);
-size_t item_smem_f64(int d, int n, int v, int fh, int ext);
-size_t item_smem_f32(int d, int n, int v, int fh, int ext);
-cudaError_t occupancy_f64(size_t smem, int* per_sm);
-cudaError_t occupancy_f32(size_t smem, int* per_sm);
+size_t item_smem_f64(int d, int n, int v, int fh, int ext, int tc);
+size_t item_smem_f32(int d, int n, int v, int fh, int ext, int tc);
+cudaError_t occupancy_f64(size_t smem, bool tc, int* per_sm);
+cudaError_t occupancy_f32(size_t smem, bool tc, int* per_sm);
 cudaError_t launch(const ProbTable<double>& tab, const Item* items, int nitems, int nsys,
-                   int nrhs, int* cnt, int* err, size_t smem, int grid, cudaStream_t st);
+                   int nrhs, int* cnt, int* err, size_t smem, int grid, int tc_cols,
+                   cudaStream_t st);
 cudaError_t launch(const ProbTable<float>& tab, const Item* items, int nitems, int nsys, int nrhs,
-                   int* cnt, int* err, size_t smem, int grid, cudaStream_t st);
+                   int* cnt, int* err, size_t smem, int grid, int tc_cols, cudaStream_t st);
 }  // namespace bk
 }  // namespace sbm
 
@@ -49,12 +50,13 @@ struct BatchSolveWs {
 
 // Knobs of one degree for one precision, chosen by the autotuner: the cell
 // kernel's tile shape (0: R cells per chunk, 1: R/2), the face batch (0:
-// 256/L faces per pass, 1: 128/L), and the measured time of every option
-// tried (ms of that degree's sub-batch; index shape + 2 * face batch; < 0:
-// not tried).
+// 256/L faces per pass, 1: 128/L), tensor-core faces (FP32, 3D: 0 CUDA
+// cores, 1 TF32 tcgen05), and the measured time of every option tried (ms
+// of that degree's sub-batch; index shape + 2 face batch + 4 tensor cores;
+// < 0: not tried).
 struct DegreeKnobs {
-  int shape = 0, face_batch = 0;
-  float ms[4] = {-1.f, -1.f, -1.f, -1.f};
+  int shape = 0, face_batch = 0, tc = 0;
+  float ms[8] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
 };
 
 // One launch of the persistent kernel: up to bk::kLaunchProbs problems of
@@ -68,12 +70,14 @@ struct LaunchPlan {
   std::vector<int> nface_items, nchunk_items;   // [local problem] items per right-hand side
   size_t smem = 0;                   // dynamic shared memory per block
   int grid = 0;
+  int tc_cols = 0;                   // tensor-memory columns per block (tensor-core faces)
   int cnt_off = 0;                   // ticket + 2 counters per system, from here
 };
 
 // Per-precision state of the batched apply: knobs, launch plans and the
 // captured graphs (one per set of vector pointers).
 struct BatchPrec {
+  bool allow_tc = false;             // FP32: tensor-core (TF32) faces may be chosen
   std::vector<int> shape;            // [nprob] tile shape per problem
   std::map<int, DegreeKnobs> knobs;  // degree -> knobs
   bool dirty = true;                 // plans to rebuild

@@ -21,11 +21,15 @@ using L_f64 = Launcher<double, U_f64>;
 cudaError_t set_unit_table(int n, const KTab<double>& t) {
   return cudaMemcpyToSymbol(c_unit_f64, &t, sizeof(t), (size_t)n * sizeof(t));
 }
-size_t item_smem_f64(int d, int n, int v, int fh, int ext) { return L_f64::smem(d, n, v, fh, ext); }
-cudaError_t occupancy_f64(size_t smem, int* per_sm) { return L_f64::occupancy(smem, per_sm); }
+size_t item_smem_f64(int d, int n, int v, int fh, int ext, int tc) {
+  return L_f64::smem(d, n, v, fh, ext, tc);
+}
+cudaError_t occupancy_f64(size_t smem, bool tc, int* per_sm) {
+  return L_f64::occupancy(smem, tc, per_sm);
+}
 cudaError_t launch(const ProbTable<double>& tab, const Item* items, int nitems, int nsys, int nrhs,
-                   int* cnt, int* err, size_t smem, int grid, cudaStream_t st) {
-  return L_f64::launch(tab, items, nitems, nsys, nrhs, cnt, err, smem, grid, st);
+                   int* cnt, int* err, size_t smem, int grid, int tc_cols, cudaStream_t st) {
+  return L_f64::launch(tab, items, nitems, nsys, nrhs, cnt, err, smem, grid, tc_cols, st);
 }
 
 }  // namespace bk

@@ -182,3 +182,39 @@ def test_batch_bounded_wait_expires_without_hang():
     for p, x, y in zip(ps[:2], xs, ys):
         assert torch.equal(y, p.apply_f64(x))
     B.close()
+
+
+def test_batch_tensor_core_faces():
+    """FP32 batched applies with the tensor-core face items (TF32 tcgen05
+    point evaluation): within the TF32 error bound of the FP64 oracle, close
+    to the single-problem TF32 apply, and the autotuner times the option."""
+    from oracle.operator import Problem as OracleProblem
+    ws = S.batched_ellipsoids(nprob=4, n_range=(6, 10))
+    ps = [G.Problem.from_workload(w) for w in ws]
+    nrhs = 2
+    B = G.Batch(ps, nrhs, autotune=True, tensor_cores=True)
+    for deg in sorted({w.degree for w in ws}):
+        k = B.knobs(32, deg)
+        assert k["ms"][4] is not None and k["ms"][5] is not None   # TC timed, both shapes
+        assert k["ms"][6] is None                                  # no face batch with TC
+        B.set_knobs(32, deg, 0, 0, 1)
+        with pytest.raises(G.SbmError):
+            B.set_knobs(64, deg, 0, 0, 1)
+    xs = [np.concatenate([S.random_vector(S.rhs_seed(w, r), p.n_dofs, "uniform")
+                          for r in range(nrhs)]) for w, p in zip(ws, ps)]
+    xd = [torch.from_numpy(x).float().cuda() for x in xs]
+    ys = [torch.full_like(x, float("nan")) for x in xd]
+    B.apply(xd, ys)
+    B.device_status()
+    for w, p, x, y in zip(ws, ps, xs, ys):
+        O = OracleProblem.from_workload(w)
+        for r in range(nrhs):
+            sl = slice(r * p.n_dofs, (r + 1) * p.n_dofs)
+            ref = O.apply(x[sl].astype(np.float32).astype(np.float64))
+            yb = y[sl].double().cpu().numpy()
+            err = float(np.abs(yb - ref).max() / np.abs(ref).max())
+            assert err <= 1.3e-3, (w.degree, err)
+            ys_ = p.apply_f32(xd[ws.index(w)][sl].contiguous(), face_mode="tf32")
+            d = float((y[sl] - ys_).abs().max() / ys_.abs().max())
+            assert d <= 1e-5, d
+    B.close()
