@@ -42,7 +42,7 @@ FP64_PIPE_GOPS = SMS * SM_MAX_MHZ * 1e6 * FP64_LANES_PER_SM_CLK / 1e9
 # from one ncu capture per (workload, tile shape) of the kernel as it stood
 # when captured (dram__bytes_read.sum + dram__bytes_write.sum), not measured
 # by this run; other shapes: not captured
-CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 0): 127.59e6 + 107.57e6,
+CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 0): 127.506944e6 + 107.981312e6,
                 ("sphere3d_cg_q4_n96", 1): 157.950720e6 + 133.191680e6}
 L2_BYTES = 129 * 1024 * 1024
 REF_BUDGET_S = 90.0              # wall-clock budget of the --impl reference run
@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--profile-applies", choices=["f64", "f32", "tf32", "bf16"], default=None,
                     help="run --steps applies of the workload in this precision and exit "
                          "(a fixed launch sequence for ncu captures; prints no JSON)")
+    ap.add_argument("--profile-batch", choices=["f64", "f32"], default=None,
+                    help="run --steps persistent batched applies of 24 rotated ellipsoids x 4 "
+                         "right-hand sides (a fixed launch sequence for ncu captures; no JSON)")
     ap.add_argument("--tile-shape", type=int, choices=[-1, 0, 1, 2], default=-1,
                     help="with --profile-applies: pin the cell kernel's tile shape "
                          "(-1 keeps the default, 0)")
@@ -740,6 +743,28 @@ def profile_applies(args, w):
     G.sbm_device_status(P.handle)
 
 
+def profile_batch(args):
+    """The batched apply on a batch small enough for a full ncu capture:
+    24 rotated ellipsoids (N ~ U{20..36}, p ~ U{2..6}) x 4 right-hand sides,
+    tile shape 0 and the full face batch (no autotuning)."""
+    import torch
+
+    import paper_2507_17053_gb300 as G
+    ws = S.batched_ellipsoids(nprob=24, n_range=(20, 36))
+    ps = [G.Problem.from_workload(w) for w in ws]
+    nrhs = 4
+    B = G.Batch(ps, nrhs, autotune=False)
+    dt = torch.float32 if args.profile_batch == "f32" else torch.float64
+    xs = [torch.from_numpy(np.concatenate([S.random_vector(S.rhs_seed(w, r), p.n_dofs, "uniform")
+                                           for r in range(nrhs)])).to("cuda", dt)
+          for w, p in zip(ws, ps)]
+    ys = [torch.empty_like(v) for v in xs]
+    for _ in range(args.steps):
+        B.apply(xs, ys)
+    torch.cuda.synchronize()
+    B.device_status()
+
+
 def run_ours(args, w):
     import torch
 
@@ -904,6 +929,8 @@ def main():
         run_reference(args, w)
     elif args.profile_applies:
         profile_applies(args, w)
+    elif args.profile_batch:
+        profile_batch(args)
     else:
         run_ours(args, w)
 
