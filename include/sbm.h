@@ -522,6 +522,11 @@ int sbm_bicgstab_mixed(sbm_problem* prob, const double* b, double* x, double rto
  * Errors: SBM_ERR_ARG (NULL, unknown id).
  */
 int sbm_rhs(const sbm_problem* prob, int manufactured, double* b_host);
+/* The same right-hand side into a device array b (n_dofs doubles) on
+ * stream: assembled on the host in FP64 as sbm_rhs, then copied (the call
+ * returns once the host data is staged).  Errors: SBM_ERR_ARG, SBM_ERR_STATE
+ * (no device data), SBM_ERR_CUDA. */
+int sbm_rhs_device(const sbm_problem* prob, int manufactured, double* b, void* stream);
 int sbm_interpolate(const sbm_problem* prob, int manufactured, double* u_host);
 
 /*

@@ -102,6 +102,8 @@ _SIGS = {
                                                                     ctypes.POINTER(ctypes.c_double),
                                                                     ctypes.c_void_p]),
     "sbm_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "sbm_rhs_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "sbm_interpolate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "sbm_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_void_p)]),
@@ -561,6 +563,16 @@ class Problem:
         b = np.zeros(self.n_dofs)
         sbm_rhs(self.handle, manufactured, b)
         return b
+
+    def rhs_device(self, manufactured=0, out=None, stream=None):
+        """The right-hand side as a device float64 tensor (sbm_rhs_device)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n_dofs, dtype=torch.float64, device="cuda")
+        _expect(out, torch.float64, self.n_dofs)
+        _check(lib().sbm_rhs_device(self.handle, manufactured, _ptr(out), _stream(stream)),
+               "sbm_rhs_device")
+        return out
 
     def interpolate(self, manufactured=0):
         import numpy as np

@@ -801,6 +801,19 @@ int sbm_rhs(const sbm_problem* prob, int manufactured, double* b_host) {
   return SBM_OK;
 }
 
+int sbm_rhs_device(const sbm_problem* prob, int manufactured, double* b, void* stream) {
+  if (!prob || !b) return fail(SBM_ERR_ARG, "NULL argument");
+  if (!manufactured_ok(manufactured, prob->hp.d)) return fail(SBM_ERR_ARG, "unknown solution id");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  std::vector<double> h((size_t)prob->hp.n_dofs);
+  build_rhs(prob->hp, manufactured, h.data());
+  // from pageable memory the call returns once h is staged for the copy
+  cudaError_t e = cudaMemcpyAsync(b, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sbm_rhs_device copy");
+  return SBM_OK;
+}
+
 int sbm_interpolate(const sbm_problem* prob, int manufactured, double* u_host) {
   if (!prob || !u_host) return fail(SBM_ERR_ARG, "NULL argument");
   if (!manufactured_ok(manufactured, prob->hp.d)) return fail(SBM_ERR_ARG, "unknown solution id");

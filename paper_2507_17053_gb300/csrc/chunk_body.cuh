@@ -319,8 +319,8 @@ __device__ __forceinline__ void chunk_loop(const ChunkArgs<T>& a, const KTab<T>&
 // issues are its own count minus one (on GB300 a double addition costs an
 // FP64-pipe slot per warp instruction, whatever its active lanes; the list
 // is grouped by colour count, so most warps need one).  FP32: all loads
-// first, then the unrolled sum (the additions are cheap, the load latency is
-// not).  Adding a 0 leaves a sum unchanged.  All 32 lanes of the warp call
+// first, then the unrolled sum over the lane's own colours (the additions
+// are cheap, the load latency is not).  All 32 lanes of the warp call
 // this together.  COH: colour buffers written by other blocks of the same
 // launch (L2 loads instead of the streaming ones).
 template <typename T, bool COH>
@@ -357,6 +357,7 @@ __device__ __forceinline__ void assemble_warp(const T* __restrict__ ycol,
       acc += v;
     }
   } else {
+    const unsigned cnt = __popc(m);
     T v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -366,7 +367,7 @@ __device__ __forceinline__ void assemble_warp(const T* __restrict__ ycol,
     acc = v[0];
 #pragma unroll
     for (int j = 1; j < 8; ++j)
-      if ((unsigned)j < kmax) acc += v[j];
+      if ((unsigned)j < cnt) acc += v[j];
   }
   if (t < nmulti) __stcs(y + i, acc);
 }

@@ -50,3 +50,4 @@ def test_nan_input_propagates_without_error():
     y = P.apply_f64(x)
     G.sbm_device_status(P.handle)
     assert torch.isnan(y).any() and not torch.isnan(y).all()
+
