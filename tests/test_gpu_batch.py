@@ -1,5 +1,7 @@
 """Batched applies (several problems, several right-hand sides, one graph
 launch) give exactly the per-problem applies."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -217,4 +219,30 @@ def test_batch_tensor_core_faces():
             ys_ = p.apply_f32(xd[ws.index(w)][sl].contiguous(), face_mode="tf32")
             d = float((y[sl] - ys_).abs().max() / ys_.abs().max())
             assert d <= 1e-5, d
+    B.close()
+
+
+def test_batch_over_one_launch_plan():
+    """More problems than one launch holds (96): the batch runs several
+    persistent launches in one graph; every problem still equals its single
+    apply bitwise, in both precisions, including a first-order Taylor one."""
+    ws = S.batched_ellipsoids(nprob=110, n_range=(3, 6), p_range=(1, 3))
+    ws.append(S.SPHERE_3D_Q4.resized(6, degree=2))
+    ws.append(dataclasses.replace(S.SPHERE_3D_Q4.resized(7, degree=3), extension="taylor1"))
+    ps = [G.Problem.from_workload(w) for w in ws]
+    nrhs = 2
+    B = G.Batch(ps, nrhs, autotune=False)
+    for dt in (torch.float64, torch.float32):
+        xs = [torch.from_numpy(np.concatenate([S.random_vector(S.rhs_seed(w, r), p.n_dofs, "uniform")
+                                               for r in range(nrhs)])).to("cuda", dt)
+              for w, p in zip(ws, ps)]
+        ys = [torch.full_like(x, float("nan")) for x in xs]
+        B.apply(xs, ys)
+        B.device_status()
+        for p, x, y in zip(ps, xs, ys):
+            for r in range(nrhs):
+                sl = slice(r * p.n_dofs, (r + 1) * p.n_dofs)
+                ref = p.apply_f64(x[sl].contiguous()) if dt == torch.float64 \
+                    else p.apply_f32(x[sl].contiguous())
+                assert torch.equal(y[sl], ref)
     B.close()
