@@ -39,13 +39,24 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (CUDA cores) nominal dense rate
 SMS, SM_MAX_MHZ, FP64_LANES_PER_SM_CLK = 152, 2070, 2
 FP64_PIPE_GOPS = SMS * SM_MAX_MHZ * 1e6 * FP64_LANES_PER_SM_CLK / 1e9
 # DRAM bytes (read + write) of one launch of the FP64 cell kernel: constants
-# from one ncu capture per (workload, tile shape) of the kernel as it stood
-# when captured (dram__bytes_read.sum + dram__bytes_write.sum), not measured
-# by this run; other shapes: not captured
-CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 0): 127.506944e6 + 107.981312e6,
-                ("sphere3d_cg_q4_n96", 1): 157.950720e6 + 133.191680e6}
+# from one ncu capture per (workload, tile shape, store mode) of the kernel as
+# it stood when captured (dram__bytes_read.sum + dram__bytes_write.sum), not
+# measured by this run; other shapes and modes: not captured
+CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 0, 0): 127.506944e6 + 107.981312e6,
+                ("sphere3d_cg_q4_n96", 1, 0): 157.950720e6 + 133.191680e6}
 L2_BYTES = 129 * 1024 * 1024
 REF_BUDGET_S = 90.0              # wall-clock budget of the --impl reference run
+
+
+def cell_kernel_name(w, shape, ordered):
+    """The FP64 cell-term kernel that tile shape and store mode launch."""
+    n = w.degree + 1
+    if shape == 2:
+        return f"cg_cell_reg_kernel<double,{n}> (cell kernel, tile shape 2)"
+    name = ("cg_direct" if shape == 3 else "cg_chunk") + ("_ord" if ordered else "")
+    dims = f"{n}" if shape == 3 else f"{w.dim},{n}"
+    return (f"{name}_kernel<double,{dims}> (cell kernel, tile shape {shape}, "
+            f"{'colour-ordered stores' if ordered else 'colour buffers'})")
 
 
 def parse():
@@ -65,9 +76,12 @@ def parse():
     ap.add_argument("--profile-batch", choices=["f64", "f32"], default=None,
                     help="run --steps persistent batched applies of 24 rotated ellipsoids x 4 "
                          "right-hand sides (a fixed launch sequence for ncu captures; no JSON)")
-    ap.add_argument("--tile-shape", type=int, choices=[-1, 0, 1, 2], default=-1,
+    ap.add_argument("--tile-shape", type=int, choices=[-1, 0, 1, 2, 3], default=-1,
                     help="with --profile-applies: pin the cell kernel's tile shape "
                          "(-1 keeps the default, 0)")
+    ap.add_argument("--ordered-stores", type=int, choices=[-1, 0, 1], default=-1,
+                    help="with --profile-applies: pin the store mode of the shared DoFs "
+                         "(1: colour-ordered stores, 0: colour buffers + assembly)")
     return ap.parse_args()
 
 
@@ -729,6 +743,11 @@ def profile_applies(args, w):
             G.sbm_set_tile_shape(P.handle, args.tile_shape, -1)
         else:
             G.sbm_set_tile_shape(P.handle, -1, args.tile_shape)
+    if args.ordered_stores >= 0:
+        if args.profile_applies == "f64":
+            G.sbm_set_ordered_stores(P.handle, args.ordered_stores, -1)
+        else:
+            G.sbm_set_ordered_stores(P.handle, -1, args.ordered_stores)
     x = torch.from_numpy(S.random_vector(w.seed, P.n_dofs, w.dist)).cuda()
     if args.profile_applies != "f64":
         x = x.float()
@@ -865,6 +884,7 @@ def run_ours(args, w):
                    "n_sfaces": P.n_sfaces, "degree": w.degree, "dim": w.dim,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "tile_shape_f64_f32": list(shapes),
+                   "ordered_stores_f64_f32": list(G.sbm_ordered_stores(P.handle)),
                    "l2": f"inputs larger than L2: x, y, colour buffers and tables "
                          f"{(2 * 8 * n + 8 * 8 * n) / 1e6:.0f} MB > 129 MB"},
         "e2e": {"value": job_rate(world, n * e2e_steps, e2e_s) / 1e9, "unit": "GDoF/s",
@@ -875,12 +895,12 @@ def run_ours(args, w):
                      "peak_src": "measured (sbm_peak_probe, this run); FP64 FMA pipe ops",
                      "peak_derived": FP64_PIPE_GOPS,
                      "frac_of_derived": achieved_gops / FP64_PIPE_GOPS,
-                     "traffic": CELL_TRAFFIC.get((w.name, shapes[0])),
+                     "traffic": CELL_TRAFFIC.get((w.name, shapes[0],
+                                                  G.sbm_ordered_stores(P.handle)[0])),
                      "traffic_src": "constant from one earlier ncu capture of this kernel "
                                     "(dram__bytes_read.sum + dram__bytes_write.sum), not "
                                     "measured by this run",
-                     "kernel": f"cg_chunk_kernel<double,{w.dim},{w.degree + 1}> (cell kernel, "
-                               f"tile shape {shapes[0]})",
+                     "kernel": cell_kernel_name(w, shapes[0], G.sbm_ordered_stores(P.handle)[0]),
                      "ops_per_launch": cops, "fma_per_launch": cfma,
                      "other_per_launch": cadd,
                      "launches_per_step": 1, "kernel_ms_per_launch": cell_ms,

@@ -552,24 +552,64 @@ int sbm_device_status(sbm_problem* prob);
 
 /*
  * Tile-shape autotuner for the single applies (continuous Galerkin; a no-op
- * for DG): times the cell kernel with chunks of R and of R/2 cells, in FP64
- * and in FP32, on this problem (temporary device buffers of n_dofs doubles,
- * freed before returning), and keeps the faster shape per precision.  Both
- * shapes compute the same operator; results differ only in the rounding of
- * the few shared nodes that one shape sums in shared memory and the other in
- * the assembly.  *shape64 / *shape32 (may be NULL) receive the choices (0 or
- * 1).  Synchronous, legacy default stream.
+ * for DG): times, in FP64 and in FP32, on this problem (temporary device
+ * buffers of n_dofs doubles, freed before returning) the cell term's tile
+ * shapes and keeps the faster per precision:
+ *   0  chunks of R consecutive cells of a mesh row (R (p+1)^(d-1) threads),
+ *      x-line runs staged in shared memory;
+ *   1  chunks of R/2 cells;
+ *   2  (3D; FP32 p <= 4, FP64 p <= 3) the cells of shape 0's chunks, one
+ *      thread per cell with the tile in registers;
+ *   3  (3D) shape 0's chunks without staged runs: each thread loads and
+ *      stores its own lines.
+ * and for shapes 0 and 3 each way of completing the DoFs several chunk
+ * colours share (see sbm_set_ordered_stores).  All compute the same
+ * operator; shapes 0, 2 and 3 give bitwise-equal results with either store
+ * mode, shape 1 differs in the rounding of the few shared nodes it sums in
+ * the assembly instead of in shared memory.  *shape64 / *shape32 (may be
+ * NULL) receive the shape choices, sbm_ordered_stores the store modes.
+ * Synchronous, legacy default stream.
  */
 int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32);
 
 /*
- * Pin the tile shapes of the single applies instead (0: chunks of R cells,
- * 1: chunks of R/2; -1 keeps the current one), e.g. to reproduce a run
- * bitwise.  DG problems accept only 0 or -1.
- * Errors: SBM_ERR_ARG (NULL, shape outside -1..1), SBM_ERR_STATE,
- * SBM_ERR_UNSUPPORTED (shape 1 on a DG problem).
+ * Pin the tile shapes of the single applies instead (0..3 as for
+ * sbm_autotune; -1 keeps the current one), e.g. to reproduce a run bitwise.
+ * DG problems accept only 0 or -1.
+ * Errors: SBM_ERR_ARG (NULL, shape outside -1..3), SBM_ERR_STATE,
+ * SBM_ERR_UNSUPPORTED (a shape the problem's dimension, degree or
+ * discretisation does not have).
  */
 int sbm_set_tile_shape(sbm_problem* prob, int shape64, int shape32);
+
+/*
+ * How the single applies (continuous Galerkin, tile shapes 0 and 3, one
+ * right-hand side, device buffers) complete the DoFs that chunks of several
+ * colours share -- the scatter of Algorithm 1's cell results (and the face
+ * terms of Algorithm 3 folded into them) into the global vector:
+ *   0  every chunk stores such DoFs into its colour's buffer
+ *      ([2^d][n_dofs] scratch) and an assembly pass sums the buffers in
+ *      colour order;
+ *   1  colour-ordered stores: one persistent launch takes the chunks in
+ *      ascending colour order from a ticket counter; the lowest colour's
+ *      chunk stores a shared DoF, each higher colour's chunk reads, adds and
+ *      stores it after a bounded wait for its lower-colour neighbours (per-
+ *      chunk completion counts), so y receives the same sums in the same
+ *      order as with 0, bitwise, without the colour buffers' traffic or the
+ *      assembly launch.  An expired wait records SBM_ERR_TIMEOUT
+ *      (sbm_device_status).  The host-buffer pipeline, shapes 1 and 2 and
+ *      multi-RHS launches always use 0.
+ * -1 keeps the current mode; the default is 0 until sbm_autotune chooses.
+ * Two applies of one problem must not run concurrently in mode 1 (they
+ * share its counters), as in mode 0 they share its colour buffers.
+ * Errors: SBM_ERR_ARG (NULL, mode outside -1..1), SBM_ERR_STATE,
+ * SBM_ERR_UNSUPPORTED (1 where the tables were not built: DG, or a chunk
+ * with more than 64 lower-colour neighbours).
+ */
+int sbm_set_ordered_stores(sbm_problem* prob, int ordered64, int ordered32);
+/* The current store modes (0 or 1) of the FP64 and FP32 applies (either
+ * pointer may be NULL).  Errors: SBM_ERR_ARG (prob NULL). */
+int sbm_ordered_stores(const sbm_problem* prob, int* ordered64, int* ordered32);
 
 /*
  * Diagnostic of the failure path (the paper has no counterpart): enqueue one

@@ -130,6 +130,9 @@ _SIGS = {
     "sbm_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]),
     "sbm_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "sbm_set_ordered_stores": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "sbm_ordered_stores": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
     "sbm_selftest_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sbm_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_void_p]),
@@ -358,6 +361,18 @@ def sbm_autotune(handle: int) -> tuple[int, int]:
 
 def sbm_set_tile_shape(handle: int, shape64=-1, shape32=-1) -> None:
     _check(lib().sbm_set_tile_shape(handle, int(shape64), int(shape32)), "sbm_set_tile_shape")
+
+
+def sbm_set_ordered_stores(handle: int, ordered64=-1, ordered32=-1) -> None:
+    _check(lib().sbm_set_ordered_stores(handle, int(ordered64), int(ordered32)),
+           "sbm_set_ordered_stores")
+
+
+def sbm_ordered_stores(handle: int) -> tuple[int, int]:
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sbm_ordered_stores(handle, ctypes.byref(a), ctypes.byref(b)),
+           "sbm_ordered_stores")
+    return a.value, b.value
 
 
 def sbm_selftest_timeout(handle: int, stream=None) -> None:

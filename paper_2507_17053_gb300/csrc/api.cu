@@ -132,6 +132,12 @@ static void free_device(DeviceData* dd) {
     cudaFree(ct.run_bits);
     cudaFree(ct.multi);
     cudaFree(ct.multi_mask);
+    cudaFree(ct.ord);
+    cudaFree(ct.add_bits);
+    cudaFree(ct.deps);
+    cudaFree(ct.ndeps);
+    cudaFree(ct.done);
+    cudaFree(ct.tickets);
   }
   cudaFree(dd->diag_pos);
   cudaFree(dd->err_flag);
@@ -332,7 +338,8 @@ static int build_device(const HostProblem& hp, DeviceData* dd) {
         goto err;
       const int R = v == 0 ? chunk_cells(d, n) : std::max(chunk_cells(d, n) / 2, 1);
       if ((e = device_chunk_tables(dd->lines, Nc, L, n, hp.n_dofs, ch_first[v], ch_col[v], R,
-                                   dd->chunks[v].first, ycut, &dd->chunks[v])) != cudaSuccess)
+                                   dd->chunks[v].first, ycut, &dd->chunks[v], v == 0)) !=
+          cudaSuccess)
         goto err;
     }
     if ((e = build_cell_reg_tables(hp, ch_first[0], dd)) != cudaSuccess) goto err;
@@ -857,9 +864,15 @@ int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32) {
   for (int prec = 0; prec < 2 && e == cudaSuccess; ++prec) {
     float best = 1e30f;
     int bestv = 0;
-    const int nv = cell_reg_available(prob->hp, prec == 1) ? 3 : 2;
-    for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+    bool besto = false;
+    for (int vo = 0; vo < 8 && e == cudaSuccess; ++vo) {
+      const int v = vo / 2;
+      const bool o = vo % 2;
+      if ((v == 2 && !cell_reg_available(prob->hp, prec == 1)) || (v == 3 && prob->hp.d != 3) ||
+          (o && (v == 1 || v == 2 || !prob->dd.chunks[0].ordered)))
+        continue;
       prob->dd.variant[prec] = v;
+      prob->dd.ordered[prec] = o;
       float tot = 0.f;
       for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
         cudaEventRecord(e0, 0);
@@ -873,12 +886,18 @@ int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32) {
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep >= 2) tot += ms;
       }
+      // colour-ordered stores only when at least 2 % faster: closer timings
+      // are within the run-to-run spread, and the colour buffers keep the
+      // cell kernel free of the ordering waits
+      if (o) tot *= 1.02f;
       if (tot < best) {
         best = tot;
         bestv = v;
+        besto = o;
       }
     }
     prob->dd.variant[prec] = bestv;
+    prob->dd.ordered[prec] = besto;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -893,8 +912,10 @@ int sbm_autotune(sbm_problem* prob, int* shape64, int* shape32) {
 int sbm_set_tile_shape(sbm_problem* prob, int shape64, int shape32) {
   if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
   if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
-  if (shape64 < -1 || shape64 > 2 || shape32 < -1 || shape32 > 2)
-    return fail(SBM_ERR_ARG, "tile shape must be -1, 0, 1 or 2");
+  if (shape64 < -1 || shape64 > 3 || shape32 < -1 || shape32 > 3)
+    return fail(SBM_ERR_ARG, "tile shape must be -1, 0, 1, 2 or 3");
+  if (prob->hp.d != 3 && (shape64 == 3 || shape32 == 3))
+    return fail(SBM_ERR_UNSUPPORTED, "tile shape 3 is for 3D problems");
   if (prob->hp.desc.dg && (shape64 >= 1 || shape32 >= 1))
     return fail(SBM_ERR_UNSUPPORTED, "DG applies have one tile shape");
   if ((shape64 == 2 && !cell_reg_available(prob->hp, false)) ||
@@ -903,6 +924,27 @@ int sbm_set_tile_shape(sbm_problem* prob, int shape64, int shape32) {
                 "tile shape 2 needs a 3D problem with p <= 4 (FP32) or p <= 3 (FP64)");
   if (shape64 >= 0) prob->dd.variant[0] = shape64;
   if (shape32 >= 0) prob->dd.variant[1] = shape32;
+  return SBM_OK;
+}
+
+int sbm_set_ordered_stores(sbm_problem* prob, int ordered64, int ordered32) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  if (!prob->on_device) return fail(SBM_ERR_STATE, "sbm_setup_face_data not called");
+  if (ordered64 < -1 || ordered64 > 1 || ordered32 < -1 || ordered32 > 1)
+    return fail(SBM_ERR_ARG, "ordered must be -1, 0 or 1");
+  if ((ordered64 == 1 || ordered32 == 1) && !prob->dd.chunks[0].ordered)
+    return fail(SBM_ERR_UNSUPPORTED,
+                "no colour-ordered stores for this problem (DG, or a chunk with more "
+                "lower-colour neighbours than the dependency table holds)");
+  if (ordered64 >= 0) prob->dd.ordered[0] = ordered64 == 1;
+  if (ordered32 >= 0) prob->dd.ordered[1] = ordered32 == 1;
+  return SBM_OK;
+}
+
+int sbm_ordered_stores(const sbm_problem* prob, int* ordered64, int* ordered32) {
+  if (!prob) return fail(SBM_ERR_ARG, "prob is NULL");
+  if (ordered64) *ordered64 = prob->dd.ordered[0] ? 1 : 0;
+  if (ordered32) *ordered32 = prob->dd.ordered[1] ? 1 : 0;
   return SBM_OK;
 }
 

@@ -198,14 +198,14 @@ cg_cell_reg_kernel(const RegArgs<T> a, const __grid_constant__ KTab<T> t,
                    const __grid_constant__ XOps<T, N> xo) {
   constexpr int L = N * N, ND = L * N, P = N - 1, W = reg_words<N>();
   __shared__ T xface[kRegThreads][L + 1];       // j0 = P face of each cell (odd row stride)
-  const int q0 = a.block_first[blockIdx.x], q1 = a.block_first[blockIdx.x + 1];
-  const int c0 = __ldg(a.chunk_first + q0), c1 = __ldg(a.chunk_first + q1);
   const int tid = threadIdx.x;
+  const int b0 = a.block_first[blockIdx.x], b1 = a.block_first[blockIdx.x + 1];
+  const int c0 = __ldg(a.chunk_first + b0), c1 = __ldg(a.chunk_first + b1);
   const int pos = c0 + tid;
   const bool act = pos < c1;
   T u[ND];
   int c = 0, nc = 0, ch = 0;
-  const int32_t* ln = a.lines + (size_t)(act ? pos : c0) * L;
+  const int32_t* ln = a.lines + (size_t)(act ? pos : 0) * L;
   if (act) {
     ch = __ldg(a.cell_chunk + pos);
     const int f = __ldg(a.chunk_first + ch);
@@ -368,7 +368,8 @@ cudaError_t launch_cell_reg(const HostProblem& hp, const DeviceData& dd, const T
     case 3: return launch_reg<T, 3>(hp, dd, x, y, fo, ycol, st);
     case 4: return launch_reg<T, 4>(hp, dd, x, y, fo, ycol, st);
     case 5:
-      if constexpr (std::is_same<T, float>::value) return launch_reg<T, 5>(hp, dd, x, y, fo, ycol, st);
+      if constexpr (std::is_same<T, float>::value)
+        return launch_reg<T, 5>(hp, dd, x, y, fo, ycol, st);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

@@ -21,6 +21,7 @@
 // No atomics, no read-modify-write, no y = 0 fill; repeated applies are
 // bitwise equal.
 #include <algorithm>
+#include <type_traits>
 
 #include "chunk_body.cuh"
 
@@ -50,6 +51,82 @@ cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   chunk_xline_build<T, D, N, R>(smem_raw, t, threadIdx.x);
   chunk_loop<T, D, N, R, false, R * Shape<D, N>::L>(a, t, smem_raw, blockIdx.y,
                                                      a.q0 + blockIdx.x, a.q1, gridDim.x);
+}
+
+// The same chunks with colour-ordered stores (chunk_loop, ORD): a
+// persistent grid taking chunks from the ticket counter, no assembly pass.
+template <typename T, int D, int N, int R>
+__global__ void __launch_bounds__(R * Shape<D, N>::L)
+cg_chunk_ord_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t,
+                    const __grid_constant__ OrdArgs o) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  chunk_xline_build<T, D, N, R>(smem_raw, t, threadIdx.x);
+  chunk_loop_ord<T, D, N, R>(a, t, smem_raw, o);
+}
+
+// Tile shape 3 (3D): the chunks of shape 0 without staged runs.  Resident
+// blocks asked of the compiler: FP32 6 (40 registers, no spills); FP64 5 up
+// to p = 4 (48 registers), 4 above (64 registers; 5 would spill).
+template <typename T, int N>
+constexpr int direct_min_blocks() {
+  return std::is_same<T, float>::value ? 6 : (N <= 5 ? 5 : 4);
+}
+
+template <typename T, int N, int R>
+__global__ void __launch_bounds__(R * N * N, (direct_min_blocks<T, N>()))
+cg_direct_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  chunk_loop_direct<T, N, R, false>(a, t, t, smem_raw, blockIdx.y, a.q0 + blockIdx.x, a.q1,
+                                    gridDim.x);
+}
+
+template <typename T, int N, int R>
+__global__ void __launch_bounds__(R * N * N, (direct_min_blocks<T, N>()))
+cg_direct_ord_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t,
+                     const __grid_constant__ OrdArgs o) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  chunk_loop_direct<T, N, R, false, true>(a, t, t, smem_raw, 0, 0, 0, 0, &o);
+}
+
+// Resident blocks per SM x SMs of a kernel (the persistent grid of the
+// colour-ordered launches), once per kernel.
+template <typename K>
+static cudaError_t resident_grid(K kernel, int threads, size_t smem, int* cache, int* grid) {
+  if (*cache == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && smem > 48 * 1024)
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    *cache = std::max(1, per_sm) * sms;
+  }
+  *grid = *cache;
+  return cudaSuccess;
+}
+
+template <typename T, int N, int R>
+static cudaError_t direct_prepare(int* grid_cap) {
+  static int per_sm = 0, sms = 0;
+  static cudaError_t attr = cudaSuccess;
+  constexpr size_t smem = DirectSmem<T, N, R>::bytes;
+  if (per_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > 48 * 1024)
+      attr = cudaFuncSetAttribute(cg_direct_kernel<T, N, R>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_direct_kernel<T, N, R>,
+                                                      R * N * N, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  *grid_cap = 4 * per_sm * sms;
+  return attr;
 }
 
 // The DoFs that several colours touch (assemble_warp), one per thread;
@@ -101,7 +178,8 @@ struct Part {
 template <typename T, int D, int N, int R>
 static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const ChunkTable& ct,
                            const T* x, T* y, int64_t ld, int nrhs, T* fo, T* ycol, int face_mode,
-                           cudaStream_t st, Profiler* prof, Part part, bool reg) {
+                           cudaStream_t st, Profiler* prof, Part part, bool reg,
+                           bool direct, bool ord) {
   constexpr int L = Shape<D, N>::L;
   const KTab<T> t = make_ktab<T>(hp);
   constexpr size_t smem = ChunkSmem<T, D, N, R>::bytes;
@@ -139,16 +217,47 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   a.ldx = ld;
   a.ld_ycol = (int64_t)dd.ncolours * hp.n_dofs;
   a.ld_face = (int64_t)dd.nface * 2 * L;
+  OrdArgs oa{ct.ord, ct.add_bits, ct.deps, ct.ndeps, ct.done, ct.tickets, dd.err_flag, ct.n,
+             ct.dep_cap};
   if (reg) {                 // tile shape 2: one thread per cell (cell_reg.cu)
     if ((err = launch_cell_reg<T>(hp, dd, x, y, fo, ycol, st)) != cudaSuccess) return err;
     nlaunch++;
+  } else if (ord && part.q1 > part.q0) {      // colour-ordered stores, no assembly
+    if constexpr (R == ChunkShape<D, N>::R) {
+      static int cache = 0;
+      int grid = 0;
+      if (direct) {
+        if constexpr (D == 3) {
+          if ((err = resident_grid(cg_direct_ord_kernel<T, N, R>, R * L,
+                                   DirectSmem<T, N, R>::bytes, &cache, &grid)) != cudaSuccess)
+            return err;
+          cg_direct_ord_kernel<T, N, R><<<std::min(grid, ct.n), R * L,
+                                          DirectSmem<T, N, R>::bytes, st>>>(a, t, oa);
+        }
+      } else {
+        static int cache0 = 0;
+        if ((err = resident_grid(cg_chunk_ord_kernel<T, D, N, R>, R * L, smem, &cache0, &grid)) !=
+            cudaSuccess)
+          return err;
+        cg_chunk_ord_kernel<T, D, N, R><<<std::min(grid, ct.n), R * L, smem, st>>>(a, t, oa);
+      }
+      nlaunch++;
+    }
+  } else if (direct && part.q1 > part.q0) {   // tile shape 3: no staged runs (3D)
+    if constexpr (D == 3 && R == ChunkShape<D, N>::R) {
+      int dcap = 0;
+      if ((err = direct_prepare<T, N, R>(&dcap)) != cudaSuccess) return err;
+      const int grid = std::min(part.q1 - part.q0, dcap);
+      cg_direct_kernel<T, N, R><<<dim3(grid, nrhs), R * L, DirectSmem<T, N, R>::bytes, st>>>(a, t);
+      nlaunch++;
+    }
   } else if (part.q1 > part.q0) {
     const int grid = std::min(part.q1 - part.q0, cap);
     cg_chunk_kernel<T, D, N, R><<<dim3(grid, nrhs), R * L, smem, st>>>(a, t);
     nlaunch++;
   }
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
-  const int64_t n = hp.n_dofs, nm = part.m1 - part.m0;
+  const int64_t n = hp.n_dofs, nm = ord ? 0 : part.m1 - part.m0;
   if (nm > 0) {
     assemble_kernel<T><<<dim3((unsigned)((nm + 255) / 256), nrhs), 256, 0, st>>>(
         ycol, ct.multi + part.m0, ct.multi_mask + part.m0, y, n, nm, dd.ncolours,
@@ -166,18 +275,23 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
 // variant 0: R cells per chunk; variant 1: R/2 (a second tile shape for the
 // autotuner); variant 2: the cells of variant 0's chunks one thread each
 // (cell_reg.cu; whole applies only -- a slab of the host pipeline runs
-// variant 0, which gives the same bits).  Both chunkings are built at set-up
+// variant 0, which gives the same bits); variant 3 (3D): variant 0's chunks
+// without staged runs (chunk_loop_direct; slabs too).  Both chunkings are built at set-up
 // with the same colouring rule, so the variants give bitwise-equal results.
 template <typename T, int D, int N>
 static cudaError_t apply_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                            int64_t ld, int nrhs, T* fo, T* ycol, int face_mode, int variant,
-                           cudaStream_t st, Profiler* prof, int slab, int stages) {
+                           bool ordered, cudaStream_t st, Profiler* prof, int slab, int stages) {
   constexpr int R = ChunkShape<D, N>::R;
   constexpr int RH = (R / 2) > 0 ? R / 2 : 1;
   const int v = (variant == 1 && RH < R) ? 1 : 0;
   const bool reg = variant == 2 && slab < 0 && nrhs == 1 &&
                    cell_reg_available(hp, std::is_same<T, float>::value);
+  const bool direct = variant == 3 && D == 3;
   const ChunkTable& ct = dd.chunks[v];
+  // colour-ordered stores: whole single applies of chunking 0 by the chunk
+  // kernels (shapes 0 and 3; shape 2 keeps the colour buffers)
+  const bool ord = ordered && v == 0 && !reg && slab < 0 && nrhs == 1 && ct.ordered;
   Part part;
   if (slab >= 0) {
     const bool faces = stages & 1, cells = stages & 2;
@@ -190,20 +304,20 @@ static cudaError_t apply_t(const HostProblem& hp, const DeviceData& dd, const T*
   }
   if (v == 1)
     return apply_r<T, D, N, RH>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part,
-                                false);
+                                false, false, false);
   return apply_r<T, D, N, R>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part,
-                             reg);
+                             reg, direct, ord);
 }
 
 template <typename T>
 static cudaError_t dispatch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                             int64_t ld, int nrhs, T* fo, T* ycol, int face_mode, int variant,
-                            cudaStream_t st, Profiler* prof, int slab = -1,
+                            bool ordered, cudaStream_t st, Profiler* prof, int slab = -1,
                             int stages = 3) {
-#define SBM_CASE(DD, NN)                                                                  \
-  if (hp.d == DD && hp.n == NN)                                                           \
-    return apply_t<T, DD, NN>(hp, dd, x, y, ld, nrhs, fo, ycol, face_mode, variant, st, prof, \
-                              slab, stages);
+#define SBM_CASE(DD, NN)                                                                   \
+  if (hp.d == DD && hp.n == NN)                                                            \
+    return apply_t<T, DD, NN>(hp, dd, x, y, ld, nrhs, fo, ycol, face_mode, variant, ordered, \
+                              st, prof, slab, stages);
   SBM_CASE(2, 2) SBM_CASE(2, 3) SBM_CASE(2, 4) SBM_CASE(2, 5) SBM_CASE(2, 6) SBM_CASE(2, 7)
   SBM_CASE(3, 2) SBM_CASE(3, 3) SBM_CASE(3, 4) SBM_CASE(3, 5) SBM_CASE(3, 6) SBM_CASE(3, 7)
 #undef SBM_CASE
@@ -213,8 +327,9 @@ static cudaError_t dispatch(const HostProblem& hp, const DeviceData& dd, const T
 template <typename T>
 cudaError_t launch_cg_apply(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                             cudaStream_t st, Profiler* prof, int face_mode) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
   return dispatch<T>(hp, dd, x, y, 0, 1, face_out_of<T>(dd), ycol_of<T>(dd), face_mode,
-                     dd.variant[std::is_same<T, float>::value ? 1 : 0], st, prof);
+                     dd.variant[pi], dd.ordered[pi], st, prof);
 }
 template cudaError_t launch_cg_apply<double>(const HostProblem&, const DeviceData&,
                                              const double*, double*, cudaStream_t, Profiler*,
@@ -228,7 +343,7 @@ template cudaError_t launch_cg_apply<float>(const HostProblem&, const DeviceData
 // slab_y[s+1]) given x on [0, slab_x[s]).
 cudaError_t launch_cg_apply_slab(const HostProblem& hp, const DeviceData& dd, const double* x,
                                  double* y, int slab, int stages, cudaStream_t st) {
-  return dispatch<double>(hp, dd, x, y, 0, 1, dd.face_out, dd.ycol, 0, dd.variant[0], st,
+  return dispatch<double>(hp, dd, x, y, 0, 1, dd.face_out, dd.ycol, 0, dd.variant[0], false, st,
                           nullptr, slab, stages);
 }
 
@@ -238,7 +353,8 @@ template <typename T>
 cudaError_t launch_cg_apply_scratch(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
                                     T* face_scratch, T* colour_scratch, int variant,
                                     cudaStream_t st) {
-  return dispatch<T>(hp, dd, x, y, 0, 1, face_scratch, colour_scratch, 0, variant, st, nullptr);
+  return dispatch<T>(hp, dd, x, y, 0, 1, face_scratch, colour_scratch, 0, variant, false, st,
+                     nullptr);
 }
 template cudaError_t launch_cg_apply_scratch<double>(const HostProblem&, const DeviceData&,
                                                      const double*, double*, double*, double*,

@@ -49,6 +49,108 @@ struct ChunkArgs {
   int64_t ldx, ld_ycol, ld_face;
 };
 
+// ---- colour-ordered stores ----------------------------------------------------
+//
+// The alternative to colour buffers and the assembly pass (single applies):
+// the chunks run in ascending colour order, taken from a ticket counter.  A
+// DoF several colours share is stored by its lowest colour's chunk, then
+// read, added to and stored back by each higher colour's chunk in colour
+// order -- the sum and the order of the assembly, so y is bitwise the same.
+// Before its stores a chunk waits (bounded) for the lower-colour chunks it
+// shares a DoF with: per-chunk completion counts that every launch raises by
+// one, the target being the chunk's own count + 1 (no reset between
+// launches).  Every dependency has a smaller ticket, taken by a block that
+// is running, so the order cannot deadlock; on expiry the block records
+// SBM_ERR_TIMEOUT and still stores and counts its chunk, so the counts stay
+// in step.  The last block to finish resets the ticket counters.
+struct OrdArgs {
+  const int32_t* __restrict__ ord;       // ticket -> chunk (colours ascending)
+  const uint32_t* __restrict__ add_bits; // per chunk: run elements to read-add-write
+  const int32_t* __restrict__ deps;      // [nchunk][cap] lower-colour neighbours
+  const int32_t* __restrict__ ndeps;
+  int* done;                             // [nchunk] completion counts
+  unsigned* tickets;                     // [0] next ticket, [1] blocks finished
+  int* err;
+  int nch, cap;
+};
+constexpr long long kOrdPolls = 1ll << 20;     // about a second of polling
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// relaxed (no ordering of later accesses: the first look at a count is
+// issued before the compute and must not hold it up); fence_acquire_gpu
+// after the counts were seen orders the reads of y that follow
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acquire_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// wrap-safe count comparison
+__device__ __forceinline__ bool count_reached(int v, int target) {
+  return (int)((unsigned)v - (unsigned)target) >= 0;
+}
+
+// The first look at chunk ch's lower-colour neighbours, issued early (one
+// per thread, blockDim >= cap) and checked by ord_wait after the compute.
+__device__ __forceinline__ int ord_peek(const OrdArgs& o, int ch, int target) {
+  const int nd = __ldg(o.ndeps + ch);
+  return (int)threadIdx.x < nd
+             ? ld_relaxed_gpu(o.done + __ldg(o.deps + (size_t)ch * o.cap + threadIdx.x))
+             : target;
+}
+
+// Block-wide: wait until chunk ch's lower-colour neighbours are done
+// (count >= target), bounded; peek: this thread's ord_peek.  All threads
+// call it.
+__device__ __forceinline__ void ord_wait(const OrdArgs& o, int ch, int target, int peek) {
+  if (__syncthreads_and(count_reached(peek, target))) {
+    if ((int)threadIdx.x < __ldg(o.ndeps + ch)) fence_acquire_gpu();
+    __syncthreads();
+    return;
+  }
+  const int nd = __ldg(o.ndeps + ch);
+  const int32_t* dl = o.deps + (size_t)ch * o.cap;
+  for (long long it = 0;; ++it) {
+    int ok = 1;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x)
+      if (!count_reached(ld_acquire_gpu(o.done + __ldg(dl + i)), target)) ok = 0;
+    if (__syncthreads_and(ok)) return;
+    if (it >= kOrdPolls) {
+      if (threadIdx.x == 0) atomicExch(o.err, SBM_ERR_TIMEOUT);
+      return;
+    }
+    __nanosleep(128);
+  }
+}
+
+// The block's last act: count it out; the last one resets the counters for
+// the next launch.
+__device__ __forceinline__ void ord_exit(const OrdArgs& o) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    if (atomicAdd(o.tickets + 1, 1u) == nb - 1u) {
+      atomicExch(o.tickets, 0u);
+      atomicExch(o.tickets + 1, 0u);
+    }
+  }
+}
+
+// a ticket's chunk, or -1 past the last
+__device__ __forceinline__ int ord_chunk(const OrdArgs& o, int tk) {
+  return tk < o.nch ? __ldg(o.ord + tk) : -1;
+}
+
 // Add the contributions of surrogate face (k, s) to the z-line result out[]
 // (nodes (a, b, m), m = 0..n-1) of a 3D cell: R[node with j_k = kend] +=
 // rv[jt], R[node] += phi_{j_k}'(s) rg[jt], jt = the node's tangential index
@@ -311,6 +413,139 @@ __device__ __forceinline__ void chunk_loop(const ChunkArgs<T>& a, const KTab<T>&
   cp_async_wait<0>();
 }
 
+// chunk_loop with colour-ordered stores (single applies, one right-hand
+// side, a block of exactly R L threads): the chunks come from the ticket
+// counter, the next ticket taken one chunk ahead; a chunk peeks at its
+// lower-colour neighbours' counts before its compute and waits, if it must,
+// before its stores.
+__shared__ int s_ord_next;
+template <typename T, int D, int N, int R>
+__device__ __forceinline__ void chunk_loop_ord(const ChunkArgs<T>& a, const KTab<T>& t,
+                                               unsigned char* smem_raw, const OrdArgs& o) {
+  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, P = N - 1;
+  constexpr int SM = ChunkSmem<T, D, N, R>::SM;
+  using P2 = typename PairOf<T>::type;
+  using CS = ChunkSmem<T, D, N, R>;
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  P2* AE = reinterpret_cast<P2*>(smem_raw);
+  T* Xbuf = tile + CS::TILE;
+  T* XLs = Xbuf + 2 * CS::XS;
+  int* Lbuf = reinterpret_cast<int*>(XLs + CS::XL);
+  uint32_t* Bs = reinterpret_cast<uint32_t*>(Lbuf + 2 * L);
+  const int tid = threadIdx.x;
+  const int c = tid / L, tl = tid - c * L;
+  const XLineShared<T, N> xop{XLs + tl * XLineOp<T, N>::kSize};
+  const T* __restrict__ xr = a.x;
+  T* yb = a.y;
+
+  if (tid == 0) s_ord_next = (int)atomicAdd(o.tickets, 1u);
+  __syncthreads();
+  int ch = ord_chunk(o, s_ord_next);
+  __syncthreads();                            // s_ord_next read by all
+  int buf = 0;
+  if (ch >= 0) {
+    const int first = __ldg(a.chunk_first + ch);
+    const int S = P * (__ldg(a.chunk_first + ch + 1) - first) + 1;
+    for (int i = tid; i < L; i += blockDim.x) Lbuf[i] = __ldg(a.lines + (size_t)first * L + i);
+    __syncthreads();
+    if (tid == 0) s_ord_next = (int)atomicAdd(o.tickets, 1u);
+    gather_runs_async<T, L, SM>(xr, Lbuf, Xbuf, S, tid, R * L);
+  }
+  cp_async_commit();
+  __syncthreads();                            // s_ord_next written
+  for (; ch >= 0; buf ^= 1) {
+    T* Xs = Xbuf + buf * CS::XS;
+    const int* Ls = Lbuf + buf * L;
+    T* Z = (D == 3) ? tile : Xs;
+    const int first = __ldg(a.chunk_first + ch);
+    const int nc = __ldg(a.chunk_first + ch + 1) - first;
+    const int S = P * nc + 1;
+    const float invS = 1.0f / (float)S;
+    const int target = __ldcg(o.done + ch) + 1;
+    const int peek = ord_peek(o, ch, target);
+    const int nx = ord_chunk(o, s_ord_next);
+    // the ticket after nx, taken now and published after the compute (its
+    // latency hidden behind this chunk)
+    unsigned tk2 = 0u;
+    if (nx >= 0) {
+      const int f2 = __ldg(a.chunk_first + nx);
+      const int S2 = P * (__ldg(a.chunk_first + nx + 1) - f2) + 1;
+      int* Ln = Lbuf + (buf ^ 1) * L;
+      for (int i = tid; i < L; i += blockDim.x) Ln[i] = __ldg(a.lines + (size_t)f2 * L + i);
+      if (tid == 0) tk2 = atomicAdd(o.tickets, 1u);
+      __syncthreads();
+      gather_runs_async<T, L, SM>(xr, Ln, Xbuf + (buf ^ 1) * CS::XS, S2, tid, R * L);
+    }
+    cp_async_commit();
+    {
+      const uint32_t* bits = o.add_bits + (size_t)ch * a.bit_words;
+      for (int i = tid; i < (L * S + 31) / 32; i += blockDim.x) Bs[i] = __ldg(bits + i);
+    }
+    cp_async_wait<1>();
+    __syncthreads();
+    const bool act = c < nc;
+    T out[N];
+    if constexpr (D == 3)
+      cell_fd_3d<T, N>(t, Xs, (tl / N) * SM + P * c + (tl % N), N * SM, tile, c, tl, act, xop,
+                       out);
+    else
+      cell_sweeps_2d<T, N>(t, Xs, P * c + tl, SM, AE, c, tl, act, out);
+    if (act) {
+      const int pos = first + c;
+      const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);
+      for (int f = fs; f < fe; ++f) {
+        const int kind = __ldg(a.face_kind + f);
+        if constexpr (D == 3)
+          fold_face_z<T, N, false>(t, a.face_out + (size_t)f * 2 * L, kind & 3, kind >> 2,
+                                   tl % N, tl / N, out);
+        else
+          fold_face<T, D, N, false>(t, a.face_out + (size_t)f * 2 * L, kind & 3, kind >> 2, tl,
+                                    out);
+      }
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        if constexpr (D == 3) Z[c * ND + tl + L * m] = out[m];
+        else Z[(c * L + tl) * N + m] = out[m];
+      }
+    }
+    __syncthreads();
+    ord_wait(o, ch, target, peek);
+    // a thread's run elements (at most n of them: L S <= L (P R + 1) <=
+    // n R L): first the earlier colours' partial sums where the bit is set,
+    // loaded together, then the values (again from shared memory, the node
+    // shared by cells c-1 and c summed in chunk_loop's order) and the stores
+    T old[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int idx = tid + k * R * L;
+      old[k] = T(0);
+      if (idx < L * S && ((Bs[idx >> 5] >> (idx & 31)) & 1u)) {
+        const int l = __float2int_rz(((float)idx + 0.5f) * invS);
+        old[k] = __ldcg(yb + Ls[l] + (idx - l * S));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int idx = tid + k * R * L;
+      if (idx < L * S) {
+        const int l = __float2int_rz(((float)idx + 0.5f) * invS), kk = idx - l * S;
+        const int cc = kk / P, m = kk - cc * P;
+        T v;
+        if (cc == nc) v = Z[((nc - 1) * L + l) * N + P];
+        else if (m == 0 && cc > 0) v = Z[((cc - 1) * L + l) * N + P] + Z[(cc * L + l) * N];
+        else v = Z[(cc * L + l) * N + m];
+        yb[(int64_t)Ls[l] + kk] = ((Bs[idx >> 5] >> (idx & 31)) & 1u) ? old[k] + v : v;
+      }
+    }
+    if (tid == 0 && nx >= 0) s_ord_next = (int)tk2;
+    __syncthreads();                          // Xs / Z / Ls / Bs are reused
+    if (tid == 0) st_release_gpu(o.done + ch, target);
+    ch = nx;
+  }
+  cp_async_wait<0>();
+  ord_exit(o);
+}
+
 // For the DoFs i = multi[t], t in [t0, t0 + 32) of one warp (lanes past
 // nmulti idle): y_i = sum_{c in mask_i} ycol[c][i], colours in increasing
 // order.  Lane by lane the j-th step adds the value of the lane's j-th colour
@@ -370,6 +605,138 @@ __device__ __forceinline__ void assemble_warp(const T* __restrict__ ycol,
       if ((unsigned)j < cnt) acc += v[j];
   }
   if (t < nmulti) __stcs(y + i, acc);
+}
+
+
+// ---- tile shape 3: the chunk loop without staged runs (3D) ------------------------
+//
+// The same chunks, phases, folds, x-face sums and single-writer stores as
+// chunk_loop, but each thread loads its own z-line (j0, j1) of x straight
+// from global memory (the chunk's runs start at its first cell's lines, cell
+// c P c further) and stores its own z-line result straight to y or to the
+// chunk's colour buffer; only the x-face nodes two cells of the chunk share
+// pass through shared memory (prev + own, as chunk_loop sums them).  Without
+// the run staging and its index splitting a chunk costs a third of the
+// instructions; the arithmetic and the summation order are unchanged, so the
+// results are bitwise those of tile shape 0.
+template <typename T, int N, int R>
+struct DirectSmem {
+  static constexpr int L = N * N, ND = L * N, P = N - 1;
+  static constexpr int TILE = R * ND;                    // the cells' tiles
+  static constexpr int XL = L * XLineOp<T, N>::kSize;    // x-line operators
+  static constexpr int XF = R * L;                       // j0 = P faces of the cells
+  static constexpr int WORDS = (L * (P * R + 1) + 31) / 32;
+  static constexpr size_t bytes = (size_t)(TILE + XL + XF) * sizeof(T) + (size_t)(L + WORDS) * 4;
+};
+
+template <typename T, int N, int R, bool COH, bool ORD = false>
+__device__ __forceinline__ void chunk_loop_direct(const ChunkArgs<T>& a, const KTab<T>& t,
+                                                  const KTab<T>& tx, unsigned char* smem_raw,
+                                                  int rhs, int ch, int q1, int step,
+                                                  const OrdArgs* o = nullptr) {
+  constexpr int L = N * N, ND = L * N, P = N - 1;
+  using DS = DirectSmem<T, N, R>;
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  T* XLs = tile + DS::TILE;
+  T* XF = XLs + DS::XL;
+  int* Ls = reinterpret_cast<int*>(XF + DS::XF);
+  uint32_t* Bs = reinterpret_cast<uint32_t*>(Ls + L);
+  const int tid = threadIdx.x;
+  const int c = tid / L, tl = tid - c * L;
+  const int j0 = tl % N, j1 = tl / N;
+  if (tid < L) XLineOp<T, N>(tx, tid % N, tid / N).store(XLs + tid * XLineOp<T, N>::kSize);
+  const XLineShared<T, N> xop{XLs + tl * XLineOp<T, N>::kSize};
+  const T* __restrict__ xr = a.x + rhs * a.ldx;
+  const T* fo = a.face_out + rhs * a.ld_face;
+  T* ycb = a.ycol + rhs * a.ld_ycol;
+  T* yb = a.y + rhs * a.ldx;
+  if constexpr (ORD) {
+    if (tid == 0) s_ord_next = (int)atomicAdd(o->tickets, 1u);
+    __syncthreads();
+    ch = ord_chunk(*o, s_ord_next);
+    q1 = ch + 1;
+    step = 0;
+  }
+  while (ORD ? ch >= 0 : ch < q1) {
+    const int first = __ldg(a.chunk_first + ch);
+    const int nc = __ldg(a.chunk_first + ch + 1) - first;
+    const int S = P * nc + 1;
+    int target = 0, peek = 0;
+    if constexpr (ORD) {
+      target = __ldcg(o->done + ch) + 1;
+      peek = ord_peek(*o, ch, target);
+    }
+    for (int i = tid; i < L; i += blockDim.x) Ls[i] = __ldg(a.lines + (size_t)first * L + i);
+    {
+      const uint32_t* bits = (ORD ? o->add_bits : a.run_bits) + (size_t)ch * a.bit_words;
+      for (int i = tid; i < (L * S + 31) / 32; i += blockDim.x) Bs[i] = __ldg(bits + i);
+    }
+    // the next ticket, taken now and published before the last barrier
+    unsigned tk2 = 0u;
+    if constexpr (ORD) {
+      if (tid == 0) tk2 = atomicAdd(o->tickets, 1u);
+    }
+    __syncthreads();                          // Ls, Bs; the x-line operators (first chunk)
+    const bool act = c < nc;
+    T out[N];
+    cell_fd_3d_l<T, N>(
+        t, [&](int j) { return __ldg(xr + Ls[j1 + N * j] + P * c + j0); }, tile, c, tl, act, xop,
+        out);
+    if (act) {
+      const int pos = first + c;
+      const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);
+      for (int f = fs; f < fe; ++f) {
+        const int kind = __ldg(a.face_kind + f);
+        fold_face_z<T, N, COH>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, j0, j1, out);
+      }
+      if (j0 == P && c < nc - 1) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) XF[c * L + j1 + N * m] = out[m];
+      }
+    }
+    __syncthreads();
+    if constexpr (ORD) ord_wait(*o, ch, target, peek);
+    if (act && !(j0 == P && c < nc - 1)) {
+      if (j0 == 0 && c > 0) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) out[m] = add_rn(XF[(c - 1) * L + j1 + N * m], out[m]);
+      }
+      if constexpr (ORD) {       // the earlier colours' partial sums, loaded together
+        T old[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          const int e = (j1 + N * m) * S + P * c + j0;
+          old[m] = ((Bs[e >> 5] >> (e & 31)) & 1u) ? __ldcg(yb + Ls[j1 + N * m] + P * c + j0)
+                                                   : T(0);
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          const int e = (j1 + N * m) * S + P * c + j0;
+          yb[(int64_t)Ls[j1 + N * m] + P * c + j0] =
+              ((Bs[e >> 5] >> (e & 31)) & 1u) ? old[m] + out[m] : out[m];
+        }
+      } else {
+        T* yc = ycb + (size_t)__ldg(a.chunk_col + ch) * a.n_dofs;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          const int l = j1 + N * m, e = l * S + P * c + j0;
+          const bool bit = (Bs[e >> 5] >> (e & 31)) & 1u;
+          (bit ? yc : yb)[(int64_t)Ls[l] + P * c + j0] = out[m];
+        }
+      }
+    }
+    if constexpr (ORD) {
+      if (tid == 0) s_ord_next = (int)tk2;
+    }
+    __syncthreads();                          // Ls, Bs, XF and the tile are reused
+    if constexpr (ORD) {
+      if (tid == 0) st_release_gpu(o->done + ch, target);
+      ch = ord_chunk(*o, s_ord_next);
+    } else {
+      ch += step;
+    }
+  }
+  if constexpr (ORD) ord_exit(*o);
 }
 
 }  // namespace sbm

@@ -71,6 +71,19 @@ struct ChunkTable {
                                  //   colour count (2, 3-4, 5-8), ascending within a group
   uint8_t* multi_mask = nullptr; // [nmulti] their colour masks
   int64_t nmulti = 0;
+  // colour-ordered stores (chunking of tile shape 0; ordered == false where
+  // not built): chunks by ascending colour (ticket -> chunk), per chunk the
+  // run bits of the DoFs a lower colour also touches (read-add-write), the
+  // chunks of lower colours it shares a DoF with ([n][dep_cap], ndeps of
+  // them), per-chunk completion counts and the ticket / exit counters
+  bool ordered = false;
+  int dep_cap = 0;
+  int32_t* ord = nullptr;
+  uint32_t* add_bits = nullptr;
+  int32_t* deps = nullptr;
+  int32_t* ndeps = nullptr;
+  int32_t* done = nullptr;
+  uint32_t* tickets = nullptr;   // [2]
   // slabs of the pipelined host-buffer apply: chunks [slab_chunk[s],
   // slab_chunk[s+1]), shared DoFs multi[slab_multi[s], slab_multi[s+1])
   std::vector<int> slab_chunk;
@@ -81,12 +94,14 @@ struct ChunkTable {
 // of every DoF (from the chunk-ordered line table `lines` on the device), the
 // list of DoFs several colours share and the per-chunk run bits, into ct.
 // The shared DoFs are listed slab by slab (slab s: DoFs [ycut[s], ycut[s+1]);
-// ct->slab_multi receives the offsets), then by colour count.
+// ct->slab_multi receives the offsets), then by colour count.  ordered:
+// also the tables of the colour-ordered stores (ct->ordered stays false if a
+// chunk has more lower-colour neighbours than the dependency table holds).
 cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, int64_t n_dofs,
                                 const std::vector<int32_t>& ch_first,
                                 const std::vector<uint8_t>& ch_col, int R,
                                 const int32_t* first_dev, const std::vector<int64_t>& ycut,
-                                ChunkTable* ct);
+                                ChunkTable* ct, bool ordered);
 
 // The 1D Lagrange values at every shifted surrogate point (exact extension) or
 // the shift vectors (first-order Taylor), in kernel face order (fsrc[k] = the
@@ -117,6 +132,7 @@ struct DeviceData {
   int* err_flag = nullptr;       // device error word (SBM_ERR_TIMEOUT from bounded waits)
   ChunkTable chunks[2];          // CG: R and R/2 cells per chunk (two tile shapes)
   int variant[2] = {0, 0};       // tile shape of the single applies: [FP64, FP32]
+  bool ordered[2] = {false, false};  // colour-ordered stores instead of the assembly
   // tile shape 2 (3D CG, n <= 5; cell_reg.cu): one thread per cell on the
   // chunks of shape 0 -- chunk of every ordered cell, blocks of whole
   // chunks, per-cell bits of the nodes several colours share

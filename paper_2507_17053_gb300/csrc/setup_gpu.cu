@@ -19,6 +19,7 @@
 // where the rest of the set-up continues.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -449,6 +450,67 @@ __global__ void k_run_bits(int nch, int L, int P, int R, int words, const int32_
   }
 }
 
+// ---- colour-ordered stores ----------------------------------------------------
+constexpr int kDepCap = 64;       // lower-colour neighbours a chunk may have
+
+// owner[g ncol + colour] = the chunk of that colour that touches DoF g, for
+// the DoFs several colours share (the chunks of one colour are disjoint)
+__global__ void k_dof_owner(int nch, int L, int P, int R, int ncol,
+                            const int32_t* __restrict__ first, const int32_t* __restrict__ lines,
+                            const uint8_t* __restrict__ col, const uint32_t* __restrict__ mask,
+                            int32_t* __restrict__ owner) {
+  const int Smax = P * R + 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nch * L * Smax;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / ((int64_t)L * Smax));
+    const int r = (int)(t - (int64_t)k * L * Smax);
+    const int l = r / Smax, kk = r - l * Smax;
+    if (kk >= P * (first[k + 1] - first[k]) + 1) continue;
+    const int64_t g = (int64_t)lines[(int64_t)first[k] * L + l] + kk;
+    if (__popc(mask[g]) >= 2) owner[g * ncol + col[k]] = k;
+  }
+}
+
+// Per chunk: the run bits of the DoFs a lower colour also touches, and the
+// set of lower-colour chunks it shares a DoF with (deps[k][0..ndeps[k]),
+// deduplicated; more than kDepCap sets *overflow).
+__global__ void k_chunk_deps(int nch, int L, int P, int R, int ncol, int words,
+                             const int32_t* __restrict__ first, const int32_t* __restrict__ lines,
+                             const uint8_t* __restrict__ col, const uint32_t* __restrict__ mask,
+                             const int32_t* __restrict__ owner, int32_t* __restrict__ deps,
+                             int32_t* __restrict__ ndeps, uint32_t* __restrict__ add_bits,
+                             int* __restrict__ overflow) {
+  const int Smax = P * R + 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)nch * L * Smax;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / ((int64_t)L * Smax));
+    const int r = (int)(t - (int64_t)k * L * Smax);
+    const int l = r / Smax, kk = r - l * Smax;
+    const int S = P * (first[k + 1] - first[k]) + 1;
+    if (kk >= S) continue;
+    const int64_t g = (int64_t)lines[(int64_t)first[k] * L + l] + kk;
+    const uint32_t m = mask[g];
+    uint32_t lower = m & ((1u << col[k]) - 1u);
+    if (__popc(m) < 2 || lower == 0u) continue;
+    const int b = l * S + kk;
+    atomicOr(add_bits + (size_t)k * words + b / 32, 1u << (b % 32));
+    for (; lower; lower &= lower - 1u) {
+      const int dep = owner[g * ncol + (__ffs(lower) - 1)];
+      int32_t* list = deps + (size_t)k * kDepCap;
+      int i = 0;
+      for (; i < kDepCap; ++i) {
+        const int old = atomicCAS(list + i, -1, dep);
+        if (old == -1) {
+          atomicAdd(ndeps + k, 1);
+          break;
+        }
+        if (old == dep) break;
+      }
+      if (i == kDepCap) atomicExch(overflow, 1);
+    }
+  }
+}
+
 struct LagArgs {
   int n, d, L, taylor;
   double nodes[kMaxN], lam[kMaxN];
@@ -492,7 +554,7 @@ cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, 
                                 const std::vector<int32_t>& ch_first,
                                 const std::vector<uint8_t>& ch_col, int R,
                                 const int32_t* first_dev, const std::vector<int64_t>& ycut,
-                                ChunkTable* ct) {
+                                ChunkTable* ct, bool ordered) {
   DevBufs B;
   const int nch = (int)ch_col.size();
   std::vector<uint8_t> col(nc);
@@ -559,6 +621,47 @@ cudaError_t device_chunk_tables(const int32_t* lines, int64_t nc, int L, int n, 
   k_run_bits<<<grid_for((int64_t)nch * L * (P * R + 1)), 256>>>(nch, L, P, R, words, first_dev,
                                                                 lines, mask, ct->run_bits);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ordered && nch > 0) {
+    // tickets in colour order (stable: row order within a colour)
+    std::vector<int32_t> ord(nch);
+    int at_ = 0;
+    for (int c = 0; c < 8; ++c)
+      for (int k = 0; k < nch; ++k)
+        if (ch_col[k] == c) ord[at_++] = k;
+    int ncol = 1;
+    for (int k = 0; k < nch; ++k) ncol = std::max(ncol, (int)ch_col[k] + 1);
+    int32_t* owner;
+    int* overflow;
+    const int64_t work = (int64_t)nch * L * (P * R + 1);
+    if ((e = B.alloc(&owner, (size_t)n_dofs * ncol)) != cudaSuccess ||
+        (e = B.alloc(&overflow, 1)) != cudaSuccess ||
+        (e = cudaMemset(overflow, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ct->ord, (size_t)nch * 4)) != cudaSuccess ||
+        (e = cudaMemcpy(ct->ord, ord.data(), (size_t)nch * 4, cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMalloc((void**)&ct->add_bits, (size_t)nch * words * 4)) != cudaSuccess ||
+        (e = cudaMemset(ct->add_bits, 0, (size_t)nch * words * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ct->deps, (size_t)nch * kDepCap * 4)) != cudaSuccess ||
+        (e = cudaMemset(ct->deps, 0xff, (size_t)nch * kDepCap * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ct->ndeps, (size_t)nch * 4)) != cudaSuccess ||
+        (e = cudaMemset(ct->ndeps, 0, (size_t)nch * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ct->done, (size_t)nch * 4)) != cudaSuccess ||
+        (e = cudaMemset(ct->done, 0, (size_t)nch * 4)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&ct->tickets, 2 * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMemset(ct->tickets, 0, 2 * sizeof(uint32_t))) != cudaSuccess)
+      return e;
+    k_dof_owner<<<grid_for(work), 256>>>(nch, L, P, R, ncol, first_dev, lines, ct->colour, mask,
+                                         owner);
+    k_chunk_deps<<<grid_for(work), 256>>>(nch, L, P, R, ncol, words, first_dev, lines,
+                                          ct->colour, mask, owner, ct->deps, ct->ndeps,
+                                          ct->add_bits, overflow);
+    int of = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpy(&of, overflow, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return e;
+    ct->dep_cap = kDepCap;
+    ct->ordered = of == 0;
+  }
   return cudaDeviceSynchronize();
 }
 

@@ -272,17 +272,18 @@ struct XLineShared {
   }
 };
 
-template <typename T, int N, typename XOp>
-__device__ __forceinline__ void cell_fd_3d(const KTab<T>& t, const T* X, int xb, int xs, T* tile,
-                                           int c, int tl, bool act, const XOp& xop,
-                                           T (&out)[N]) {
+// The thread's z-line of x comes from load(j), j = 0..n-1 (staged runs in
+// shared memory, or global memory directly).
+template <typename T, int N, typename XOp, typename Load>
+__device__ __forceinline__ void cell_fd_3d_l(const KTab<T>& t, const Load& load, T* tile, int c,
+                                             int tl, bool act, const XOp& xop, T (&out)[N]) {
   constexpr int L = N * N, ND = L * N;
   const int a = tl % N, b = tl / N;
   T* cell = tile + c * ND;
   if (act) {                       // z-lines (j0, j1) = (a, b) -> z-modes
     T v[N], w[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = X[xb + xs * j];
+    for (int j = 0; j < N; ++j) v[j] = load(j);
     line_to_modes<T, N>(t.fVt, v, w);
 #pragma unroll
     for (int k = 0; k < N; ++k) cell[tl + L * k] = w[k];
@@ -321,6 +322,13 @@ __device__ __forceinline__ void cell_fd_3d(const KTab<T>& t, const T* X, int xb,
     for (int k = 0; k < N; ++k) w[k] = cell[tl + L * k];
     modes_to_line<T, N>(t.fV, w, out);
   }
+}
+
+template <typename T, int N, typename XOp>
+__device__ __forceinline__ void cell_fd_3d(const KTab<T>& t, const T* X, int xb, int xs, T* tile,
+                                           int c, int tl, bool act, const XOp& xop,
+                                           T (&out)[N]) {
+  cell_fd_3d_l<T, N>(t, [&](int j) { return X[xb + xs * j]; }, tile, c, tl, act, xop, out);
 }
 
 // ---- cell term -------------------------------------------------------------

@@ -145,7 +145,7 @@ def test_autotuned_tile_shapes_keep_parity(w):
     xd = torch.from_numpy(x).cuda()
     ref = O.apply(x)
     shapes = G.sbm_autotune(P.handle)
-    assert all(s in (0, 1) for s in shapes)
+    assert all(s in ((0, 1, 2, 3) if w.dim == 3 else (0, 1)) for s in shapes)
     assert _rel(P.apply_f64(xd).cpu().numpy(), ref) <= TOL
     ref32 = O.apply(x.astype(np.float32).astype(np.float64))
     y32 = P.apply_f32(xd.float()).double().cpu().numpy()
@@ -156,7 +156,7 @@ def test_autotuned_tile_shapes_keep_parity(w):
         assert _rel(P.apply_f64(xd).cpu().numpy(), ref) <= TOL
         assert _rel(P.apply_f32(xd.float()).double().cpu().numpy(), ref32) <= F32_TOL
     with pytest.raises(G.SbmError):
-        G.sbm_set_tile_shape(P.handle, 3, 0)
+        G.sbm_set_tile_shape(P.handle, 4, 0)
 
 
 # tile shape 2: one thread per cell, the tile in registers (3D, FP32 p <= 4,
@@ -192,8 +192,84 @@ def test_register_tile_shape_equals_shape0_and_oracle(w):
 def test_register_tile_shape_rejected_where_unavailable():
     for w, shapes in ((S.SPHERE_3D_Q4.resized(6, degree=5), (-1, 2)),
                       (S.SPHERE_3D_Q4.resized(6, degree=4), (2, -1)),
-                      (S.DISK_2D_Q2, (-1, 2))):
+                      (S.DISK_2D_Q2, (-1, 2)), (S.DISK_2D_Q2, (3, -1)),
+                      (S.TORUS_3D_DG_Q3.resized(8), (3, -1))):
         P = G.Problem.from_workload(w)
         with pytest.raises(G.SbmError) as e:
             G.sbm_set_tile_shape(P.handle, *shapes)
         assert G.STATUS[e.value.status] == "SBM_ERR_UNSUPPORTED"
+
+
+# tile shape 3 (3D, every degree): shape 0's chunks, each thread loading and
+# storing its own z-lines instead of staging x-line runs in shared memory
+DIRECT_CASES = [S.SPHERE_3D_Q4.resized(7, degree=p) for p in range(1, 7)] \
+    + [S.SPHERE_3D_Q4.resized(17, degree=2), S.ELLIPSOID_3D_Q6.resized(10), _TWO_BALLS_3D] \
+    + S.batched_ellipsoids(nprob=3, n_range=(7, 11))
+
+
+@pytest.mark.parametrize("w", DIRECT_CASES, ids=lambda w: f"{w.name}_q{w.degree}")
+def test_direct_tile_shape_equals_shape0_and_oracle(w):
+    O, P = _pair(w)
+    x = S.random_vector(w.seed, O.n_dofs, w.dist)
+    xd = torch.from_numpy(x).cuda()
+    ref = O.apply(x)
+    ref32 = O.apply(x.astype(np.float32).astype(np.float64))
+    G.sbm_set_tile_shape(P.handle, 0, 0)
+    y64_0, y32_0 = P.apply_f64(xd), P.apply_f32(xd.float())
+    yh_0 = P.apply_f64_host(x)
+    G.sbm_set_tile_shape(P.handle, 3, 3)
+    y64, y32 = P.apply_f64(xd), P.apply_f32(xd.float())
+    assert torch.equal(y64, y64_0), "shape 3 differs from shape 0 in FP64"
+    assert torch.equal(y32, y32_0), "shape 3 differs from shape 0 in FP32"
+    assert torch.equal(y64, P.apply_f64(xd)), "repeated apply differs"
+    assert _rel(y64.cpu().numpy(), ref) <= TOL
+    assert _rel(y32.double().cpu().numpy(), ref32) <= F32_TOL
+    # the host-buffer pipeline runs shape 3 slab by slab: the same bits
+    assert np.array_equal(P.apply_f64_host(x), yh_0)
+
+
+# colour-ordered stores (no colour buffers, no assembly pass): bitwise the
+# colour-buffer applies of the same tile shape, applied repeatedly (the
+# per-chunk completion counts carry over between launches)
+ORDERED_CASES = [S.SPHERE_3D_Q4.resized(9, degree=p) for p in range(1, 7)] \
+    + [S.DISK_2D_Q2.resized(13, degree=p) for p in range(1, 7)] \
+    + [S.DISK_2D_Q2, S.SPHERE_3D_Q4.resized(24), S.ELLIPSOID_3D_Q6.resized(10), _TWO_BALLS_3D,
+       _TWO_BALLS_2D] + S.batched_ellipsoids(nprob=3, n_range=(7, 11))
+
+
+@pytest.mark.parametrize("w", ORDERED_CASES, ids=lambda w: f"{w.name}_q{w.degree}")
+def test_ordered_stores_equal_colour_buffers(w):
+    O, P = _pair(w)
+    x = S.random_vector(w.seed, O.n_dofs, w.dist)
+    xd = torch.from_numpy(x).cuda()
+    ref = O.apply(x)
+    ref32 = O.apply(x.astype(np.float32).astype(np.float64))
+    for shape in [0] + ([3] if w.dim == 3 else []):
+        G.sbm_set_tile_shape(P.handle, shape, shape)
+        G.sbm_set_ordered_stores(P.handle, 0, 0)
+        y64_0, y32_0 = P.apply_f64(xd), P.apply_f32(xd.float())
+        G.sbm_set_ordered_stores(P.handle, 1, 1)
+        assert G.sbm_ordered_stores(P.handle) == (1, 1)
+        for rep in range(3):
+            y64, y32 = P.apply_f64(xd), P.apply_f32(xd.float())
+            assert torch.equal(y64, y64_0), f"FP64 shape {shape}: ordered != colour buffers"
+            assert torch.equal(y32, y32_0), f"FP32 shape {shape}: ordered != colour buffers"
+        G.sbm_device_status(P.handle)
+        assert _rel(y64.cpu().numpy(), ref) <= TOL
+        assert _rel(y32.double().cpu().numpy(), ref32) <= F32_TOL
+    # the host-buffer pipeline keeps the colour buffers: the same bits
+    assert np.array_equal(P.apply_f64_host(x), y64_0.cpu().numpy())
+
+
+def test_ordered_stores_autotuned_and_rejected_for_dg():
+    w = S.SPHERE_3D_Q4.resized(20)
+    O, P = _pair(w)
+    x = S.random_vector(w.seed, O.n_dofs, w.dist)
+    xd = torch.from_numpy(x).cuda()
+    G.sbm_autotune(P.handle)
+    assert all(o in (0, 1) for o in G.sbm_ordered_stores(P.handle))
+    assert _rel(P.apply_f64(xd).cpu().numpy(), O.apply(x)) <= TOL
+    D = G.Problem.from_workload(S.TORUS_3D_DG_Q3.resized(8))
+    with pytest.raises(G.SbmError) as e:
+        G.sbm_set_ordered_stores(D.handle, 1, -1)
+    assert G.STATUS[e.value.status] == "SBM_ERR_UNSUPPORTED"
