@@ -321,19 +321,22 @@ int sbm_batch_apply_f32(sbm_batch* batch, const float* const* x, float* const* y
 int sbm_batch_apply_f64(sbm_batch* batch, const double* const* x, double* const* y,
                         void* stream);
 
-/* Tile shape (0 or 1) of a problem's cell chunks (the FP32 choice; both
- * precisions after an override); override it for both precisions (drops
- * the cached graphs; synchronises the device). */
+/* Tile shape (0, 1; 3 after the FP32 autotuner chose it) of a problem's
+ * cell chunks (the FP32 choice; both precisions after an override);
+ * override it for both precisions with 0 or 1 (drops the cached graphs;
+ * synchronises the device). */
 int sbm_batch_tile_shape(const sbm_batch* batch, int problem, int* variant);
 int sbm_batch_set_tile_shape(sbm_batch* batch, int problem, int variant);
 
 /*
  * The autotuner's record for one degree and precision (32 or 64):
- * *tile_shape (0: R cells per chunk, 1: R/2), *face_batch (0: 256/L faces
- * per pass, 1: 128/L), *tensor_cores (tensor-core face path on: 1, off: 0);
- * ms[8] (may be NULL): the measured time in ms of that degree's sub-batch
- * for option index tile_shape + 2 face_batch + 4 tensor_cores, < 0 where
- * the option was not timed.  Any output may be NULL.
+ * *tile_shape (0: R cells per chunk, 1: R/2, 3: R cells without staged
+ * runs -- FP32 batches of 3D problems), *face_batch (0: 256/L faces per
+ * pass, 1: 128/L), *tensor_cores (tensor-core face path on: 1, off: 0);
+ * ms[10] (may be NULL): the measured time in ms of that degree's sub-batch
+ * for option index tile_shape + 2 face_batch + 4 tensor_cores (tile shapes
+ * 0 and 1) or 8 + face_batch (tile shape 3), < 0 where the option was not
+ * timed.  Any output may be NULL.
  * Errors: SBM_ERR_ARG (bad precision, no tuned problem of that degree).
  */
 int sbm_batch_knobs(const sbm_batch* batch, int precision, int degree, int* tile_shape,
@@ -341,11 +344,13 @@ int sbm_batch_knobs(const sbm_batch* batch, int precision, int degree, int* tile
 
 /*
  * Pin the knobs of one degree and precision (32 or 64) instead of the
- * autotuner's choice: tile shape (0, 1), face batch (0, 1), tensor-core
- * faces (0, 1; FP32 batches created with SBM_BATCH_TENSOR_CORES only).
+ * autotuner's choice: tile shape (0, 1, or 3 for FP32 batches of 3D
+ * problems), face batch (0, 1), tensor-core faces (0, 1; FP32 batches
+ * created with SBM_BATCH_TENSOR_CORES only, not with tile shape 3).
  * Drops the cached graphs; synchronises the device.
  * Errors: SBM_ERR_ARG (bad value, no problem of that degree),
- * SBM_ERR_UNSUPPORTED (tensor cores not allowed).
+ * SBM_ERR_UNSUPPORTED (tensor cores not allowed, tile shape 3 where it does
+ * not run).
  */
 int sbm_batch_set_knobs(sbm_batch* batch, int precision, int degree, int tile_shape,
                         int face_batch, int tensor_cores);

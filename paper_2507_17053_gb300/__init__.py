@@ -491,9 +491,10 @@ class Batch:
     def knobs(self, precision, degree):
         """The autotuner's choice for one degree: dict with tile_shape,
         face_batch, tensor_cores and ms (the timed options, index shape +
-        2 face_batch + 4 tensor_cores; None where not timed)."""
+        2 face_batch + 4 tensor_cores for tile shapes 0 and 1, 8 +
+        face_batch for tile shape 3; None where not timed)."""
         v, f, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        ms = (ctypes.c_float * 8)()
+        ms = (ctypes.c_float * 10)()
         _check(lib().sbm_batch_knobs(self.handle, precision, degree, ctypes.byref(v),
                                      ctypes.byref(f), ctypes.byref(t), ms), "sbm_batch_knobs")
         return {"tile_shape": v.value, "face_batch": f.value, "tensor_cores": t.value,

@@ -43,6 +43,10 @@ cudaError_t occupancy(int pi, size_t smem, bool tc, int* per_sm) {
   return pi ? bk::occupancy_f64(smem, tc, per_sm) : bk::occupancy_f32(smem, tc, per_sm);
 }
 
+// Tile shape 3 in the batch: FP32 (precision index 0), 3D problems (the
+// FP64 kernel's 48-register budget would make its loop spill).
+bool direct_ok(int pi, const sbm_problem* p) { return pi == 0 && p->hp.d == 3; }
+
 int face_batch_faces(int d, int n, int fh) {
   const int L = (d == 3) ? n * n : n;
   const int ff = bk::kThreads / L;
@@ -139,7 +143,7 @@ void make_items(const sbm_batch* B, int pi, const std::vector<int>& probs, int g
     const int d = p->hp.d, n = p->hp.n;
     const double cost = std::pow((double)n, d + 1);
     const double wface = (d == 3 ? 40.0 : 20.0) * cost, wcell = 10.0 * cost;
-    const int v = P.shape[k];
+    const int v = chunking(P.shape[k]);
     auto kn = P.knobs.find(p->hp.p);
     const int fh = (kn == P.knobs.end() || p->hp.desc.extension == SBM_EXT_TAYLOR1)
                        ? 0 : kn->second.face_batch;
@@ -280,7 +284,7 @@ void make_table(const sbm_batch* B, const LaunchPlan& L, const T* const* x, T* c
     const sbm_problem* p = B->probs[k];
     const DeviceData& dd = p->dd;
     const int v = P.shape[k];
-    const ChunkTable& ct = dd.chunks[v];
+    const ChunkTable& ct = dd.chunks[chunking(v)];
     auto kn = P.knobs.find(p->hp.p);
     const int fh = kn == P.knobs.end() ? 0 : kn->second.face_batch;
     const int ext = p->hp.desc.extension == SBM_EXT_TAYLOR1;
@@ -452,11 +456,12 @@ int autotune(sbm_batch* B) {
     size_t n = 0;
     for (int k : ks) {
       const sbm_problem* p = B->probs[k];
-      for (int v = 0; v < 2; ++v)
+      for (int v : {0, 1, 3})
         for (int fh = 0; fh < 2; ++fh)
-          smem = std::max(smem, item_smem(pi, p->hp.d, p->hp.n, v, fh,
-                                          p->hp.desc.extension == SBM_EXT_TAYLOR1,
-                                          P.allow_tc && pi == 0 && p->hp.d == 3));
+          if (v != 3 || direct_ok(pi, p))
+            smem = std::max(smem, item_smem(pi, p->hp.d, p->hp.n, v, fh,
+                                            p->hp.desc.extension == SBM_EXT_TAYLOR1,
+                                            P.allow_tc && pi == 0 && p->hp.d == 3));
       n += (size_t)p->hp.n_dofs * B->nrhs;
     }
     most = std::max(most, n);
@@ -483,9 +488,13 @@ int autotune(sbm_batch* B) {
     for (int k : ks)
       tc_ok |= B->probs[k]->hp.d == 3 && B->probs[k]->hp.desc.extension == SBM_EXT_EXACT;
     tc_ok = tc_ok && pi == 0 && P.allow_tc;
-    for (int opt = 0; opt < 8 && status == SBM_OK; ++opt) {
-      const int v = opt & 1, fh = (opt >> 1) & 1, tcv = opt >> 2;
-      if (tcv && (!tc_ok || fh)) continue;
+    // tile shape 3 (options 8, 9): FP32, when every problem of the degree is 3D
+    bool direct = pi == 0;
+    for (int k : ks) direct = direct && direct_ok(pi, B->probs[k]);
+    for (int opt = 0; opt < kKnobOptions && status == SBM_OK; ++opt) {
+      const int v = opt >= 8 ? 3 : (opt & 1), fh = opt >= 8 ? opt - 8 : (opt >> 1) & 1;
+      const int tcv = opt >= 8 ? 0 : opt >> 2;
+      if ((tcv && (!tc_ok || fh)) || (v == 3 && !direct)) continue;
       kn.shape = v;
       kn.face_batch = fh;
       kn.tc = tcv;
@@ -687,22 +696,29 @@ int sbm_batch_knobs(const sbm_batch* batch, int precision, int degree, int* tile
   if (face_batch) *face_batch = it->second.face_batch;
   if (tensor_cores) *tensor_cores = it->second.tc;
   if (ms)
-    for (int i = 0; i < 8; ++i) ms[i] = it->second.ms[i];
+    for (int i = 0; i < kKnobOptions; ++i) ms[i] = it->second.ms[i];
   return SBM_OK;
 }
 
 int sbm_batch_set_knobs(sbm_batch* batch, int precision, int degree, int tile_shape,
                         int face_batch, int tensor_cores) {
-  if (!batch || (precision != 32 && precision != 64) || tile_shape < 0 || tile_shape > 1 ||
-      face_batch < 0 || face_batch > 1 || tensor_cores < 0 || tensor_cores > 1)
+  if (!batch || (precision != 32 && precision != 64) || tile_shape < 0 || tile_shape > 3 ||
+      tile_shape == 2 || face_batch < 0 || face_batch > 1 || tensor_cores < 0 ||
+      tensor_cores > 1)
     return sbm_fail_detail(SBM_ERR_ARG, "bad argument");
   const int pi = precision == 64 ? 1 : 0;
   if (tensor_cores && (pi != 0 || !batch->prec[0].allow_tc))
     return sbm_fail_detail(SBM_ERR_UNSUPPORTED,
                            "tensor-core faces: FP32 batches created with SBM_BATCH_TENSOR_CORES");
+  if (tile_shape == 3 && tensor_cores)
+    return sbm_fail_detail(SBM_ERR_UNSUPPORTED, "tile shape 3 runs CUDA-core faces");
   bool any = false;
   for (size_t k = 0; k < batch->probs.size(); ++k)
-    if (batch->probs[k]->hp.p == degree) any = true;
+    if (batch->probs[k]->hp.p == degree) {
+      any = true;
+      if (tile_shape == 3 && !direct_ok(pi, batch->probs[k]))
+        return sbm_fail_detail(SBM_ERR_UNSUPPORTED, "tile shape 3: FP32 batches of 3D problems");
+    }
   if (!any) return sbm_fail_detail(SBM_ERR_ARG, "no problem of that degree");
   cudaDeviceSynchronize();
   BatchPrec& P = batch->prec[pi];

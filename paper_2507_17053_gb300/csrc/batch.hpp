@@ -49,15 +49,20 @@ struct BatchSolveWs {
 };
 
 // Knobs of one degree for one precision, chosen by the autotuner: the cell
-// kernel's tile shape (0: R cells per chunk, 1: R/2), the face batch (0:
-// 256/L faces per pass, 1: 128/L), tensor-core faces (FP32, 3D: 0 CUDA
-// cores, 1 TF32 tcgen05), and the measured time of every option tried (ms
-// of that degree's sub-batch; index shape + 2 face batch + 4 tensor cores;
-// < 0: not tried).
+// kernel's tile shape (0: R cells per chunk, 1: R/2, 3: R cells without
+// staged runs, 3D FP32), the face batch (0: 256/L faces per pass, 1:
+// 128/L), tensor-core faces (FP32, 3D: 0 CUDA cores, 1 TF32 tcgen05), and
+// the measured time of every option tried (ms of that degree's sub-batch;
+// index shape + 2 face batch + 4 tensor cores for shapes 0 and 1, 8 + face
+// batch for shape 3; < 0: not tried).
+constexpr int kKnobOptions = 10;
 struct DegreeKnobs {
   int shape = 0, face_batch = 0, tc = 0;
-  float ms[8] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+  float ms[kKnobOptions] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
 };
+
+// The chunk table a tile shape uses (shape 3 runs shape 0's chunks).
+inline int chunking(int shape) { return shape == 1 ? 1 : 0; }
 
 // One launch of the persistent kernel: up to bk::kLaunchProbs problems of
 // the batch (global indices in probs; the work list uses local ones), their

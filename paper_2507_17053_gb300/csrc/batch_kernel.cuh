@@ -50,8 +50,9 @@ struct Item {
 };
 
 // dispatch code of a problem: dimension, degree, tile shape (0: R cells per
-// chunk, 1: R/2), tensor-core faces (0: CUDA cores, 1: TF32 tcgen05), face
-// batch (0: 256/L faces per pass, 1: 128/L), extension
+// chunk, 1: R/2, 3: R cells without staged runs, 3D FP32), tensor-core
+// faces (0: CUDA cores, 1: TF32 tcgen05), face batch (0: 256/L faces per
+// pass, 1: 128/L), extension
 __host__ __device__ constexpr int code_of(int d, int n, int v, int fh, int ext, int tc = 0) {
   return ((d * 10 + n) * 10 + v) * 100 + tc * 10 + fh * 2 + ext;
 }
@@ -142,6 +143,13 @@ __device__ SBM_BK_ITEM void chunk_item(const Prob<T>& P, const KTab<T>& tu, cons
                                         int rhs) {
   chunk_xline_build<T, D, N, R>(bk_smem, *P.kt, threadIdx.x);
   chunk_loop<T, D, N, R, true, kThreads>(P.ca, tu, bk_smem, rhs, it.b, it.e, 1);
+}
+
+// tile shape 3 (3D FP32): the same chunks without staged runs
+template <typename T, int N, int R>
+__device__ SBM_BK_ITEM void direct_item(const Prob<T>& P, const KTab<T>& tu, const Item& it,
+                                         int rhs) {
+  chunk_loop_direct<T, N, R, true>(P.ca, tu, *P.kt, bk_smem, rhs, it.b, it.e, 1);
 }
 
 template <typename T>
@@ -366,7 +374,13 @@ __device__ __forceinline__ bool run_dn(const Prob<T>& P, const KTab<T>& tu, cons
     else if (fh) face_item<T, D, N, 0, FHALF>(P, tu, it, rhs);
     else face_item<T, D, N, 0, FF>(P, tu, it, rhs);
   } else {
-    if (v) chunk_item<T, D, N, RH>(P, tu, it, rhs);
+    if constexpr (D == 3 && std::is_same<T, float>::value) {
+      if (v == 3) {
+        direct_item<T, N, R>(P, tu, it, rhs);
+        return true;
+      }
+    }
+    if (v == 1) chunk_item<T, D, N, RH>(P, tu, it, rhs);
     else chunk_item<T, D, N, R>(P, tu, it, rhs);
   }
   return true;
@@ -380,7 +394,10 @@ size_t smem_dn(int v, int fh, int ext, int tc) {
   constexpr int RH = (R / 2) > 0 ? R / 2 : 1;
   constexpr int FF = kThreads / L;
   constexpr int FHALF = (FF / 2) > 0 ? FF / 2 : 1;
-  const size_t c = v ? ChunkSmem<T, D, N, RH>::bytes : ChunkSmem<T, D, N, R>::bytes;
+  size_t c = v == 1 ? ChunkSmem<T, D, N, RH>::bytes : ChunkSmem<T, D, N, R>::bytes;
+  if constexpr (D == 3) {
+    if (v == 3) c = DirectSmem<T, N, R>::bytes;
+  }
   const size_t f = ext ? face_group_smem<T, D, N, 1, FF>()
                        : (fh ? face_group_smem<T, D, N, 0, FHALF>()
                              : face_group_smem<T, D, N, 0, FF>());

@@ -54,6 +54,40 @@ def test_batch_equals_single_applies(dtype):
         assert float((y - y2).abs().max() / y.abs().max()) <= tol
 
 
+def test_batch_tile_shape_3_equals_single_applies():
+    """FP32 batches of 3D problems run tile shape 3 (the chunks without
+    staged runs) when pinned: bitwise the single FP32 applies (any of tile
+    shapes 0, 2, 3).  FP64 batches and degrees with a 2D problem reject it."""
+    ws = S.batched_ellipsoids(nprob=6, n_range=(6, 12), p_range=(2, 6))
+    ps = [G.Problem.from_workload(w) for w in ws]
+    nrhs = 2
+    B = G.Batch(ps, nrhs, autotune=False)
+    for deg in sorted({w.degree for w in ws}):
+        B.set_knobs(32, deg, 3, 0, 0)
+        with pytest.raises(G.SbmError) as e:
+            B.set_knobs(64, deg, 3, 0, 0)
+        assert G.STATUS[e.value.status] == "SBM_ERR_UNSUPPORTED"
+    xs = [torch.from_numpy(np.concatenate([S.random_vector(w.seed + r, p.n_dofs, "uniform")
+                                           for r in range(nrhs)])).to("cuda", torch.float32)
+          for w, p in zip(ws, ps)]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    for _ in range(2):
+        B.apply(xs, ys)
+        B.device_status()
+        for p, x, y in zip(ps, xs, ys):
+            for r in range(nrhs):
+                xr = x[r * p.n_dofs:(r + 1) * p.n_dofs].contiguous()
+                assert torch.equal(y[r * p.n_dofs:(r + 1) * p.n_dofs], p.apply_f32(xr))
+    B.close()
+    mixed = [G.Problem.from_workload(S.DISK_2D_Q2.resized(12, degree=3)),
+             G.Problem.from_workload(S.SPHERE_3D_Q4.resized(6, degree=3))]
+    B2 = G.Batch(mixed, 1, autotune=False)
+    with pytest.raises(G.SbmError) as e:
+        B2.set_knobs(32, 3, 3, 0, 0)
+    assert G.STATUS[e.value.status] == "SBM_ERR_UNSUPPORTED"
+    B2.close()
+
+
 def test_batch_rejects_dg_and_bad_sizes():
     dg = G.Problem.from_workload(S.TORUS_3D_DG_Q3.resized(8))
     with pytest.raises(G.SbmError) as e:
@@ -156,10 +190,17 @@ def test_batch_8rhs_matches_oracle_elementwise():
     for prec in (32, 64):
         for deg in sorted({w.degree for w in ws}):
             k = B.knobs(prec, deg)
-            assert k["tile_shape"] in (0, 1) and k["face_batch"] in (0, 1)
-            timed = [m for m in k["ms"][:4] if m is not None]
-            assert len(timed) == 4 and all(m > 0 for m in timed)
-            best = k["tile_shape"] + 2 * k["face_batch"]
+            # tile shape 3 (options 8, 9): FP32, degrees whose problems are all 3D
+            direct = prec == 32 and all(w.dim == 3 for w in ws if w.degree == deg)
+            shapes = (0, 1, 3) if direct else (0, 1)
+            assert k["tile_shape"] in shapes and k["face_batch"] in (0, 1)
+            opts = list(range(4)) + ([8, 9] if direct else [])
+            timed = [k["ms"][i] for i in opts]
+            assert all(m is not None and m > 0 for m in timed)
+            if not direct:
+                assert k["ms"][8] is None and k["ms"][9] is None
+            best = (8 + k["face_batch"] if k["tile_shape"] == 3
+                    else k["tile_shape"] + 2 * k["face_batch"])
             assert k["ms"][best] == min(timed)
     with pytest.raises(G.SbmError):
         B.knobs(64, 9)
