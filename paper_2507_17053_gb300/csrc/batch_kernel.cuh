@@ -156,9 +156,9 @@ template <typename T>
 __device__ SBM_BK_ITEM void asm_item(const Prob<T>& P, const Item& it, int rhs) {
   const T* ycol = P.ca.ycol + rhs * P.ld_asm_ycol;
   T* y = P.ca.y + rhs * P.ca.ldx;
-  for (int64_t t0 = it.b; t0 < it.e; t0 += kThreads)
-    assemble_warp<T, true>(ycol, P.multi, P.mask, y, P.ca.n_dofs, it.e, P.ncol,
-                           t0 + threadIdx.x);
+  for (int64_t t0 = it.b; t0 < it.e; t0 += 2 * kThreads)
+    assemble_pair<T, true>(ycol, P.multi, P.mask, y, P.ca.n_dofs, it.e, P.ncol,
+                           t0 + threadIdx.x, kThreads);
 }
 
 // ---- tensor-core face items (FP32 applies, 3D) ---------------------------------

@@ -141,62 +141,16 @@ __global__ void assemble_kernel(const T* __restrict__ ycol, const int32_t* __res
                           nmulti, ncol, t);
 }
 
-// Single right-hand side: kAsmE shared DoFs per thread (entries b + tid +
-// 256 e of a 256 kAsmE entry tile), all colour values of all of them loaded
-// before any is summed, the loads unrolled to the warp's largest colour
-// count K (the list is grouped by count).  The sums are assemble_warp's: in
-// colour order, FP32 over the lane's own colours, FP64 over the warp's
-// largest count (zeros past the lane's own), so the result is bitwise the
-// same.  Two per thread, FP32: Q4 sphere 41 -> 37.5 us, p = 3 20.6 -> 16.7
-// us (one: 41 / 20.8; four: 41 / 20.6 us).
-constexpr int kAsmE = 2;
-
-template <typename T, int K>
-__device__ __forceinline__ void assemble_set(const T* __restrict__ ycol,
-                                             const int64_t (&i)[kAsmE], unsigned (&m)[kAsmE],
-                                             const int64_t (&t)[kAsmE], unsigned kmax,
-                                             T* __restrict__ y, int64_t n, int64_t nmulti) {
-  T v[kAsmE][K];
-  unsigned cnt[kAsmE];
-#pragma unroll
-  for (int e = 0; e < kAsmE; ++e) {
-    cnt[e] = std::is_same<T, float>::value ? __popc(m[e]) : kmax;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      v[e][j] = m[e] ? __ldcs(ycol + (size_t)(__ffs(m[e]) - 1) * n + i[e]) : T(0);
-      m[e] &= m[e] - 1u;
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < kAsmE; ++e) {
-    T acc = v[e][0];
-#pragma unroll
-    for (int j = 1; j < K; ++j)
-      if ((unsigned)j < cnt[e]) acc += v[e][j];
-    if (t[e] < nmulti) __stcs(y + i[e], acc);
-  }
-}
-
+// Single right-hand side: two shared DoFs per thread (entries b + tid and
+// b + 256 + tid of a 512-entry tile; assemble_pair).  FP32: Q4 sphere 41 ->
+// 37.5 us, p = 3 20.6 -> 16.7 us against one per thread (four: 41 / 20.6).
 template <typename T>
 __global__ void __launch_bounds__(256)
 assemble_set_kernel(const T* __restrict__ ycol, const int32_t* __restrict__ multi,
                     const uint8_t* __restrict__ multi_mask, T* __restrict__ y, int64_t n,
                     int64_t nmulti, int ncol) {
-  const int64_t b = blockIdx.x * (256ll * kAsmE) + threadIdx.x;
-  int64_t t[kAsmE], i[kAsmE];
-  unsigned m[kAsmE], kmax = 0u;
-#pragma unroll
-  for (int e = 0; e < kAsmE; ++e) {
-    t[e] = b + 256 * e;
-    i[e] = t[e] < nmulti ? __ldg(multi + t[e]) : 0;
-    m[e] = t[e] < nmulti ? (unsigned)__ldg(multi_mask + t[e]) : 0u;
-    if (ncol < 8) m[e] &= (1u << ncol) - 1u;
-    kmax = max(kmax, (unsigned)__popc(m[e]));
-  }
-  kmax = __reduce_max_sync(0xffffffffu, kmax);
-  if (kmax <= 2) assemble_set<T, 2>(ycol, i, m, t, kmax, y, n, nmulti);
-  else if (kmax <= 4) assemble_set<T, 4>(ycol, i, m, t, kmax, y, n, nmulti);
-  else assemble_set<T, 8>(ycol, i, m, t, kmax, y, n, nmulti);
+  assemble_pair<T, false>(ycol, multi, multi_mask, y, n, nmulti, ncol,
+                          blockIdx.x * 512ll + threadIdx.x, 256);
 }
 
 // Blocks of the chunk kernel: 4 x (resident blocks per SM) x SMs at most
@@ -317,7 +271,7 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   const int64_t n = hp.n_dofs, nm = ord ? 0 : part.m1 - part.m0;
   if (nm > 0 && nrhs == 1) {
-    assemble_set_kernel<T><<<(unsigned)((nm + 256 * kAsmE - 1) / (256 * kAsmE)), 256, 0, st>>>(
+    assemble_set_kernel<T><<<(unsigned)((nm + 511) / 512), 256, 0, st>>>(
         ycol, ct.multi + part.m0, ct.multi_mask + part.m0, y, n, nm, dd.ncolours);
     nlaunch++;
   } else if (nm > 0) {

@@ -607,6 +607,61 @@ __device__ __forceinline__ void assemble_warp(const T* __restrict__ ycol,
   if (t < nmulti) __stcs(y + i, acc);
 }
 
+// Two shared DoFs per thread, entries t0 and t0 + stride: all colour values
+// of both loaded before either is summed, the loads unrolled to the warp's
+// largest colour count K (the list is grouped by count).  The sums are
+// assemble_warp's -- in colour order, FP32 over the lane's own colours,
+// FP64 over the warp's largest count (zeros past the lane's own) -- so the
+// results are bitwise the same.  All 32 lanes of the warp call this.
+template <typename T, bool COH, int K>
+__device__ __forceinline__ void assemble_pair_k(const T* __restrict__ ycol,
+                                                const int64_t (&i)[2], unsigned (&m)[2],
+                                                const int64_t (&t)[2], unsigned kmax,
+                                                T* __restrict__ y, int64_t n, int64_t nmulti) {
+  T v[2][K];
+  unsigned cnt[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    cnt[e] = std::is_same<T, float>::value ? __popc(m[e]) : kmax;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const T* p = ycol + (size_t)(__ffs(m[e]) - 1) * n + i[e];
+      v[e][j] = m[e] ? (COH ? __ldcg(p) : __ldcs(p)) : T(0);
+      m[e] &= m[e] - 1u;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    T acc = v[e][0];
+#pragma unroll
+    for (int j = 1; j < K; ++j)
+      if ((unsigned)j < cnt[e]) acc += v[e][j];
+    if (t[e] < nmulti) __stcs(y + i[e], acc);
+  }
+}
+
+template <typename T, bool COH>
+__device__ __forceinline__ void assemble_pair(const T* __restrict__ ycol,
+                                              const int32_t* __restrict__ multi,
+                                              const uint8_t* __restrict__ multi_mask,
+                                              T* __restrict__ y, int64_t n, int64_t nmulti,
+                                              int ncol, int64_t t0, int stride) {
+  const int64_t t[2] = {t0, t0 + stride};
+  int64_t i[2];
+  unsigned m[2], kmax = 0u;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    i[e] = t[e] < nmulti ? __ldg(multi + t[e]) : 0;
+    m[e] = t[e] < nmulti ? (unsigned)__ldg(multi_mask + t[e]) : 0u;
+    if (ncol < 8) m[e] &= (1u << ncol) - 1u;
+    kmax = max(kmax, (unsigned)__popc(m[e]));
+  }
+  kmax = __reduce_max_sync(0xffffffffu, kmax);
+  if (kmax <= 2) assemble_pair_k<T, COH, 2>(ycol, i, m, t, kmax, y, n, nmulti);
+  else if (kmax <= 4) assemble_pair_k<T, COH, 4>(ycol, i, m, t, kmax, y, n, nmulti);
+  else assemble_pair_k<T, COH, 8>(ycol, i, m, t, kmax, y, n, nmulti);
+}
+
 
 // ---- tile shape 3: the chunk loop without staged runs (3D) ------------------------
 //
