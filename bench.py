@@ -629,6 +629,8 @@ def batched(G, torch, steps=10):
     right-hand sides each, one CUDA-graph launch per batched apply."""
     ws = S.batched_ellipsoids()
     ps = [G.Problem.from_workload(w) for w in ws]
+    for P in ps:
+        G.sbm_autotune(P.handle)
     nrhs = 8
     # the autotuner may choose tensor-core (TF32) faces for the FP32 applies
     # per degree; it keeps the fastest option and records every timing
@@ -653,7 +655,29 @@ def batched(G, torch, steps=10):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         res[name] = {"gdofs": tot / ms / 1e6, "ms": ms}
-        del xs, ys
+        # the same systems through the single-problem entry point, one
+        # problem and right-hand side after another (each problem with its
+        # autotuned tile shape and store mode): what the batch replaces
+        apply1 = (lambda P, a, b: P.apply_f32(a, b)) if dt == torch.float32 else \
+            (lambda P, a, b: P.apply_f64(a, b))
+        views = [[(x[r * P.n_dofs:(r + 1) * P.n_dofs], y[r * P.n_dofs:(r + 1) * P.n_dofs])
+                  for r in range(nrhs)] for P, x, y in zip(ps, xs, ys)]
+        for P, vs in zip(ps, views):
+            apply1(P, *vs[0])
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(2):
+            for P, vs in zip(ps, views):
+                for a, b in vs:
+                    apply1(P, a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1) / 2
+        res[name]["single_applies"] = {"gdofs": tot / ms1 / 1e6, "ms": ms1,
+                                       "launches": "one apply per problem and right-hand "
+                                                   "side, issued from Python through the "
+                                                   "binding (host overhead included)"}
+        del xs, ys, views
     B.device_status()
     res["knobs_by_degree"] = {
         str(prec): {str(deg): B.knobs(prec, deg) for deg in sorted({w.degree for w in ws})}
