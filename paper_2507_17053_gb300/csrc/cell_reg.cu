@@ -172,7 +172,7 @@ __device__ __forceinline__ void fold_reg(const KTab<T>& t, const T* __restrict__
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       if (K == 2) {
-        const T vv = __ldg(rv + a + N * b), g = __ldg(rg + a + N * b);
+        const T vv = __ldcg(rv + a + N * b), g = __ldcg(rg + a + N * b);
 #pragma unroll
         for (int m = 0; m < N; ++m) {
           T& o = u[a + N * b + L * m];
@@ -184,8 +184,8 @@ __device__ __forceinline__ void fold_reg(const KTab<T>& t, const T* __restrict__
         const T dk = SD ? t.D1[jk] : t.D0[jk];
 #pragma unroll
         for (int m = 0; m < N; ++m) {
-          T add = mul_rn(dk, __ldg(rg + jo + N * m));
-          if (jk == KEND) add = add_rn(add, __ldg(rv + jo + N * m));
+          T add = mul_rn(dk, __ldcg(rg + jo + N * m));
+          if (jk == KEND) add = add_rn(add, __ldcg(rv + jo + N * m));
           u[a + N * b + L * m] = add_rn(u[a + N * b + L * m], add);
         }
       }
@@ -206,6 +206,7 @@ cg_cell_reg_kernel(const RegArgs<T> a, const __grid_constant__ KTab<T> t,
   T u[ND];
   int c = 0, nc = 0, ch = 0;
   const int32_t* ln = a.lines + (size_t)(act ? pos : 0) * L;
+  pdl_trigger();
   if (act) {
     ch = __ldg(a.cell_chunk + pos);
     const int f = __ldg(a.chunk_first + ch);
@@ -218,6 +219,7 @@ cg_cell_reg_kernel(const RegArgs<T> a, const __grid_constant__ KTab<T> t,
       for (int j0 = 0; j0 < N; ++j0) u[j0 + N * l] = __ldg(xl + j0);
     }
     cell_phases<T, N>(t, xo, u);
+    pdl_wait();                      // the face kernel's results
     const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);
     for (int f2 = fs; f2 < fe; ++f2) {
       const int kind = __ldg(a.face_kind + f2);
@@ -289,7 +291,7 @@ __global__ void k_reg_mask(const int32_t* __restrict__ cell_chunk,
 
 template <typename T, int N>
 cudaError_t launch_reg(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                       const T* fo, T* ycol, cudaStream_t st) {
+                       const T* fo, T* ycol, cudaStream_t st, bool pdl) {
   RegArgs<T> a;
   a.x = x;
   a.y = y;
@@ -306,8 +308,9 @@ cudaError_t launch_reg(const HostProblem& hp, const DeviceData& dd, const T* x, 
   a.n_dofs = hp.n_dofs;
   const KTab<T> t = make_ktab<T>(hp);
   const XOps<T, N> xo = make_xops<T, N>(t);
-  cg_cell_reg_kernel<T, N><<<dd.reg_nblocks, kRegThreads, 0, st>>>(a, t, xo);
-  return cudaGetLastError();
+  cudaError_t e = launch_maybe_pdl(cg_cell_reg_kernel<T, N>, dim3(dd.reg_nblocks),
+                                   dim3(kRegThreads), 0, st, pdl, a, t, xo);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -360,23 +363,25 @@ cudaError_t build_cell_reg_tables(const HostProblem& hp, const std::vector<int32
 
 template <typename T>
 cudaError_t launch_cell_reg(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            const T* fo, T* ycol, cudaStream_t st) {
+                            const T* fo, T* ycol, cudaStream_t st, bool pdl) {
   if (!cell_reg_available(hp, std::is_same<T, float>::value) || !dd.reg_mask)
     return cudaErrorInvalidValue;
   switch (hp.n) {
-    case 2: return launch_reg<T, 2>(hp, dd, x, y, fo, ycol, st);
-    case 3: return launch_reg<T, 3>(hp, dd, x, y, fo, ycol, st);
-    case 4: return launch_reg<T, 4>(hp, dd, x, y, fo, ycol, st);
+    case 2: return launch_reg<T, 2>(hp, dd, x, y, fo, ycol, st, pdl);
+    case 3: return launch_reg<T, 3>(hp, dd, x, y, fo, ycol, st, pdl);
+    case 4: return launch_reg<T, 4>(hp, dd, x, y, fo, ycol, st, pdl);
     case 5:
       if constexpr (std::is_same<T, float>::value)
-        return launch_reg<T, 5>(hp, dd, x, y, fo, ycol, st);
+        return launch_reg<T, 5>(hp, dd, x, y, fo, ycol, st, pdl);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
 template cudaError_t launch_cell_reg<double>(const HostProblem&, const DeviceData&, const double*,
-                                             double*, const double*, double*, cudaStream_t);
+                                             double*, const double*, double*, cudaStream_t,
+                                             bool);
 template cudaError_t launch_cell_reg<float>(const HostProblem&, const DeviceData&, const float*,
-                                            float*, const float*, float*, cudaStream_t);
+                                            float*, const float*, float*, cudaStream_t,
+                                            bool);
 
 }  // namespace sbm

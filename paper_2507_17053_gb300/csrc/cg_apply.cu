@@ -48,9 +48,10 @@ template <typename T, int D, int N, int R>
 __global__ void __launch_bounds__(R * Shape<D, N>::L)
 cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_trigger();
   chunk_xline_build<T, D, N, R>(smem_raw, t, threadIdx.x);
-  chunk_loop<T, D, N, R, false, R * Shape<D, N>::L>(a, t, smem_raw, blockIdx.y,
-                                                     a.q0 + blockIdx.x, a.q1, gridDim.x);
+  chunk_loop<T, D, N, R, true, R * Shape<D, N>::L, true>(a, t, smem_raw, blockIdx.y,
+                                                         a.q0 + blockIdx.x, a.q1, gridDim.x);
 }
 
 // The same chunks with colour-ordered stores (chunk_loop, ORD): a
@@ -76,8 +77,9 @@ template <typename T, int N, int R>
 __global__ void __launch_bounds__(R * N * N, (direct_min_blocks<T, N>()))
 cg_direct_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  chunk_loop_direct<T, N, R, false>(a, t, t, smem_raw, blockIdx.y, a.q0 + blockIdx.x, a.q1,
-                                    gridDim.x);
+  pdl_trigger();
+  chunk_loop_direct<T, N, R, true, false, true>(a, t, t, smem_raw, blockIdx.y,
+                                                a.q0 + blockIdx.x, a.q1, gridDim.x);
 }
 
 template <typename T, int N, int R>
@@ -149,8 +151,8 @@ __global__ void __launch_bounds__(256)
 assemble_set_kernel(const T* __restrict__ ycol, const int32_t* __restrict__ multi,
                     const uint8_t* __restrict__ multi_mask, T* __restrict__ y, int64_t n,
                     int64_t nmulti, int ncol) {
-  assemble_pair<T, false>(ycol, multi, multi_mask, y, n, nmulti, ncol,
-                          blockIdx.x * 512ll + threadIdx.x, 256);
+  assemble_pair<T, false, true>(ycol, multi, multi_mask, y, n, nmulti, ncol,
+                                blockIdx.x * 512ll + threadIdx.x, 256);
 }
 
 // Blocks of the chunk kernel: 4 x (resident blocks per SM) x SMs at most
@@ -191,7 +193,7 @@ template <typename T, int D, int N, int R>
 static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const ChunkTable& ct,
                            const T* x, T* y, int64_t ld, int nrhs, T* fo, T* ycol, int face_mode,
                            cudaStream_t st, Profiler* prof, Part part, bool reg,
-                           bool direct, bool ord) {
+                           bool direct, bool ord, bool allow_pdl) {
   constexpr int L = Shape<D, N>::L;
   const KTab<T> t = make_ktab<T>(hp);
   constexpr size_t smem = ChunkSmem<T, D, N, R>::bytes;
@@ -202,11 +204,21 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   const bool pr = prof && prof->on;
   int nlaunch = 0;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
+  // programmatic dependent launches (FP32 whole applies, no profiling marks
+  // between the kernels): the cell kernel after the CUDA-core face kernel
+  // (which x's producers precede in the stream), the assembly after the cell
+  // kernel.  Measured (unprofiled applies, GB300): FP32 p = 3 sphere 68.7 ->
+  // 65.2 us, p = 6 ellipsoid (shape 3) 62.7 -> 57.4 us, p = 4 sphere within
+  // 1 %; the FP64 p = 4 sphere 2.3 % slower (1.026 -> 1.049 ms), so FP64
+  // launches without it.
+  allow_pdl = allow_pdl && std::is_same<T, float>::value;
+  bool pdl_cell = false;
   if (part.f1 > part.f0) {
     err = face_mode != 0 ? launch_faces<T>(hp, dd, x, fo, face_mode, st)
                          : launch_face_kernel<T>(hp, dd, x, fo, st, part.f0, part.f1);
     if (err != cudaSuccess) return err;
     nlaunch++;
+    pdl_cell = allow_pdl && !pr && face_mode == 0;
   }
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   int cap = 0;
@@ -231,8 +243,10 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   a.ld_face = (int64_t)dd.nface * 2 * L;
   OrdArgs oa{ct.ord, ct.add_bits, ct.deps, ct.ndeps, ct.done, ct.tickets, dd.err_flag, ct.n,
              ct.dep_cap};
+  const int nl0 = nlaunch;
   if (reg) {                 // tile shape 2: one thread per cell (cell_reg.cu)
-    if ((err = launch_cell_reg<T>(hp, dd, x, y, fo, ycol, st)) != cudaSuccess) return err;
+    if ((err = launch_cell_reg<T>(hp, dd, x, y, fo, ycol, st, pdl_cell)) != cudaSuccess)
+      return err;
     nlaunch++;
   } else if (ord && part.q1 > part.q0) {      // colour-ordered stores, no assembly
     if constexpr (R == ChunkShape<D, N>::R) {
@@ -243,15 +257,19 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
           if ((err = resident_grid(cg_direct_ord_kernel<T, N, R>, R * L,
                                    DirectSmem<T, N, R>::bytes, &cache, &grid)) != cudaSuccess)
             return err;
-          cg_direct_ord_kernel<T, N, R><<<std::min(grid, ct.n), R * L,
-                                          DirectSmem<T, N, R>::bytes, st>>>(a, t, oa);
+          if ((err = launch_maybe_pdl(cg_direct_ord_kernel<T, N, R>, dim3(std::min(grid, ct.n)),
+                                      dim3(R * L), DirectSmem<T, N, R>::bytes, st, pdl_cell, a,
+                                      t, oa)) != cudaSuccess)
+            return err;
         }
       } else {
         static int cache0 = 0;
         if ((err = resident_grid(cg_chunk_ord_kernel<T, D, N, R>, R * L, smem, &cache0, &grid)) !=
             cudaSuccess)
           return err;
-        cg_chunk_ord_kernel<T, D, N, R><<<std::min(grid, ct.n), R * L, smem, st>>>(a, t, oa);
+        if ((err = launch_maybe_pdl(cg_chunk_ord_kernel<T, D, N, R>, dim3(std::min(grid, ct.n)),
+                                    dim3(R * L), smem, st, pdl_cell, a, t, oa)) != cudaSuccess)
+          return err;
       }
       nlaunch++;
     }
@@ -260,19 +278,29 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
       int dcap = 0;
       if ((err = direct_prepare<T, N, R>(&dcap)) != cudaSuccess) return err;
       const int grid = std::min(part.q1 - part.q0, dcap);
-      cg_direct_kernel<T, N, R><<<dim3(grid, nrhs), R * L, DirectSmem<T, N, R>::bytes, st>>>(a, t);
+      if ((err = launch_maybe_pdl(cg_direct_kernel<T, N, R>, dim3(grid, nrhs), dim3(R * L),
+                                  DirectSmem<T, N, R>::bytes, st, pdl_cell, a, t)) !=
+          cudaSuccess)
+        return err;
       nlaunch++;
     }
   } else if (part.q1 > part.q0) {
     const int grid = std::min(part.q1 - part.q0, cap);
-    cg_chunk_kernel<T, D, N, R><<<dim3(grid, nrhs), R * L, smem, st>>>(a, t);
+    if ((err = launch_maybe_pdl(cg_chunk_kernel<T, D, N, R>, dim3(grid, nrhs), dim3(R * L), smem,
+                                st, pdl_cell, a, t)) != cudaSuccess)
+      return err;
     nlaunch++;
   }
+  const bool pdl_asm = allow_pdl && !pr && nlaunch > nl0;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   const int64_t n = hp.n_dofs, nm = ord ? 0 : part.m1 - part.m0;
   if (nm > 0 && nrhs == 1) {
-    assemble_set_kernel<T><<<(unsigned)((nm + 511) / 512), 256, 0, st>>>(
-        ycol, ct.multi + part.m0, ct.multi_mask + part.m0, y, n, nm, dd.ncolours);
+    if ((err = launch_maybe_pdl(assemble_set_kernel<T>, dim3((unsigned)((nm + 511) / 512)),
+                                dim3(256), 0, st, pdl_asm, (const T*)ycol,
+                                (const int32_t*)(ct.multi + part.m0),
+                                (const uint8_t*)(ct.multi_mask + part.m0), y, n, nm,
+                                dd.ncolours)) != cudaSuccess)
+      return err;
     nlaunch++;
   } else if (nm > 0) {
     assemble_kernel<T><<<dim3((unsigned)((nm + 255) / 256), nrhs), 256, 0, st>>>(
@@ -320,9 +348,9 @@ static cudaError_t apply_t(const HostProblem& hp, const DeviceData& dd, const T*
   }
   if (v == 1)
     return apply_r<T, D, N, RH>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part,
-                                false, false, false);
+                                false, false, false, slab < 0);
   return apply_r<T, D, N, R>(hp, dd, ct, x, y, ld, nrhs, fo, ycol, face_mode, st, prof, part,
-                             reg, direct, ord);
+                             reg, direct, ord, slab < 0);
 }
 
 template <typename T>

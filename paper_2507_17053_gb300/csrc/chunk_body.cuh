@@ -301,7 +301,7 @@ __device__ __forceinline__ void chunk_xline_build(unsigned char* smem_raw, const
 // derivatives; 2D: the 1D mass and stiffness, h^(d-2) = 1); the x-line
 // operators are already in shared memory (chunk_xline_build).  The next
 // chunk's runs are copied in (cp.async) while the current one is computed.
-template <typename T, int D, int N, int R, bool COH, int NTHR>
+template <typename T, int D, int N, int R, bool COH, int NTHR, bool PDL = false>
 __device__ __forceinline__ void chunk_loop(const ChunkArgs<T>& a, const KTab<T>& t,
                                            unsigned char* smem_raw, int rhs, int ch, int q1,
                                            int step) {
@@ -338,6 +338,9 @@ __device__ __forceinline__ void chunk_loop(const ChunkArgs<T>& a, const KTab<T>&
     gather_runs_async<T, L, SM>(xr, Lbuf, Xbuf, S, tid, nthr);
   }
   cp_async_commit();
+  // PDL: the first chunk's runs are in flight; the face kernel's results
+  // are read from here on
+  if (PDL) pdl_wait();
   for (; ch < q1; ch += step, buf ^= 1) {
     T* Xs = Xbuf + buf * CS::XS;              // this chunk's runs
     const int* Ls = Lbuf + buf * L;
@@ -490,17 +493,18 @@ __device__ __forceinline__ void chunk_loop_ord(const ChunkArgs<T>& a, const KTab
                        out);
     else
       cell_sweeps_2d<T, N>(t, Xs, P * c + tl, SM, AE, c, tl, act, out);
+    pdl_wait();                               // the face kernel's results
     if (act) {
       const int pos = first + c;
       const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);
       for (int f = fs; f < fe; ++f) {
         const int kind = __ldg(a.face_kind + f);
         if constexpr (D == 3)
-          fold_face_z<T, N, false>(t, a.face_out + (size_t)f * 2 * L, kind & 3, kind >> 2,
-                                   tl % N, tl / N, out);
+          fold_face_z<T, N, true>(t, a.face_out + (size_t)f * 2 * L, kind & 3, kind >> 2,
+                                  tl % N, tl / N, out);
         else
-          fold_face<T, D, N, false>(t, a.face_out + (size_t)f * 2 * L, kind & 3, kind >> 2, tl,
-                                    out);
+          fold_face<T, D, N, true>(t, a.face_out + (size_t)f * 2 * L, kind & 3, kind >> 2, tl,
+                                   out);
       }
 #pragma unroll
       for (int m = 0; m < N; ++m) {
@@ -640,7 +644,7 @@ __device__ __forceinline__ void assemble_pair_k(const T* __restrict__ ycol,
   }
 }
 
-template <typename T, bool COH>
+template <typename T, bool COH, bool PDL = false>
 __device__ __forceinline__ void assemble_pair(const T* __restrict__ ycol,
                                               const int32_t* __restrict__ multi,
                                               const uint8_t* __restrict__ multi_mask,
@@ -657,6 +661,7 @@ __device__ __forceinline__ void assemble_pair(const T* __restrict__ ycol,
     kmax = max(kmax, (unsigned)__popc(m[e]));
   }
   kmax = __reduce_max_sync(0xffffffffu, kmax);
+  if (PDL) pdl_wait();                        // the cell kernel's colour buffers
   if (kmax <= 2) assemble_pair_k<T, COH, 2>(ycol, i, m, t, kmax, y, n, nmulti);
   else if (kmax <= 4) assemble_pair_k<T, COH, 4>(ycol, i, m, t, kmax, y, n, nmulti);
   else assemble_pair_k<T, COH, 8>(ycol, i, m, t, kmax, y, n, nmulti);
@@ -684,7 +689,7 @@ struct DirectSmem {
   static constexpr size_t bytes = (size_t)(TILE + XL + XF) * sizeof(T) + (size_t)(L + WORDS) * 4;
 };
 
-template <typename T, int N, int R, bool COH, bool ORD = false>
+template <typename T, int N, int R, bool COH, bool ORD = false, bool PDL = false>
 __device__ __forceinline__ void chunk_loop_direct(const ChunkArgs<T>& a, const KTab<T>& t,
                                                   const KTab<T>& tx, unsigned char* smem_raw,
                                                   int rhs, int ch, int q1, int step,
@@ -737,6 +742,7 @@ __device__ __forceinline__ void chunk_loop_direct(const ChunkArgs<T>& a, const K
     cell_fd_3d_l<T, N>(
         t, [&](int j) { return __ldg(xr + Ls[j1 + N * j] + P * c + j0); }, tile, c, tl, act, xop,
         out);
+    if (PDL) pdl_wait();                      // the face kernel's results
     if (act) {
       const int pos = first + c;
       const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);

@@ -213,6 +213,26 @@ template <typename T> inline T* face_out_of(const DeviceData& dd);
 template <> inline double* face_out_of<double>(const DeviceData& dd) { return dd.face_out; }
 template <> inline float* face_out_of<float>(const DeviceData& dd) { return dd.face_out32; }
 
+// Launch kern<<<grid, block, smem, st>>>(args...), with programmatic
+// stream serialization when pdl (the kernel may start before the previous
+// kernel of the stream completes; it waits with griddepcontrol.wait before
+// it reads that kernel's results).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Tile shape 2: the cell term with one thread per cell and the tile in
 // registers (cell_reg.cu); available for 3D CG problems with n <= 5 (FP32)
 // or n <= 4 (FP64); bitwise equal to tile shape 0.
@@ -221,7 +241,7 @@ cudaError_t build_cell_reg_tables(const HostProblem& hp, const std::vector<int32
                                   DeviceData* dd);
 template <typename T>
 cudaError_t launch_cell_reg(const HostProblem& hp, const DeviceData& dd, const T* x, T* y,
-                            const T* fo, T* ycol, cudaStream_t st);
+                            const T* fo, T* ycol, cudaStream_t st, bool pdl = false);
 
 // The surrogate faces [fb, fe) of the kernel face order (all: 0, -1) into
 // the per-face scratch (face_kernel.cu).

@@ -16,6 +16,19 @@
 
 namespace sbm {
 
+// Programmatic dependent launch (the single applies: face kernel -> cell
+// kernel -> assembly).  A kernel lets the next one in the stream start once
+// all of its blocks run (pdl_trigger); the next one does its independent work
+// (the gather, the cell term) and waits for the previous grid's completion
+// and memory (pdl_wait) only before it reads that grid's results (it reads
+// them with coherent loads, not the read-only path).  Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+
 template <int D, int N>
 struct Shape {
   static constexpr int L = (D == 3) ? N * N : N;   // lines per cell, points per face
