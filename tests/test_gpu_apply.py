@@ -136,6 +136,26 @@ def test_full_size_sampled_rows(w):
     assert np.abs(y[rows] - ref).max() <= TOL * scale
 
 
+@pytest.mark.parametrize("w", [S.SPHERE_3D_Q4, S.ELLIPSOID_3D_Q6], ids=lambda w: w.name)
+def test_full_size_sampled_rows_autotuned(w):
+    """Full-size workload in the benchmark's launch configuration (the
+    autotuner's tile shape and store mode per precision): FP64 and FP32
+    applies on 10^4 random rows plus every row of 200 sampled surrogate-face
+    cells against the oracle."""
+    O, P = _pair(w)
+    shapes = G.sbm_autotune(P.handle)
+    x = S.random_vector(w.seed, O.n_dofs, w.dist)
+    xd = torch.from_numpy(x).cuda()
+    rows = _sample_rows(O, np.random.default_rng(1))
+    y = P.apply_f64(xd).cpu().numpy()
+    ref = O.apply_rows(x, rows)
+    assert np.abs(y[rows] - ref).max() <= TOL * np.abs(ref).max(), shapes
+    x32 = x.astype(np.float32).astype(np.float64)
+    y32 = P.apply_f32(xd.float()).double().cpu().numpy()
+    ref32 = O.apply_rows(x32, rows)
+    assert np.abs(y32[rows] - ref32).max() <= F32_TOL * np.abs(ref32).max(), shapes
+
+
 @pytest.mark.parametrize("w", [S.SPHERE_3D_Q4.resized(12), S.ELLIPSOID_3D_Q6.resized(9),
                                S.DISK_2D_Q2], ids=lambda w: w.name)
 def test_autotuned_tile_shapes_keep_parity(w):
