@@ -205,12 +205,12 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   int nlaunch = 0;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   // programmatic dependent launches (FP32 whole applies, no profiling marks
-  // between the kernels): the cell kernel after the CUDA-core face kernel
-  // (which x's producers precede in the stream), the assembly after the cell
-  // kernel.  Measured (unprofiled applies, GB300): FP32 p = 3 sphere 68.7 ->
-  // 65.2 us, p = 6 ellipsoid (shape 3) 62.7 -> 57.4 us, p = 4 sphere within
-  // 1 %; the FP64 p = 4 sphere 2.3 % slower (1.026 -> 1.049 ms), so FP64
-  // launches without it.
+  // between the kernels): the chunk kernels (shapes 0, 3) after the
+  // CUDA-core face kernel (which x's producers precede in the stream), the
+  // assembly after the cell kernel.  Measured (unprofiled applies, GB300):
+  // FP32 p = 6 ellipsoid (shape 3) 62.7 -> 57.4 us, p = 3 / 4 spheres
+  // (shapes 0, 3) 1-5 % faster; the FP64 p = 4 sphere 2.3 % slower (1.026 ->
+  // 1.049 ms), so FP64 launches without it.
   allow_pdl = allow_pdl && std::is_same<T, float>::value;
   bool pdl_cell = false;
   if (part.f1 > part.f0) {
