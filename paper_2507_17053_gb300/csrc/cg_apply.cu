@@ -48,9 +48,12 @@ template <typename T, int D, int N, int R>
 __global__ void __launch_bounds__(R * Shape<D, N>::L)
 cg_chunk_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_trigger();
+  // FP32: launched as a programmatic dependent of the face kernel (coherent
+  // face loads, a wait before the first fold); FP64 launches plainly
+  constexpr bool kPdl = std::is_same<T, float>::value;
+  if constexpr (kPdl) pdl_trigger();
   chunk_xline_build<T, D, N, R>(smem_raw, t, threadIdx.x);
-  chunk_loop<T, D, N, R, true, R * Shape<D, N>::L, true>(a, t, smem_raw, blockIdx.y,
+  chunk_loop<T, D, N, R, kPdl, R * Shape<D, N>::L, kPdl>(a, t, smem_raw, blockIdx.y,
                                                          a.q0 + blockIdx.x, a.q1, gridDim.x);
 }
 
@@ -77,8 +80,9 @@ template <typename T, int N, int R>
 __global__ void __launch_bounds__(R * N * N, (direct_min_blocks<T, N>()))
 cg_direct_kernel(const ChunkArgs<T> a, const __grid_constant__ KTab<T> t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_trigger();
-  chunk_loop_direct<T, N, R, true, false, true>(a, t, t, smem_raw, blockIdx.y,
+  constexpr bool kPdl = std::is_same<T, float>::value;     // as cg_chunk_kernel
+  if constexpr (kPdl) pdl_trigger();
+  chunk_loop_direct<T, N, R, kPdl, false, kPdl>(a, t, t, smem_raw, blockIdx.y,
                                                 a.q0 + blockIdx.x, a.q1, gridDim.x);
 }
 
@@ -151,8 +155,9 @@ __global__ void __launch_bounds__(256)
 assemble_set_kernel(const T* __restrict__ ycol, const int32_t* __restrict__ multi,
                     const uint8_t* __restrict__ multi_mask, T* __restrict__ y, int64_t n,
                     int64_t nmulti, int ncol) {
-  assemble_pair<T, false, true>(ycol, multi, multi_mask, y, n, nmulti, ncol,
-                                blockIdx.x * 512ll + threadIdx.x, 256);
+  assemble_pair<T, false, std::is_same<T, float>::value>(ycol, multi, multi_mask, y, n, nmulti,
+                                                         ncol, blockIdx.x * 512ll + threadIdx.x,
+                                                         256);
 }
 
 // Blocks of the chunk kernel: 4 x (resident blocks per SM) x SMs at most

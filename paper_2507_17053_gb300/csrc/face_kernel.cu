@@ -27,7 +27,8 @@ template <typename T, int D, int N, int EXT>
 __global__ void __launch_bounds__(Shape<D, N>::CPB * Shape<D, N>::L)
 sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_trigger();                     // the cell kernel may start (it waits before its folds)
+  // FP32: the cell kernel may start (it waits before its folds)
+  if constexpr (std::is_same<T, float>::value) pdl_trigger();
   face_group<T, D, N, EXT, Shape<D, N>::CPB>(a, t, t, smem_raw,
                                               a.face0 + blockIdx.x * Shape<D, N>::CPB, a.nface,
                                               blockIdx.y);
