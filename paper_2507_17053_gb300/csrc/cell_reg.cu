@@ -29,17 +29,21 @@ namespace sbm {
 
 namespace {
 
-// 64 cells per block (whole chunks), sized for 6 resident blocks per SM:
-// at 168 registers a thread that is the most the register file holds, and
-// the smaller blocks fill it better than 128-cell ones (Q4 FP32 cell term
-// 0.096 -> 0.083 ms)
+// 64 cells per block (whole chunks): the smaller blocks fill the register
+// file better than 128-cell ones (Q4 FP32 cell term 0.096 -> 0.083 ms).
 #ifndef SBM_REG_THREADS
 #define SBM_REG_THREADS 64
 #endif
-#ifndef SBM_REG_MINB
-#define SBM_REG_MINB 6
-#endif
 constexpr int kRegThreads = SBM_REG_THREADS;
+
+// Resident blocks asked of the compiler: FP32 p <= 3, 8 (128 registers, no
+// spills; p = 3 cell term 41.2 -> 37.9 us against 6 blocks at 148
+// registers); p = 4 and FP64, 6 (168 registers; 7 or 8 blocks spill the
+// p = 4 tile: 83 -> 102 us).
+template <typename T, int N>
+constexpr int reg_min_blocks() {
+  return (std::is_same<T, float>::value && N <= 4) ? 8 : 6;
+}
 
 template <int N>
 constexpr int reg_words() {
@@ -193,7 +197,7 @@ __device__ __forceinline__ void fold_reg(const KTab<T>& t, const T* __restrict__
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kRegThreads, SBM_REG_MINB)
+__global__ void __launch_bounds__(kRegThreads, (reg_min_blocks<T, N>()))
 cg_cell_reg_kernel(const RegArgs<T> a, const __grid_constant__ KTab<T> t,
                    const __grid_constant__ XOps<T, N> xo) {
   constexpr int L = N * N, ND = L * N, P = N - 1, W = reg_words<N>();
