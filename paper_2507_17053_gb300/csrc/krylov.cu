@@ -27,6 +27,14 @@ constexpr int CG_CHUNK = 16;
 
 // ---- deterministic reductions ---------------------------------------------
 
+// The BiCGStab chunk's vector and scalar kernels are launched as
+// programmatic dependents of the kernel before them (their launch overlaps
+// its end); each waits for it before touching memory, so the order is that
+// of the stream.  A no-op when a kernel is launched without the attribute.
+__device__ __forceinline__ void pdl_wait_all() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   const int tid = threadIdx.x;
   sh[tid] = v;
@@ -45,6 +53,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 template <typename T>
 __global__ void k_multi_dot(const T* __restrict__ a, int64_t lda, const T* __restrict__ b,
                             int64_t n, double* __restrict__ part) {
+  pdl_wait_all();
   __shared__ double sh[RED_THREADS];
   const T* aj = a + (int64_t)blockIdx.y * lda;
   double s = 0.0;
@@ -599,6 +608,7 @@ __global__ void k_bi_init_fin(const double* __restrict__ part, BiState* st) {
 
 // alpha = rho / (r^, v)
 __global__ void k_bi_alpha(const double* __restrict__ part, BiState* st) {
+  pdl_wait_all();
   __shared__ double sh[RED_THREADS];
   if (st->done) return;
   double s = 0.0;
@@ -614,6 +624,7 @@ __global__ void k_bi_alpha(const double* __restrict__ part, BiState* st) {
 template <typename T>
 __global__ void k_bi_s(const T* __restrict__ r, const T* __restrict__ v, T* __restrict__ s,
                        int64_t n, const BiState* st) {
+  pdl_wait_all();
   if (st->done) return;
   const double al = st->alpha;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -625,6 +636,7 @@ __global__ void k_bi_s(const T* __restrict__ r, const T* __restrict__ v, T* __re
 template <typename T>
 __global__ void k_bi_dot2(const T* __restrict__ t, const T* __restrict__ s, int64_t n,
                           const BiState* st, double* __restrict__ part) {
+  pdl_wait_all();
   __shared__ double sh[RED_THREADS];
   if (st->done) return;
   double sts = 0.0, stt = 0.0;
@@ -644,6 +656,7 @@ __global__ void k_bi_dot2(const T* __restrict__ t, const T* __restrict__ s, int6
 
 // omega = (t, s) / (t, t)  (0 when t = 0: the update then keeps r = s)
 __global__ void k_bi_omega(const double* __restrict__ part, BiState* st) {
+  pdl_wait_all();
   __shared__ double sh[RED_THREADS];
   if (st->done) return;
   double v[2];
@@ -664,6 +677,7 @@ __global__ void k_bi_update(T* __restrict__ x, T* __restrict__ r, const T* __res
                             const T* __restrict__ s, const T* __restrict__ t,
                             const T* __restrict__ rh, int64_t n, const BiState* st,
                             double* __restrict__ part) {
+  pdl_wait_all();
   __shared__ double sh[RED_THREADS];
   if (st->done) return;
   const double al = st->alpha, om = st->omega;
@@ -687,6 +701,7 @@ __global__ void k_bi_update(T* __restrict__ x, T* __restrict__ r, const T* __res
 
 // rho' = (r^, r); convergence / breakdown tests; beta = (rho'/rho)(alpha/omega)
 __global__ void k_bi_beta(const double* __restrict__ part, BiState* st) {
+  pdl_wait_all();
   __shared__ double sh[RED_THREADS];
   if (st->done) return;
   double v[2];
@@ -754,6 +769,7 @@ __global__ void k_bi_replace_fin(const double* __restrict__ part, BiState* st) {
 template <typename T>
 __global__ void k_bi_p(T* __restrict__ p, const T* __restrict__ r, const T* __restrict__ v,
                        int64_t n, const BiState* st) {
+  pdl_wait_all();
   if (st->done) return;
   const double be = st->beta, om = st->omega;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -784,16 +800,33 @@ cudaError_t Bicgstab<T>::setup(const ApplyFn<T>& apply_, int64_t n_, const T* b_
   for (int it = 0; it < BI_CHUNK && ae == cudaSuccess; ++it) {
     ae = apply(p, v, cap);
     if (ae != cudaSuccess) break;
-    k_multi_dot<T><<<dim3(RED_BLOCKS, 1), RED_THREADS, 0, cap>>>(rh, 0, v, n, part);
-    k_bi_alpha<<<1, RED_THREADS, 0, cap>>>(part, dst);
-    k_bi_s<T><<<vec_grid(n), 256, 0, cap>>>(r, v, s, n, dst);
+    const T* crh = rh;
+    const T* cv = v;
+    const T* cr = r;
+    const T* cs = s;
+    const T* ct = t;
+    const T* cp = p;
+    if ((ae = launch_maybe_pdl(k_multi_dot<T>, dim3(RED_BLOCKS, 1), dim3(RED_THREADS), 0, cap,
+                               true, crh, (int64_t)0, cv, n, part)) != cudaSuccess ||
+        (ae = launch_maybe_pdl(k_bi_alpha, dim3(1), dim3(RED_THREADS), 0, cap, true,
+                               (const double*)part, dst)) != cudaSuccess ||
+        (ae = launch_maybe_pdl(k_bi_s<T>, dim3(vec_grid(n)), dim3(256), 0, cap, true, cr, cv, s,
+                               n, (const BiState*)dst)) != cudaSuccess)
+      break;
     ae = apply(s, t, cap);
     if (ae != cudaSuccess) break;
-    k_bi_dot2<T><<<RED_BLOCKS, RED_THREADS, 0, cap>>>(t, s, n, dst, part);
-    k_bi_omega<<<1, RED_THREADS, 0, cap>>>(part, dst);
-    k_bi_update<T><<<RED_BLOCKS, RED_THREADS, 0, cap>>>(x, r, p, s, t, rh, n, dst, part);
-    k_bi_beta<<<1, RED_THREADS, 0, cap>>>(part, dst);
-    k_bi_p<T><<<vec_grid(n), 256, 0, cap>>>(p, r, v, n, dst);
+    if ((ae = launch_maybe_pdl(k_bi_dot2<T>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, cap, true,
+                               ct, cs, n, (const BiState*)dst, part)) != cudaSuccess ||
+        (ae = launch_maybe_pdl(k_bi_omega, dim3(1), dim3(RED_THREADS), 0, cap, true,
+                               (const double*)part, dst)) != cudaSuccess ||
+        (ae = launch_maybe_pdl(k_bi_update<T>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, cap,
+                               true, x, r, cp, cs, ct, crh, n, (const BiState*)dst, part)) !=
+            cudaSuccess ||
+        (ae = launch_maybe_pdl(k_bi_beta, dim3(1), dim3(RED_THREADS), 0, cap, true,
+                               (const double*)part, dst)) != cudaSuccess ||
+        (ae = launch_maybe_pdl(k_bi_p<T>, dim3(vec_grid(n)), dim3(256), 0, cap, true, p, cr, cv,
+                               n, (const BiState*)dst)) != cudaSuccess)
+      break;
   }
   e = cudaStreamEndCapture(cap, &graph);
   if (ae != cudaSuccess) {
