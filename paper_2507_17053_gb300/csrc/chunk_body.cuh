@@ -235,7 +235,8 @@ struct ChunkSmem {
   static constexpr int TILE = (D == 3) ? R * ND : 2 * R * ND;  // scalars before the runs
   static constexpr int XS = (D == 3) ? L * SM : XZ;
   static constexpr int WORDS = (L * SM + 31) / 32;              // run-element bits
-  static constexpr int XL = (D == 3) ? L * XLineOp<T, N>::kSize : 0;  // x-line operators
+  static constexpr int XL =                                     // x-line operators
+      (D == 3) ? XLineOp<T, N>::kSlots * XLineOp<T, N>::kPacked : 0;
   // two run areas and two run-start tables: the next chunk's runs are copied
   // in (cp.async) while the current chunk is computed
   static constexpr size_t bytes =
@@ -290,9 +291,10 @@ template <typename T, int D, int N, int R>
 __device__ __forceinline__ void chunk_xline_build(unsigned char* smem_raw, const KTab<T>& tx,
                                                   int tid) {
   constexpr int L = Shape<D, N>::L;
-  if (D == 3 && tid < L)
+  if (D == 3 && tid < L && tid % N <= tid / N)
     XLineOp<T, N>(tx, tid % N, tid / N)
-        .store(chunk_xline_smem<T, D, N, R>(smem_raw) + tid * XLineOp<T, N>::kSize);
+        .store(chunk_xline_smem<T, D, N, R>(smem_raw) +
+               XLineOp<T, N>::slot(tid % N, tid / N) * XLineOp<T, N>::kPacked);
 }
 
 // Chunks ch, ch + step, ... (< q1) of right-hand side rhs, by the whole block
@@ -322,7 +324,8 @@ __device__ __forceinline__ void chunk_loop(const ChunkArgs<T>& a, const KTab<T>&
   // registers)
   constexpr int nthr = NTHR;
   const int c = tid / L, tl = tid - c * L;
-  const XLineShared<T, N> xop{XLs + tl * XLineOp<T, N>::kSize};
+  const XLineShared<T, N> xop{XLs + XLineOp<T, N>::slot(tl % N, tl / N) *
+                                         XLineOp<T, N>::kPacked};
   const T* __restrict__ xr = a.x + rhs * a.ldx;
   const T* fo = a.face_out + rhs * a.ld_face;
   T* ycb = a.ycol + rhs * a.ld_ycol;
@@ -437,7 +440,8 @@ __device__ __forceinline__ void chunk_loop_ord(const ChunkArgs<T>& a, const KTab
   uint32_t* Bs = reinterpret_cast<uint32_t*>(Lbuf + 2 * L);
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
-  const XLineShared<T, N> xop{XLs + tl * XLineOp<T, N>::kSize};
+  const XLineShared<T, N> xop{XLs + XLineOp<T, N>::slot(tl % N, tl / N) *
+                                         XLineOp<T, N>::kPacked};
   const T* __restrict__ xr = a.x;
   T* yb = a.y;
 
@@ -683,7 +687,7 @@ template <typename T, int N, int R>
 struct DirectSmem {
   static constexpr int L = N * N, ND = L * N, P = N - 1;
   static constexpr int TILE = R * ND;                    // the cells' tiles
-  static constexpr int XL = L * XLineOp<T, N>::kSize;    // x-line operators
+  static constexpr int XL = XLineOp<T, N>::kSlots * XLineOp<T, N>::kPacked;  // x-line ops
   static constexpr int XF = R * L;                       // j0 = P faces of the cells
   static constexpr int WORDS = (L * (P * R + 1) + 31) / 32;
   static constexpr size_t bytes = (size_t)(TILE + XL + XF) * sizeof(T) + (size_t)(L + WORDS) * 4;
@@ -704,8 +708,11 @@ __device__ __forceinline__ void chunk_loop_direct(const ChunkArgs<T>& a, const K
   const int tid = threadIdx.x;
   const int c = tid / L, tl = tid - c * L;
   const int j0 = tl % N, j1 = tl / N;
-  if (tid < L) XLineOp<T, N>(tx, tid % N, tid / N).store(XLs + tid * XLineOp<T, N>::kSize);
-  const XLineShared<T, N> xop{XLs + tl * XLineOp<T, N>::kSize};
+  if (tid < L && tid % N <= tid / N)
+    XLineOp<T, N>(tx, tid % N, tid / N)
+        .store(XLs + XLineOp<T, N>::slot(tid % N, tid / N) * XLineOp<T, N>::kPacked);
+  const XLineShared<T, N> xop{XLs + XLineOp<T, N>::slot(tl % N, tl / N) *
+                                         XLineOp<T, N>::kPacked};
   const T* __restrict__ xr = a.x + rhs * a.ldx;
   const T* fo = a.face_out + rhs * a.ld_face;
   T* ycb = a.ycol + rhs * a.ld_ycol;

@@ -251,16 +251,29 @@ struct XLineOp {
     acc.unfold(y);
   }
   static constexpr int kSize = HE * HE + H * H;   // scalars of one line's operator
-  // into shared memory (E row-major, then O), for XLineShared
+  // Shared-memory form: both blocks are symmetric, so only their upper
+  // triangles are kept (row-major, E then O), and the operator of modes
+  // (a, b) equals that of (b, a) (mu_ab = mu_ba), so one slot serves both:
+  // n(n+1)/2 slots of kPacked scalars (an odd count: the threads of a warp
+  // read different slots without bank conflicts).
+  static constexpr int kPacked = (HE * (HE + 1) / 2 + H * (H + 1) / 2) | 1;
+  static constexpr int kSlots = N * (N + 1) / 2;
+  __host__ __device__ static constexpr int tri(int i, int j, int n) {   // i <= j < n
+    return i * n - i * (i - 1) / 2 + (j - i);
+  }
+  __host__ __device__ static constexpr int sym(int i, int j, int n) {
+    return i <= j ? tri(i, j, n) : tri(j, i, n);
+  }
+  __device__ static int slot(int a, int b) { return sym(a, b, N); }
   __device__ __forceinline__ void store(T* m) const {
 #pragma unroll
     for (int i = 0; i < HE; ++i)
 #pragma unroll
-      for (int j = 0; j < HE; ++j) m[i * HE + j] = E[i][j];
+      for (int j = i; j < HE; ++j) m[tri(i, j, HE)] = E[i][j];
 #pragma unroll
     for (int i = 0; i < H; ++i)
 #pragma unroll
-      for (int j = 0; j < H; ++j) m[HE * HE + i * H + j] = O[i][j];
+      for (int j = i; j < H; ++j) m[HE * (HE + 1) / 2 + tri(i, j, H)] = O[i][j];
   }
 };
 
@@ -269,18 +282,20 @@ struct XLineOp {
 template <typename T, int N>
 struct XLineShared {
   static constexpr int H = N / 2, HE = (N + 1) / 2;
-  const T* m;
+  using Op = XLineOp<T, N>;
+  const T* m;                       // the slot of the thread's modes (a, b)
   __device__ __forceinline__ void apply(const T (&v)[N], T (&y)[N]) const {
     const LineFold<T, N> f(v);
     LineAcc<T, N> acc;
 #pragma unroll
     for (int i = 0; i < HE; ++i)
 #pragma unroll
-      for (int j = 0; j < HE; ++j) acc.s[i] = fma(m[i * HE + j], f.e[j], acc.s[i]);
+      for (int j = 0; j < HE; ++j) acc.s[i] = fma(m[Op::sym(i, j, HE)], f.e[j], acc.s[i]);
 #pragma unroll
     for (int i = 0; i < H; ++i)
 #pragma unroll
-      for (int j = 0; j < H; ++j) acc.d[i] = fma(m[HE * HE + i * H + j], f.o[j], acc.d[i]);
+      for (int j = 0; j < H; ++j)
+        acc.d[i] = fma(m[HE * (HE + 1) / 2 + Op::sym(i, j, H)], f.o[j], acc.d[i]);
     acc.unfold(y);
   }
 };
