@@ -232,7 +232,8 @@ struct ChunkSmem {
   static constexpr int SM0 = (N - 1) * R + 1;
   static constexpr int SM = (SM0 % 2) ? SM0 : SM0 + 1;        // odd row stride of the runs
   static constexpr int XZ = (L * SM > R * L * N) ? L * SM : R * L * N;
-  static constexpr int TILE = (D == 3) ? R * ND : 2 * R * ND;  // scalars before the runs
+  static constexpr int TILE =                                   // scalars before the runs
+      (D == 3) ? R * TilePad<T, N>::NDP : 2 * R * ND;
   static constexpr int XS = (D == 3) ? L * SM : XZ;
   static constexpr int WORDS = (L * SM + 31) / 32;              // run-element bits
   static constexpr int XL =                                     // x-line operators
@@ -277,6 +278,14 @@ __device__ __forceinline__ void gather_runs_async(const T* __restrict__ xr, cons
   }
 }
 
+
+// Position of node (j0 = m, x-line l) of chunk cell cc among the per-cell
+// results: 3D, the padded tile (TilePad); 2D, the run area ((cc L + l) n + m).
+template <typename T, int D, int N>
+__device__ __forceinline__ int zix(int cc, int l, int m) {
+  if constexpr (D == 3) return cc * TilePad<T, N>::NDP + TilePad<T, N>::PX * l + m;
+  else return (cc * Shape<D, N>::L + l) * N + m;
+}
 
 // h K + mu M of the 3D x-lines into the chunk's shared memory (one operator
 // per x-line of modes (a, b) = (tl % n, tl / n), built by the threads of
@@ -394,7 +403,8 @@ __device__ __forceinline__ void chunk_loop(const ChunkArgs<T>& a, const KTab<T>&
       // 3D: z-line (j0, j1) = tl, back to the nodes it was read from
 #pragma unroll
       for (int m = 0; m < N; ++m) {
-        if constexpr (D == 3) Z[c * ND + tl + L * m] = out[m];
+        if constexpr (D == 3)
+          Z[c * TilePad<T, N>::NDP + tl % N + TilePad<T, N>::PX * (tl / N + N * m)] = out[m];
         else Z[(c * L + tl) * N + m] = out[m];
       }
     }
@@ -407,9 +417,9 @@ __device__ __forceinline__ void chunk_loop(const ChunkArgs<T>& a, const KTab<T>&
       const int l = __float2int_rz(((float)idx + 0.5f) * invS), kk = idx - l * S;
       const int cc = kk / P, m = kk - cc * P;
       T v;
-      if (cc == nc) v = Z[((nc - 1) * L + l) * N + P];
-      else if (m == 0 && cc > 0) v = Z[((cc - 1) * L + l) * N + P] + Z[(cc * L + l) * N];
-      else v = Z[(cc * L + l) * N + m];
+      if (cc == nc) v = Z[zix<T, D, N>(nc - 1, l, P)];
+      else if (m == 0 && cc > 0) v = Z[zix<T, D, N>(cc - 1, l, P)] + Z[zix<T, D, N>(cc, l, 0)];
+      else v = Z[zix<T, D, N>(cc, l, m)];
       const int64_t g = (int64_t)Ls[l] + kk;
       if ((Bs[idx >> 5] >> (idx & 31)) & 1u) yc[g] = v;
       else yb[g] = v;
@@ -512,7 +522,8 @@ __device__ __forceinline__ void chunk_loop_ord(const ChunkArgs<T>& a, const KTab
       }
 #pragma unroll
       for (int m = 0; m < N; ++m) {
-        if constexpr (D == 3) Z[c * ND + tl + L * m] = out[m];
+        if constexpr (D == 3)
+          Z[c * TilePad<T, N>::NDP + tl % N + TilePad<T, N>::PX * (tl / N + N * m)] = out[m];
         else Z[(c * L + tl) * N + m] = out[m];
       }
     }
@@ -539,9 +550,10 @@ __device__ __forceinline__ void chunk_loop_ord(const ChunkArgs<T>& a, const KTab
         const int l = __float2int_rz(((float)idx + 0.5f) * invS), kk = idx - l * S;
         const int cc = kk / P, m = kk - cc * P;
         T v;
-        if (cc == nc) v = Z[((nc - 1) * L + l) * N + P];
-        else if (m == 0 && cc > 0) v = Z[((cc - 1) * L + l) * N + P] + Z[(cc * L + l) * N];
-        else v = Z[(cc * L + l) * N + m];
+        if (cc == nc) v = Z[zix<T, D, N>(nc - 1, l, P)];
+        else if (m == 0 && cc > 0)
+          v = Z[zix<T, D, N>(cc - 1, l, P)] + Z[zix<T, D, N>(cc, l, 0)];
+        else v = Z[zix<T, D, N>(cc, l, m)];
         yb[(int64_t)Ls[l] + kk] = ((Bs[idx >> 5] >> (idx & 31)) & 1u) ? old[k] + v : v;
       }
     }
@@ -686,7 +698,7 @@ __device__ __forceinline__ void assemble_pair(const T* __restrict__ ycol,
 template <typename T, int N, int R>
 struct DirectSmem {
   static constexpr int L = N * N, ND = L * N, P = N - 1;
-  static constexpr int TILE = R * ND;                    // the cells' tiles
+  static constexpr int TILE = R * TilePad<T, N>::NDP;    // the cells' tiles
   static constexpr int XL = XLineOp<T, N>::kSlots * XLineOp<T, N>::kPacked;  // x-line ops
   static constexpr int XF = R * L;                       // j0 = P faces of the cells
   static constexpr int WORDS = (L * (P * R + 1) + 31) / 32;

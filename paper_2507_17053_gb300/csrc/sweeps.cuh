@@ -300,54 +300,66 @@ struct XLineShared {
   }
 };
 
+// The 3D cell tile in shared memory: node (j0, j1, j2) of a cell at
+// j0 + PX j1 + PX n j2, cells NDP apart.  For even n the x-stride is padded
+// to PX = n + 1 (FP32, and FP64 at n = 4) so that the x-line phase (stride PX
+// between threads) and the y-line phase (stride PX n) spread over the
+// shared-memory banks; odd n are conflict-free unpadded.
+template <typename T, int N>
+struct TilePad {
+  static constexpr int PX =
+      (N % 2 == 0 && (std::is_same<T, float>::value || N == 4)) ? N + 1 : N;
+  static constexpr int NDP = PX * N * N;
+};
+
 // The thread's z-line of x comes from load(j), j = 0..n-1 (staged runs in
 // shared memory, or global memory directly).
 template <typename T, int N, typename XOp, typename Load>
 __device__ __forceinline__ void cell_fd_3d_l(const KTab<T>& t, const Load& load, T* tile, int c,
                                              int tl, bool act, const XOp& xop, T (&out)[N]) {
-  constexpr int L = N * N, ND = L * N;
+  constexpr int PX = TilePad<T, N>::PX, NDP = TilePad<T, N>::NDP, PL = PX * N;
   const int a = tl % N, b = tl / N;
-  T* cell = tile + c * ND;
+  T* cell = tile + c * NDP;
   if (act) {                       // z-lines (j0, j1) = (a, b) -> z-modes
     T v[N], w[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) v[j] = load(j);
     line_to_modes<T, N>(t.fVt, v, w);
 #pragma unroll
-    for (int k = 0; k < N; ++k) cell[tl + L * k] = w[k];
+    for (int k = 0; k < N; ++k) cell[a + PX * b + PL * k] = w[k];
   }
   __syncthreads();
   if (act) {                       // y-lines (j0 = a, z-mode b) -> y-modes
     T v[N], w[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = cell[a + N * j + L * b];
+    for (int j = 0; j < N; ++j) v[j] = cell[a + PX * j + PL * b];
     line_to_modes<T, N>(t.fVt, v, w);
 #pragma unroll
-    for (int k = 0; k < N; ++k) cell[a + N * k + L * b] = w[k];
+    for (int k = 0; k < N; ++k) cell[a + PX * k + PL * b] = w[k];
   }
   __syncthreads();
   if (act) {                       // x-lines (y-mode a, z-mode b): h K + mu_ab M
     T v[N], y[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = cell[N * tl + j];
+    for (int j = 0; j < N; ++j) v[j] = cell[PX * tl + j];
     xop.apply(v, y);
 #pragma unroll
-    for (int j = 0; j < N; ++j) cell[N * tl + j] = y[j];
+    for (int j = 0; j < N; ++j) cell[PX * tl + j] = y[j];
   }
   __syncthreads();
   if (act) {                       // y-modes back (j0 = a, z-mode b)
     T w[N], y[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) w[k] = cell[a + N * k + L * b];
+    for (int k = 0; k < N; ++k) w[k] = cell[a + PX * k + PL * b];
     modes_to_line<T, N>(t.fV, w, y);
 #pragma unroll
-    for (int j = 0; j < N; ++j) cell[a + N * j + L * b] = y[j];
+    for (int j = 0; j < N; ++j) cell[a + PX * j + PL * b] = y[j];
   }
   __syncthreads();
   if (act) {                       // z-modes back (j0, j1) = (a, b)
     T w[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) w[k] = cell[tl + L * k];
+    for (int k = 0; k < N; ++k) w[k] = cell[a + PX * b + PL * k];
     modes_to_line<T, N>(t.fV, w, out);
   }
 }
