@@ -77,7 +77,7 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
     T out[N];
     if constexpr (D == 3) {
       const XLineOp<T, N> xop(t, tl % N, tl / N);
-      cell_fd_3d<T, N>(t, X, c * ND + tl, N * N, A, c, tl, act, xop, out);
+      cell_fd_3d<T, N, false>(t, X, c * ND + tl, N * N, A, c, tl, act, xop, out);
       if (act) {
 #pragma unroll
         for (int m = 0; m < N; ++m) R[tl + N * N * m] = out[m];

@@ -314,10 +314,12 @@ struct TilePad {
 
 // The thread's z-line of x comes from load(j), j = 0..n-1 (staged runs in
 // shared memory, or global memory directly).
-template <typename T, int N, typename XOp, typename Load>
+// PAD = false: the unpadded layout (PX = n), for callers that address the
+// tile themselves (the DG kernel).
+template <typename T, int N, bool PAD = true, typename XOp, typename Load>
 __device__ __forceinline__ void cell_fd_3d_l(const KTab<T>& t, const Load& load, T* tile, int c,
                                              int tl, bool act, const XOp& xop, T (&out)[N]) {
-  constexpr int PX = TilePad<T, N>::PX, NDP = TilePad<T, N>::NDP, PL = PX * N;
+  constexpr int PX = PAD ? TilePad<T, N>::PX : N, NDP = PX * N * N, PL = PX * N;
   const int a = tl % N, b = tl / N;
   T* cell = tile + c * NDP;
   if (act) {                       // z-lines (j0, j1) = (a, b) -> z-modes
@@ -364,11 +366,11 @@ __device__ __forceinline__ void cell_fd_3d_l(const KTab<T>& t, const Load& load,
   }
 }
 
-template <typename T, int N, typename XOp>
+template <typename T, int N, bool PAD = true, typename XOp>
 __device__ __forceinline__ void cell_fd_3d(const KTab<T>& t, const T* X, int xb, int xs, T* tile,
                                            int c, int tl, bool act, const XOp& xop,
                                            T (&out)[N]) {
-  cell_fd_3d_l<T, N>(t, [&](int j) { return X[xb + xs * j]; }, tile, c, tl, act, xop, out);
+  cell_fd_3d_l<T, N, PAD>(t, [&](int j) { return X[xb + xs * j]; }, tile, c, tl, act, xop, out);
 }
 
 // ---- cell term -------------------------------------------------------------
