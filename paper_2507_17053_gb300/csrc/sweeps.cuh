@@ -321,6 +321,7 @@ __device__ __forceinline__ void cell_fd_3d_l(const KTab<T>& t, const Load& load,
                                              int tl, bool act, const XOp& xop, T (&out)[N]) {
   constexpr int PX = PAD ? TilePad<T, N>::PX : N, NDP = PX * N * N, PL = PX * N;
   const int a = tl % N, b = tl / N;
+  const int zl = (PX == N) ? tl : a + PX * b;     // the z-line's first node
   T* cell = tile + c * NDP;
   if (act) {                       // z-lines (j0, j1) = (a, b) -> z-modes
     T v[N], w[N];
@@ -328,7 +329,7 @@ __device__ __forceinline__ void cell_fd_3d_l(const KTab<T>& t, const Load& load,
     for (int j = 0; j < N; ++j) v[j] = load(j);
     line_to_modes<T, N>(t.fVt, v, w);
 #pragma unroll
-    for (int k = 0; k < N; ++k) cell[a + PX * b + PL * k] = w[k];
+    for (int k = 0; k < N; ++k) cell[zl + PL * k] = w[k];
   }
   __syncthreads();
   if (act) {                       // y-lines (j0 = a, z-mode b) -> y-modes
@@ -361,7 +362,7 @@ __device__ __forceinline__ void cell_fd_3d_l(const KTab<T>& t, const Load& load,
   if (act) {                       // z-modes back (j0, j1) = (a, b)
     T w[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) w[k] = cell[a + PX * b + PL * k];
+    for (int k = 0; k < N; ++k) w[k] = cell[zl + PL * k];
     modes_to_line<T, N>(t.fV, w, out);
   }
 }
