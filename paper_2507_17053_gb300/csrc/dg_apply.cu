@@ -29,6 +29,17 @@ struct DgShape {
   static constexpr int CPB = (128 / L) > 0 ? (128 / L) : 1;
 };
 
+// The result tile A (3D FP32: the padded layout of TilePad, node (j0, j1, j2)
+// at j0 + PX j1 + PX n j2, cells NDP apart; FP64 (pipe-bound, registers
+// first) and 2D unpadded; 2D: the pair tile's two halves).
+template <typename T, int D, int N>
+struct DgTile {
+  static constexpr bool kPad = D == 3 && std::is_same<T, float>::value;
+  static constexpr int PX = kPad ? TilePad<T, N>::PX : N;
+  static constexpr int NDP = kPad ? TilePad<T, N>::NDP : (D == 3 ? 1 : 2) * DgShape<D, N>::ND;
+  static constexpr int elems = DgShape<D, N>::CPB * NDP;   // A, before the input tiles
+};
+
 template <typename T>
 struct DgArgs {
   const T* __restrict__ x;
@@ -49,9 +60,10 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // 3D: a scalar sweep tile (the eigenbasis phases run in place and leave the
   // cell results there); 2D: a pair tile for the sweeps, then the results
+  using DT = DgTile<T, D, N>;
   T* A = reinterpret_cast<T*>(smem_raw);       // sweep tile, then the result tile
   Pair2* AE = reinterpret_cast<Pair2*>(smem_raw);
-  T* X = A + (D == 3 ? 1 : 2) * CPB * ND;      // CPB input tiles
+  T* X = A + DT::elems;                        // CPB input tiles (unpadded)
   T* U1 = X + CPB * ND;        // face scratch, CPB * L each
   T* U2 = U1 + CPB * L;
   T* P1 = U2 + CPB * L;
@@ -69,7 +81,7 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
   const int pos = first + (act ? c : 0);
   const int rank = __ldg(a.cell_rank + pos);
   T* Xc = X + c * ND;
-  T* R = A + c * ND;
+  T* R = A + c * (D == 3 ? DT::NDP : ND);
   {
     // cell term (Algorithm 1), then the line result into R (node (j0, j1, j2)
     // at j0 + n j1 + n^2 j2): 3D the z-line tl, back to the nodes its last
@@ -77,10 +89,11 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
     T out[N];
     if constexpr (D == 3) {
       const XLineOp<T, N> xop(t, tl % N, tl / N);
-      cell_fd_3d<T, N, false>(t, X, c * ND + tl, N * N, A, c, tl, act, xop, out);
+      cell_fd_3d<T, N, DT::kPad>(t, X, c * ND + tl, N * N, A, c, tl, act, xop, out);
       if (act) {
 #pragma unroll
-        for (int m = 0; m < N; ++m) R[tl + N * N * m] = out[m];
+        for (int m = 0; m < N; ++m)
+          R[DT::PX == N ? tl + N * N * m : tl % N + DT::PX * (tl / N + N * m)] = out[m];
       }
     } else {
       cell_sweeps_2d<T, N>(t, X, c * ND + tl, N, AE, c, tl, act, out);
@@ -110,6 +123,12 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
       sb = (k == 2) ? N : N * N;
     }
     const int bt = (tl % N) * sa + (D == 3 ? (tl / N) * sb : 0);
+    // the same strides in the result tile (3D FP32: padded)
+    int rk = sk, rbt = bt;
+    if constexpr (DT::PX != N) {
+      rk = (k == 0) ? 1 : (k == 1 ? DT::PX : DT::PX * N);
+      rbt = (tl % N) * ((k == 0) ? DT::PX : 1) + (tl / N) * ((k == 2) ? DT::PX : DT::PX * N);
+    }
     for (int s = 0; s < 2; ++s) {
       const int nb = act ? __ldg(a.nbr + (size_t)rank * 2 * D + 2 * k + s) : -1;
       const bool interior = nb >= 0;
@@ -181,16 +200,18 @@ dg_apply_kernel(const DgArgs<T> a, const __grid_constant__ KTab<T> t) {
         rg = __ldg(fo + L + tl);
       }
       if (act) {
-        R[kend * sk + bt] += rv;
+        R[kend * rk + rbt] += rv;
 #pragma unroll
-        for (int j = 0; j < N; ++j) R[j * sk + bt] = fma(s ? t.D1[j] : t.D0[j], rg, R[j * sk + bt]);
+        for (int j = 0; j < N; ++j)
+          R[j * rk + rbt] = fma(s ? t.D1[j] : t.D0[j], rg, R[j * rk + rbt]);
       }
       __syncthreads();
     }
   }
   for (int r = tid; r < ncells * ND; r += blockDim.x) {
-    const int cc = r / ND;
-    a.y[(size_t)__ldg(a.cell_rank + first + cc) * ND + (r - cc * ND)] = A[r];
+    const int cc = r / ND, q = r - cc * ND;
+    const int ar = DT::PX != N ? cc * DT::NDP + q % N + DT::PX * (q / N) : r;
+    a.y[(size_t)__ldg(a.cell_rank + first + cc) * ND + q] = A[ar];
   }
 }
 
@@ -199,7 +220,7 @@ static cudaError_t dg_t(const HostProblem& hp, const DeviceData& dd, const T* x,
                         cudaStream_t st, Profiler* prof, int face_mode) {
   constexpr int L = DgShape<D, N>::L, ND = DgShape<D, N>::ND, CPB = DgShape<D, N>::CPB;
   const KTab<T> t = make_ktab<T>(hp);
-  const size_t smem = (size_t)(((D == 3) ? 2 : 3) * CPB * ND + 4 * CPB * L) * sizeof(T);
+  const size_t smem = (size_t)(DgTile<T, D, N>::elems + CPB * ND + 4 * CPB * L) * sizeof(T);
   cudaError_t err;
   if (smem > 48 * 1024) {
     err = cudaFuncSetAttribute(dg_apply_kernel<T, D, N>,
