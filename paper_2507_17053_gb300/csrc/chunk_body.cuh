@@ -316,7 +316,7 @@ template <typename T, int D, int N, int R, bool COH, int NTHR, bool PDL = false>
 __device__ __forceinline__ void chunk_loop(const ChunkArgs<T>& a, const KTab<T>& t,
                                            unsigned char* smem_raw, int rhs, int ch, int q1,
                                            int step) {
-  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, P = N - 1;
+  constexpr int L = Shape<D, N>::L, P = N - 1;
   constexpr int SM = ChunkSmem<T, D, N, R>::SM;
   using P2 = typename PairOf<T>::type;
   using CS = ChunkSmem<T, D, N, R>;
@@ -438,7 +438,7 @@ __shared__ int s_ord_next;
 template <typename T, int D, int N, int R>
 __device__ __forceinline__ void chunk_loop_ord(const ChunkArgs<T>& a, const KTab<T>& t,
                                                unsigned char* smem_raw, const OrdArgs& o) {
-  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, P = N - 1;
+  constexpr int L = Shape<D, N>::L, P = N - 1;
   constexpr int SM = ChunkSmem<T, D, N, R>::SM;
   using P2 = typename PairOf<T>::type;
   using CS = ChunkSmem<T, D, N, R>;
@@ -710,7 +710,7 @@ __device__ __forceinline__ void chunk_loop_direct(const ChunkArgs<T>& a, const K
                                                   const KTab<T>& tx, unsigned char* smem_raw,
                                                   int rhs, int ch, int q1, int step,
                                                   const OrdArgs* o = nullptr) {
-  constexpr int L = N * N, ND = L * N, P = N - 1;
+  constexpr int L = N * N, P = N - 1;
   using DS = DirectSmem<T, N, R>;
   T* tile = reinterpret_cast<T*>(smem_raw);
   T* XLs = tile + DS::TILE;
@@ -733,8 +733,6 @@ __device__ __forceinline__ void chunk_loop_direct(const ChunkArgs<T>& a, const K
     if (tid == 0) s_ord_next = (int)atomicAdd(o->tickets, 1u);
     __syncthreads();
     ch = ord_chunk(*o, s_ord_next);
-    q1 = ch + 1;
-    step = 0;
   }
   while (ORD ? ch >= 0 : ch < q1) {
     const int first = __ldg(a.chunk_first + ch);

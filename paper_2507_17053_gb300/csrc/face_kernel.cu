@@ -37,7 +37,7 @@ sface_kernel(const FaceArgs<T> a, const __grid_constant__ KTab<T> t) {
 template <typename T, int D, int N, int EXT>
 static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* x, T* out,
                           cudaStream_t st, int64_t ldx, int nrhs, int fb, int fe) {
-  constexpr int L = Shape<D, N>::L, ND = Shape<D, N>::ND, FPB = Shape<D, N>::CPB;
+  constexpr int L = Shape<D, N>::L, FPB = Shape<D, N>::CPB;
   if (fe <= fb) return cudaSuccess;
   const KTab<T> t = make_ktab<T>(hp);
   FaceArgs<T> a;
@@ -54,7 +54,7 @@ static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* 
   a.dg = hp.desc.dg;
   a.ldx = ldx;
   a.ld_out = (int64_t)dd.nface * 2 * L;
-  const size_t smem = (size_t)(FPB * ND + FPB * FaceScratch<EXT>::n * L) * sizeof(T);
+  const size_t smem = (size_t)(FPB * Shape<D, N>::ND + FPB * FaceScratch<EXT>::n * L) * sizeof(T);
   sface_kernel<T, D, N, EXT><<<dim3((fe - fb + FPB - 1) / FPB, nrhs), FPB * L, smem, st>>>(a, t);
   return cudaGetLastError();
 }
