@@ -54,7 +54,7 @@ static cudaError_t face_t(const HostProblem& hp, const DeviceData& dd, const T* 
   a.dg = hp.desc.dg;
   a.ldx = ldx;
   a.ld_out = (int64_t)dd.nface * 2 * L;
-  const size_t smem = (size_t)(FPB * Shape<D, N>::ND + FPB * FaceScratch<EXT>::n * L) * sizeof(T);
+  const size_t smem = face_group_smem<T, D, N, EXT, FPB>();
   sface_kernel<T, D, N, EXT><<<dim3((fe - fb + FPB - 1) / FPB, nrhs), FPB * L, smem, st>>>(a, t);
   return cudaGetLastError();
 }
