@@ -42,7 +42,7 @@ FP64_PIPE_GOPS = SMS * SM_MAX_MHZ * 1e6 * FP64_LANES_PER_SM_CLK / 1e9
 # from one ncu capture per (workload, tile shape, store mode) of the kernel as
 # it stood when captured (dram__bytes_read.sum + dram__bytes_write.sum), not
 # measured by this run; other shapes and modes: not captured
-CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 0, 0): 127.35e6 + 108.24e6,
+CELL_TRAFFIC = {("sphere3d_cg_q4_n96", 0, 0): 127.09e6 + 106.99e6,
                 ("sphere3d_cg_q4_n96", 1, 0): 157.950720e6 + 133.191680e6}
 L2_BYTES = 129 * 1024 * 1024
 REF_BUDGET_S = 90.0              # wall-clock budget of the --impl reference run
