@@ -303,6 +303,29 @@ def time_applies(P, fn, x, y, steps, warmup, st, dist=None, dev=None, clocks=Non
     return ms, [p / steps for p in phases], launches, clk
 
 
+def time_plain(fn, x, y, steps, warmup, st, dist=None, dev=None):
+    """CUDA-event time of `steps` applies (after `warmup`) with the library's
+    profiler off: no events between an apply's kernels, so FP32 applies keep
+    their programmatic dependent launches (the call a user makes), max over
+    ranks."""
+    import torch
+
+    for _ in range(max(3, warmup)):
+        fn(x, y)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn(x, y)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1), dist, dev)
+
+
 def solve_times(G, torch):
     """Time-to-1e-10 (true FP64 relative residual; b from u = prod sin(pi x_i)).
 
@@ -873,6 +896,8 @@ def run_ours(args, w):
     y32 = torch.empty_like(x32)
     ms32, ph32, launches32, _ = time_applies(P, lambda a, b: P.apply_f32(a, b), x32, y32,
                                              args.steps, args.warmup, st, dist, dev)
+    ms32u = time_plain(lambda a, b: P.apply_f32(a, b), x32, y32, args.steps, args.warmup, st,
+                       dist, dev)
 
     # end to end through the C ABI with host buffers (H2D + apply + D2H per step)
     xh = torch.from_numpy(x_host).pin_memory()
@@ -890,6 +915,7 @@ def run_ours(args, w):
         return
     value = job_rate(world, n * args.steps, ms * 1e-3) / 1e9
     value32 = job_rate(world, n * args.steps, ms32 * 1e-3) / 1e9
+    value32u = job_rate(world, n * args.steps, ms32u * 1e-3) / 1e9
     pk, pk_src = peaks()
     cfma, cadd = cell_ops(w.dim, w.degree, P.n_cells)
     cflops = 2 * cfma + cadd
@@ -898,7 +924,7 @@ def run_ours(args, w):
     cell_ms = ph[1]
     achieved_gops = cops / (cell_ms * 1e-3) / 1e9
     step_s = ms / args.steps * 1e-3
-    step32_s = ms32 / args.steps * 1e-3
+    step32_s = ms32u / args.steps * 1e-3
     line = {
         "metric": "GDoF/s per operator apply (FP64)",
         "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -939,7 +965,11 @@ def run_ours(args, w):
                              "achieved_gbs": 16 * n / step_s / 1e9,
                              "peak_gbs": pk.get("hbm_gbs"), "peak_src": pk_src,
                              "frac": 16 * n / step_s / 1e9 / pk["hbm_gbs"]}},
-        "fp32_apply": {"value": value32, "unit": "GDoF/s", "ms_per_step": ms32 / args.steps,
+        "fp32_apply": {"value": value32u, "unit": "GDoF/s", "ms_per_step": ms32u / args.steps,
+                       "timing": "profiler off (the applies as a user calls them, programmatic "
+                                 "dependent launches active); the phases come from a second, "
+                                 "profiled loop of the same applies",
+                       "profiled": {"value": value32, "ms_per_step": ms32 / args.steps},
                        "launches": launches32,
                        "phases_ms_per_step": {"face": ph32[0], "cell": ph32[1],
                                               "assembly": ph32[2]},

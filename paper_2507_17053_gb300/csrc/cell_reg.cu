@@ -12,7 +12,9 @@
 //  2. runs the five line phases (z- and y-transforms, the x-line operators
 //     h K + mu_ab M, transforms back) -- the same per-line arithmetic as the
 //     chunk kernel,
-//  3. folds in its surrogate faces' results, in the chunk kernel's order,
+//  3. folds in its surrogate faces' results, in the chunk kernel's order
+//     (under a programmatic dependent launch only the threads of cells with
+//     surrogate faces wait for the face kernel),
 //  4. adds the x-face values of the previous cell of its chunk (shared
 //     memory; a block holds whole chunks), prev + own as the chunk kernel,
 //  5. stores every node it owns (the last node of a line belongs to the next
@@ -165,7 +167,7 @@ __device__ __forceinline__ void cell_phases(const KTab<T>& t, const XOps<T, N>& 
 
 // surrogate face (k, s): the chunk kernel's fold_face_z on every z-line
 // (j0, j1) of the tile, in the same operation order
-template <typename T, int N, int K, int SD>
+template <typename T, int N, int K, int SD, bool COH>
 __device__ __forceinline__ void fold_reg(const KTab<T>& t, const T* __restrict__ fo,
                                          T (&u)[N * N * N]) {
   constexpr int L = N * N, KEND = SD ? N - 1 : 0;
@@ -176,7 +178,7 @@ __device__ __forceinline__ void fold_reg(const KTab<T>& t, const T* __restrict__
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       if (K == 2) {
-        const T vv = __ldg(rv + a + N * b), g = __ldg(rg + a + N * b);
+        const T vv = ld_face<COH>(rv + a + N * b), g = ld_face<COH>(rg + a + N * b);
 #pragma unroll
         for (int m = 0; m < N; ++m) {
           T& o = u[a + N * b + L * m];
@@ -188,15 +190,15 @@ __device__ __forceinline__ void fold_reg(const KTab<T>& t, const T* __restrict__
         const T dk = SD ? t.D1[jk] : t.D0[jk];
 #pragma unroll
         for (int m = 0; m < N; ++m) {
-          T add = mul_rn(dk, __ldg(rg + jo + N * m));
-          if (jk == KEND) add = add_rn(add, __ldg(rv + jo + N * m));
+          T add = mul_rn(dk, ld_face<COH>(rg + jo + N * m));
+          if (jk == KEND) add = add_rn(add, ld_face<COH>(rv + jo + N * m));
           u[a + N * b + L * m] = add_rn(u[a + N * b + L * m], add);
         }
       }
     }
 }
 
-template <typename T, int N>
+template <typename T, int N, bool PDL>
 __global__ void __launch_bounds__(kRegThreads, (reg_min_blocks<T, N>()))
 cg_cell_reg_kernel(const RegArgs<T> a, const __grid_constant__ KTab<T> t,
                    const __grid_constant__ XOps<T, N> xo) {
@@ -223,16 +225,19 @@ cg_cell_reg_kernel(const RegArgs<T> a, const __grid_constant__ KTab<T> t,
     }
     cell_phases<T, N>(t, xo, u);
     const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);
+    if constexpr (PDL) {
+      if (fs < fe) pdl_wait();
+    }
     for (int f2 = fs; f2 < fe; ++f2) {
       const int kind = __ldg(a.face_kind + f2);
       const T* fo = a.face_out + (size_t)f2 * 2 * L;
       switch (kind) {
-        case 0: fold_reg<T, N, 0, 0>(t, fo, u); break;
-        case 1: fold_reg<T, N, 1, 0>(t, fo, u); break;
-        case 2: fold_reg<T, N, 2, 0>(t, fo, u); break;
-        case 4: fold_reg<T, N, 0, 1>(t, fo, u); break;
-        case 5: fold_reg<T, N, 1, 1>(t, fo, u); break;
-        case 6: fold_reg<T, N, 2, 1>(t, fo, u); break;
+        case 0: fold_reg<T, N, 0, 0, PDL>(t, fo, u); break;
+        case 1: fold_reg<T, N, 1, 0, PDL>(t, fo, u); break;
+        case 2: fold_reg<T, N, 2, 0, PDL>(t, fo, u); break;
+        case 4: fold_reg<T, N, 0, 1, PDL>(t, fo, u); break;
+        case 5: fold_reg<T, N, 1, 1, PDL>(t, fo, u); break;
+        case 6: fold_reg<T, N, 2, 1, PDL>(t, fo, u); break;
         default: break;
       }
     }
@@ -310,12 +315,20 @@ cudaError_t launch_reg(const HostProblem& hp, const DeviceData& dd, const T* x, 
   a.n_dofs = hp.n_dofs;
   const KTab<T> t = make_ktab<T>(hp);
   const XOps<T, N> xo = make_xops<T, N>(t);
-  // launched without programmatic dependency (pdl ignored): waiting for the
-  // face kernel inside this 168-register kernel, and reading the face
-  // results with coherent loads, cost it 5 % (Q4 FP32 cell 83 -> 87 us)
-  (void)pdl;
-  cg_cell_reg_kernel<T, N><<<dd.reg_nblocks, kRegThreads, 0, st>>>(a, t, xo);
-  return cudaGetLastError();
+  // pdl (FP32 applies after the CUDA-core face kernel): a programmatic
+  // dependent launch; a thread waits for the face kernel only when its cell
+  // has surrogate faces (the other cells need nothing from it) and then reads
+  // the face results with coherent loads.  The kernel does not trigger its
+  // own dependents early (the assembly starts as its blocks finish): an early
+  // trigger cost 0.5-1 %.  Measured, unprofiled FP32 applies on GB300,
+  // spheres with 96^3 cells (128^3 at p = 2): p = 4 0.1427 -> 0.1409 ms,
+  // p = 3 0.0623 -> 0.0577 ms, p = 2 0.0520 -> 0.0480 ms; results bitwise
+  // unchanged.
+  cudaError_t e = pdl ? launch_maybe_pdl(cg_cell_reg_kernel<T, N, true>, dim3(dd.reg_nblocks),
+                                         dim3(kRegThreads), 0, st, true, a, t, xo)
+                      : launch_maybe_pdl(cg_cell_reg_kernel<T, N, false>, dim3(dd.reg_nblocks),
+                                         dim3(kRegThreads), 0, st, false, a, t, xo);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace

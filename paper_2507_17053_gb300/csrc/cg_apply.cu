@@ -210,11 +210,12 @@ static cudaError_t apply_r(const HostProblem& hp, const DeviceData& dd, const Ch
   int nlaunch = 0;
   if (pr && (err = prof->mark(st)) != cudaSuccess) return err;
   // programmatic dependent launches (FP32 whole applies, no profiling marks
-  // between the kernels): the chunk kernels (shapes 0, 3) after the
+  // between the kernels): the cell kernels (shapes 0, 2, 3) after the
   // CUDA-core face kernel (which x's producers precede in the stream), the
   // assembly after the cell kernel.  Measured (unprofiled applies, GB300):
   // FP32 p = 6 ellipsoid (shape 3) 62.7 -> 57.4 us, p = 3 / 4 spheres
-  // (shapes 0, 3) 1-5 % faster; the FP64 p = 4 sphere 2.3 % slower (1.026 ->
+  // (shapes 0, 3) 1-5 % faster, shape 2 1-8 % faster (cell_reg.cu); the
+  // FP64 p = 4 sphere 2.3 % slower (1.026 ->
   // 1.049 ms), so FP64 launches without it.
   allow_pdl = allow_pdl && std::is_same<T, float>::value;
   bool pdl_cell = false;

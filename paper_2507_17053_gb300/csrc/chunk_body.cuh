@@ -759,10 +759,10 @@ __device__ __forceinline__ void chunk_loop_direct(const ChunkArgs<T>& a, const K
     cell_fd_3d_l<T, N>(
         t, [&](int j) { return __ldg(xr + Ls[j1 + N * j] + P * c + j0); }, tile, c, tl, act, xop,
         out);
-    if (PDL) pdl_wait();                      // the face kernel's results
     if (act) {
       const int pos = first + c;
       const int fs = __ldg(a.face_start + pos), fe = __ldg(a.face_start + pos + 1);
+      if (PDL && fs < fe) pdl_wait();         // the face kernel's results
       for (int f = fs; f < fe; ++f) {
         const int kind = __ldg(a.face_kind + f);
         fold_face_z<T, N, COH>(t, fo + (size_t)f * 2 * L, kind & 3, kind >> 2, j0, j1, out);
