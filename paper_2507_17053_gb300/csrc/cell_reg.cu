@@ -31,20 +31,24 @@ namespace sbm {
 
 namespace {
 
-// 64 cells per block (whole chunks): the smaller blocks fill the register
-// file better than 128-cell ones (Q4 FP32 cell term 0.096 -> 0.083 ms).
-#ifndef SBM_REG_THREADS
-#define SBM_REG_THREADS 64
-#endif
-constexpr int kRegThreads = SBM_REG_THREADS;
+// Threads (cells) per block, a block holding whole chunks of R = 256 / n^2
+// cells: 96 at p = 4, 32 at p = 2, 3, 64 at p = 1 (a chunk of 64 cells).
+// A thread lives one cell, about 25 us at p = 4, so the grid's last,
+// partly filled wave costs up to that much; the sizes were measured
+// (unprofiled FP32 applies, spheres of 96^3 cells, 128^3 at p = 2; 64
+// threads before): p = 4 0.1352 -> 0.1331 ms (96; 32: 0.1429, 128:
+// 0.1351), p = 3 0.0577 -> 0.0562 ms (32; 96: 0.0597), p = 2 0.0469 ->
+// 0.0458 ms (32).  (Earlier, without the programmatic launch, 64-cell
+// blocks beat 128-cell ones at p = 4: 0.096 -> 0.083 ms.)
+constexpr int reg_threads(int n) { return n == 5 ? 96 : (n == 2 ? 64 : 32); }
 
-// Resident blocks asked of the compiler: FP32 p <= 3, 8 (128 registers, no
-// spills; p = 3 cell term 41.2 -> 37.9 us against 6 blocks at 148
-// registers); p = 4 and FP64, 6 (168 registers; 7 or 8 blocks spill the
-// p = 4 tile: 83 -> 102 us).
+// Resident blocks asked of the compiler, as warps per SM: FP32 p <= 3, 16
+// (128 registers, no spills; p = 3 cell term 41.2 -> 37.9 us against 12 at
+// 148 registers); p = 4 and FP64, 12 (168 registers; 14 or 16 warps spill
+// the p = 4 tile: 83 -> 102 us).
 template <typename T, int N>
 constexpr int reg_min_blocks() {
-  return (std::is_same<T, float>::value && N <= 4) ? 8 : 6;
+  return ((std::is_same<T, float>::value && N <= 4) ? 16 : 12) * 32 / reg_threads(N);
 }
 
 template <int N>
@@ -199,11 +203,11 @@ __device__ __forceinline__ void fold_reg(const KTab<T>& t, const T* __restrict__
 }
 
 template <typename T, int N, bool PDL>
-__global__ void __launch_bounds__(kRegThreads, (reg_min_blocks<T, N>()))
+__global__ void __launch_bounds__(reg_threads(N), (reg_min_blocks<T, N>()))
 cg_cell_reg_kernel(const RegArgs<T> a, const __grid_constant__ KTab<T> t,
                    const __grid_constant__ XOps<T, N> xo) {
   constexpr int L = N * N, ND = L * N, P = N - 1, W = reg_words<N>();
-  __shared__ T xface[kRegThreads][L + 1];       // j0 = P face of each cell (odd row stride)
+  __shared__ T xface[reg_threads(N)][L + 1];    // j0 = P face of each cell (odd row stride)
   const int tid = threadIdx.x;
   const int b0 = a.block_first[blockIdx.x], b1 = a.block_first[blockIdx.x + 1];
   const int c0 = __ldg(a.chunk_first + b0), c1 = __ldg(a.chunk_first + b1);
@@ -325,9 +329,9 @@ cudaError_t launch_reg(const HostProblem& hp, const DeviceData& dd, const T* x, 
   // p = 3 0.0623 -> 0.0577 ms, p = 2 0.0520 -> 0.0480 ms; results bitwise
   // unchanged.
   cudaError_t e = pdl ? launch_maybe_pdl(cg_cell_reg_kernel<T, N, true>, dim3(dd.reg_nblocks),
-                                         dim3(kRegThreads), 0, st, true, a, t, xo)
+                                         dim3(reg_threads(N)), 0, st, true, a, t, xo)
                       : launch_maybe_pdl(cg_cell_reg_kernel<T, N, false>, dim3(dd.reg_nblocks),
-                                         dim3(kRegThreads), 0, st, false, a, t, xo);
+                                         dim3(reg_threads(N)), 0, st, false, a, t, xo);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -338,21 +342,25 @@ bool cell_reg_available(const HostProblem& hp, bool fp32) {
 }
 
 // The per-cell tables of tile shape 2 (3D continuous Galerkin, n <= 5): the
-// chunk of every ordered cell, blocks of whole chunks (at most kRegThreads
-// cells), and the per-cell multi-colour bits (from the device run bits of
-// tile shape 0).
+// chunk of every ordered cell, blocks of whole chunks (at most
+// reg_threads(n) cells; a chunk has at most 256 / n^2 <= reg_threads(n)),
+// and the per-cell multi-colour bits (from the device run bits of tile
+// shape 0).
 cudaError_t build_cell_reg_tables(const HostProblem& hp, const std::vector<int32_t>& ch_first,
                                   DeviceData* dd) {
   if (!cell_reg_available(hp, true)) return cudaSuccess;
   const int nch = (int)ch_first.size() - 1;
   const int nc_all = ch_first.back();
+  const int threads = reg_threads(hp.n);
   std::vector<int32_t> cell_chunk(nc_all), block_first;
-  for (int q = 0; q < nch; ++q)
+  for (int q = 0; q < nch; ++q) {
+    if (ch_first[q + 1] - ch_first[q] > threads) return cudaErrorInvalidValue;
     for (int i = ch_first[q]; i < ch_first[q + 1]; ++i) cell_chunk[i] = q;
+  }
   for (int q = 0; q < nch;) {
     block_first.push_back(q);
     int q1 = q;
-    while (q1 < nch && ch_first[q1 + 1] - ch_first[q] <= kRegThreads) ++q1;
+    while (q1 < nch && ch_first[q1 + 1] - ch_first[q] <= threads) ++q1;
     q = std::max(q1, q + 1);
   }
   block_first.push_back(nch);
