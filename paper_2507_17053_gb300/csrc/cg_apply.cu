@@ -150,11 +150,12 @@ __global__ void assemble_kernel(const T* __restrict__ ycol, const int32_t* __res
 // Single right-hand side: two shared DoFs per thread (entries b + tid and
 // b + 256 + tid of a 512-entry tile; assemble_pair).  FP32: Q4 sphere 41 ->
 // 37.5 us, p = 3 20.6 -> 16.7 us against one per thread (four: 41 / 20.6).
-// The tiles go in reverse list order (block 0 takes the last tile): the list
-// ascends in DoF number like the cell kernel's stores, so the first blocks
-// read the colour values written last, while they are still in L2 (every
-// DoF's sum is independent of the order; Q4 sphere FP32 35.6 -> 33.1 us,
-// FP64 50.0 -> 46.3 us).
+// The tiles go in reverse list order (block 0 takes the last tile), so that
+// the first blocks read the colour values the cell kernel stored last (the
+// list ascends in DoF number, as its stores do).  Every DoF's sum is
+// independent of the order.  Measured: Q4 sphere FP32 35.6 -> 33.1 us, FP64
+// 50.0 -> 46.3 us in a loop of applies, and also faster with cold caches
+// (ncu, FP64 39.0 -> 34.7 us), so L2 reuse is not the whole reason.
 template <typename T>
 __global__ void __launch_bounds__(256)
 assemble_set_kernel(const T* __restrict__ ycol, const int32_t* __restrict__ multi,
